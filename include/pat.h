@@ -1,0 +1,231 @@
+/*
+ * pat.h -- C ABI of the GB300 photoacoustic operator library (libpat.so).
+ *
+ * The library applies the planar-geometry photoacoustic forward operator H of
+ * Küçükkömürcü, Labouesse, Allain & Chaigne ("A depth-dependent, transverse
+ * shift-invariant operator for fast iterative 3D photoacoustic tomography in
+ * planar geometry"), its discrete adjoint H*, and FISTA on top of them, with
+ * hand-written CUDA kernels for sm_103a.
+ *
+ *   Eq. 7-8   d(r, t)   = sum_z  h_z(., t) (*) rho(., z)        (forward)
+ *   Eq. 9-11  H*d(r, z) = sum_t  h_z(., t) (x) d(., t)          (adjoint: correlation)
+ *   Eq. 12-15 FISTA for 1/2 ||H rho - d||^2 + lambda ||rho||_1 + indicator(rho >= 0)
+ *
+ * Both operators run as three stages (Sec. 3.2, Eq. 16): zero-padded 2D real
+ * FFTs of every slice, a per-frequency contraction with the stored spectra of
+ * the impulse-response library, and cropped 2D inverse FFTs.
+ *
+ * ---------------------------------------------------------------------------
+ * Conventions (every entry point)
+ *   Arrays are dense, row-major, x fastest:
+ *     object rho [batch][nz][ny][nx],  data d [batch][nt][ny][nx].
+ *   Element type: float for single-precision plans, double for plans created
+ *   with PAT_FLAG_FP64 ("real_t" below).
+ *   Pointers may be device memory (the normal case; the call is asynchronous on
+ *   `stream`) or host memory (pageable or pinned): host arrays are copied
+ *   through plan-owned device staging buffers and the call returns after the
+ *   result is back in host memory.
+ *   The caller owns every array it passes; the library keeps no pointer to
+ *   them after a call returns. A plan owns its table copy and its workspace.
+ *   `stream` is a cudaStream_t (0 = legacy default stream).
+ *   Calls on one plan must not overlap (one plan = one stream of work); plans
+ *   are independent of each other.
+ * Errors
+ *   Every int-returning function returns PAT_OK (0) or a negative pat_status.
+ *   No C++ exception crosses the ABI. On an argument error nothing is launched
+ *   and outputs are untouched. pat_last_error() gives a message for the last
+ *   failure on the calling thread.
+ * ---------------------------------------------------------------------------
+ */
+#ifndef PAT_H
+#define PAT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pat_plan pat_plan;       /* opaque */
+typedef struct CUstream_st* pat_stream; /* the same handle as cudaStream_t */
+
+typedef enum {
+  PAT_OK = 0,
+  PAT_ERR_ARG = -1,         /* invalid argument (size, pointer, format, batch)  */
+  PAT_ERR_OOM = -2,         /* device or host allocation failed                  */
+  PAT_ERR_CUDA = -3,        /* a CUDA runtime call or kernel launch failed       */
+  PAT_ERR_TIMEOUT = -4,     /* a bounded device-side wait gave up                */
+  PAT_ERR_UNSUPPORTED = -5  /* valid request this build does not implement       */
+} pat_status;
+
+enum {
+  PAT_FLAG_FP64 = 1,          /* table, workspace and arrays in double precision */
+  PAT_FLAG_FORCE_COMPLEX = 2  /* keep the complex table even when it is real     */
+};
+
+/* Grid of one plan.
+ *   nx, ny   transverse grid of rho and d (Sec. 2.2, G_xy)
+ *   nz       depth planes of rho (G_z);  nt  time samples of d (T)
+ *   px, py   padded transverse grid for linear convolution (Sec. 2.3, end):
+ *            powers of two, 16 <= p <= 1024, px >= 2 nx - 1, py >= 2 ny - 1
+ *   max_batch  largest `batch` any call on this plan may pass (sizes workspace)
+ *   flags    PAT_FLAG_* */
+typedef struct {
+  int32_t nx, ny, nz, nt;
+  int32_t px, py;
+  int32_t max_batch;
+  int32_t flags;
+} pat_geometry;
+
+/* Layout of the impulse-response library handed to pat_plan_create.
+ * SPATIAL: h[nz][nt][py][px] real; the kernel value for transverse
+ *   displacement (ux, uy) sits at [uy mod py][ux mod px] ("wrapped origin");
+ *   constant discretisation factors are already folded in (Sec. 2.2).
+ * SPECTRAL: Hh[nz][nt][py][px/2 + 1] complex (re, im interleaved), the
+ *   non-negative-kx half of the unnormalised 2D DFT exp(-2 pi i k.n / P) of h. */
+typedef enum {
+  PAT_TABLE_SPATIAL_F64 = 0,
+  PAT_TABLE_SPATIAL_F32 = 1,
+  PAT_TABLE_SPECTRAL_C128 = 2,
+  PAT_TABLE_SPECTRAL_C64 = 3
+} pat_table_format;
+
+/* Homogeneous lossless medium for a library generated on the device from the
+ * exact k-space solution of Eq. 1-2 on a periodic px x py x mz grid (one
+ * unit point source, recorded on the planes z = (z0 + j) dz, Sec. 3.2):
+ *   Hh[j][t](kx, ky) = (1/mz) sum_m cos(c t dt |k|) cos(2 pi m (z0 + j) / mz),
+ *   |k|^2 = kx^2 + ky^2 + (2 pi m_s / (mz dz))^2, m_s the signed index of m. */
+typedef struct {
+  double c;          /* sound speed [m/s] */
+  double dx, dy, dz; /* voxel steps [m] */
+  double dt;         /* sampling step [s]; t_n = n dt, n = 0..nt-1 */
+  int32_t mz;        /* depth period of the solve: power of two > z0 + nz */
+  int32_t z0;        /* index of the first object plane (>= 0) */
+} pat_medium;
+
+/* Information about a plan (filled by pat_plan_info). */
+typedef struct {
+  int32_t real_table;      /* 1: the stored spectra are real (even kernels) */
+  int32_t fp64;            /* 1: double-precision plan */
+  int64_t bins;            /* stored frequency bins K = (px/2 + 1) py */
+  int64_t table_bytes;     /* device bytes of the resident table */
+  int64_t workspace_bytes; /* device bytes of the plan's workspace */
+  double table_max_abs;    /* max |Hh| seen while building the table */
+  double table_max_imag;   /* max |Im Hh| seen while building the table */
+} pat_plan_info_t;
+
+/* FISTA settings (Eq. 12-14; Beck & Teboulle's constant-step scheme).
+ *   iters       iterations (>= 0)
+ *   lambda      l1 weight of Eq. 14 (>= 0); lambda = 0 gives non-negative least squares
+ *   L           Lipschitz constant ||H*H|| used as step 1/L; L <= 0 asks the
+ *               solver to estimate it with pat_power_norm (power_iters steps
+ *               from a fixed-seed start vector) and multiply by 1.01
+ *   power_iters steps of that estimate (ignored when L > 0)
+ *   warm_start  1: start from the x passed in; 0: start from zero */
+typedef struct {
+  int32_t iters;
+  int32_t power_iters;
+  int32_t warm_start;
+  int32_t reserved;
+  double lambda;
+  double L;
+} pat_fista_params;
+
+/* What pat_fista_solve reports (written after the solve has finished). */
+typedef struct {
+  double L;             /* step-size constant actually used */
+  double resid2_first;  /* ||H y_1 - d||^2 of the first gradient step (batch sum) */
+  double resid2_last;   /* ||H y_k - d||^2 of the last gradient step (batch sum) */
+  int32_t iters;        /* iterations run */
+  int32_t reserved;
+} pat_fista_report;
+
+/* --- plans ------------------------------------------------------------------ */
+
+/* Builds a plan: validates the grid, allocates the device table and workspace,
+ * and converts `table` (host or device memory, layout `fmt`) into the plan's
+ * resident spectral layout. The spectra are scaled by 1/(px py) once here so
+ * the inverse FFTs need no normalisation. When every |Im Hh| <= 1e-6 max |Hh|
+ * (kernels even under (x, y) -> (-x, -y), e.g. the radially symmetric
+ * kernels of Eq. 5) and PAT_FLAG_FORCE_COMPLEX is not set, the imaginary part
+ * is dropped and the real-spectrum contraction is used (half the bytes).
+ * Synchronises `stream` before returning. Table source: Sec. 3.2. */
+int pat_plan_create(const pat_geometry* g, const void* table, pat_table_format fmt,
+                    pat_stream stream, pat_plan** out);
+
+/* Builds a plan whose library is generated on the device from `m` (formula
+ * above; Eq. 1-2 and the single-solve reciprocity construction of Sec. 3.2). */
+int pat_plan_create_kspace(const pat_geometry* g, const pat_medium* m,
+                           pat_stream stream, pat_plan** out);
+
+/* Frees the plan's device memory (synchronises the device first). NULL is a no-op. */
+int pat_plan_destroy(pat_plan* plan);
+
+int pat_plan_info(const pat_plan* plan, pat_plan_info_t* info);
+
+/* Message of the last failure on the calling thread ("" if none). */
+const char* pat_last_error(void);
+
+/* --- operators ----------------------------------------------------------------- */
+
+/* d = H rho (Eq. 7-8) for `batch` volumes. rho: real_t[batch][nz][ny][nx] in,
+ * d: real_t[batch][nt][ny][nx] out. 1 <= batch <= max_batch. */
+int pat_forward(pat_plan* plan, const void* rho, void* d, int batch, pat_stream stream);
+
+/* rho = H* d (Eq. 11), the exact transpose of pat_forward under the Euclidean
+ * inner products of Eq. 10. */
+int pat_adjoint(pat_plan* plan, const void* d, void* rho, int batch, pat_stream stream);
+
+/* Gradient of the data term, Eq. 15: grad = H*(H x - y). x, grad:
+ * real_t[batch][nz][ny][nx]; y: real_t[batch][nt][ny][nx]. If resid2 is not
+ * NULL, *resid2 (host) receives ||H x - y||^2 summed over the batch
+ * (FP64 accumulation) and the call synchronises `stream`. */
+int pat_gradient(pat_plan* plan, const void* x, const void* y, void* grad, int batch,
+                 double* resid2, pat_stream stream);
+
+/* L = ||H*H||_2 by power iteration (not printed in the paper; FISTA's step):
+ * v <- H*H v / ||H*H v|| from the start vector v0 (real_t[nz][ny][nx], host or
+ * device, need not be normalised), `iters` >= 1 steps; *L_out (host) =
+ * ||H*H v|| of the last step. Norms accumulate in FP64. Synchronises `stream`. */
+int pat_power_norm(pat_plan* plan, const void* v0, int iters, double* L_out,
+                   pat_stream stream);
+
+/* FISTA for Eq. 12 with f of Eq. 13 and g of Eq. 14, per volume:
+ *   y_1 = x_0, t_1 = 1;  x_k = max(y_k - (H*(H y_k - d))/L - lambda/L, 0);
+ *   t_{k+1} = (1 + sqrt(1 + 4 t_k^2)) / 2;
+ *   y_{k+1} = x_k + ((t_k - 1)/t_{k+1}) (x_k - x_{k-1}).
+ * y: measured data real_t[batch][nt][ny][nx]; x: real_t[batch][nz][ny][nx],
+ * read when warm_start = 1, overwritten with x_iters. Each iteration runs as
+ * one replay of a CUDA graph captured on the first call for this batch size.
+ * `report` may be NULL; if given, the call synchronises `stream` and fills it. */
+int pat_fista_solve(pat_plan* plan, const void* y, void* x, int batch,
+                    const pat_fista_params* params, pat_fista_report* report,
+                    pat_stream stream);
+
+/* <a, b> = sum_i a[i] b[i] with products and sums in FP64 (the adjoint test of
+ * Eq. 9 and the norms). a, b: real_t[n] device arrays of the plan's precision.
+ * *out (host) receives the result; synchronises `stream`. Deterministic: the
+ * same inputs give the same bits. */
+int pat_dot_f64(pat_plan* plan, const void* a, const void* b, int64_t n, double* out,
+                pat_stream stream);
+
+/* --- diagnostics: the FFT stages on their own ----------------------------------- */
+
+/* Zero-pads `slices` real [ny][nx] slices to py x px and applies the 2D real
+ * DFT (stage i of Sec. 3.2; Eq. 16 term (i)). Output in the plan's spectral
+ * layout: complex[slices][px/2 + 1][py] (kx-major, ky contiguous).
+ * in: real_t[slices][ny][nx] device; out: device. slices <= max_batch * max(nz, nt). */
+int pat_stage_spectrum(pat_plan* plan, const void* in, void* out, int slices,
+                       pat_stream stream);
+
+/* Inverse of the layout above for `slices` planes: unnormalised inverse 2D DFT
+ * (sum over k of X(k) exp(+2 pi i k.n / P)), real part, cropped to [ny][nx]
+ * (stage iii; Eq. 16 term (iii)). */
+int pat_stage_image(pat_plan* plan, const void* in, void* out, int slices,
+                    pat_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PAT_H */

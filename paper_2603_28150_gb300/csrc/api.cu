@@ -1,0 +1,639 @@
+// C ABI of libpat (declared in include/pat.h): plans, the operator H (Eq. 7-8),
+// its adjoint H* (Eq. 11), the gradient of Eq. 15, the power iteration for
+// ||H*H|| and FISTA (Eq. 12-14) composed from the stage kernels.
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "pat_internal.h"
+
+namespace pat {
+
+static thread_local std::string g_err;
+
+void set_error(const std::string& msg) { g_err = msg; }
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+int cuda_fail(cudaError_t e, const char* what) {
+  g_err = std::string(what) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? PAT_ERR_OOM : PAT_ERR_CUDA;
+}
+
+struct Graph {
+  int batch = 0;
+  cudaGraphExec_t exec = nullptr;
+  Graph* next = nullptr;
+};
+
+// Extra plan state that only this file touches.
+struct PlanExt {
+  void* io_obj[2] = {nullptr, nullptr};  // host-pointer staging (objects)
+  void* io_dat = nullptr;                // host-pointer staging (data)
+  double* res = nullptr;                 // device scalars: [0] dot, [1] r2 current, [2] norm
+  double* scal = nullptr;                // device scalars: [0] 1/L, [1] lambda/L
+  cudaStream_t cap = nullptr;            // private stream for graph capture
+  int c2r_partials = 0;
+};
+
+}  // namespace pat
+
+struct pat_plan {
+  pat::Plan p;
+  pat::PlanExt x;
+};
+
+using namespace pat;
+
+namespace {
+
+bool pow2_in(int v, int lo, int hi) { return v >= lo && v <= hi && (v & (v - 1)) == 0; }
+
+int validate(const pat_geometry* g) {
+  if (!g) return fail(PAT_ERR_ARG, "geometry is NULL");
+  if (g->nx < 1 || g->ny < 1 || g->nz < 1 || g->nt < 1)
+    return fail(PAT_ERR_ARG, "nx, ny, nz, nt must be >= 1");
+  if (!pow2_in(g->px, 16, 1024) || !pow2_in(g->py, 16, 1024))
+    return fail(PAT_ERR_UNSUPPORTED, "px and py must be powers of two in [16, 1024]");
+  if (g->px < 2 * g->nx - 1 || g->py < 2 * g->ny - 1)
+    return fail(PAT_ERR_ARG, "padding too small for linear convolution: need px >= 2nx-1, py >= 2ny-1");
+  if (g->max_batch < 1) return fail(PAT_ERR_ARG, "max_batch must be >= 1");
+  if (g->flags & ~(PAT_FLAG_FP64 | PAT_FLAG_FORCE_COMPLEX)) return fail(PAT_ERR_ARG, "unknown flags");
+  const int64_t smax = (int64_t)g->max_batch * std::max(g->nz, g->nt);
+  if (smax > 65535) return fail(PAT_ERR_UNSUPPORTED, "max_batch * max(nz, nt) must be <= 65535");
+  return PAT_OK;
+}
+
+Layout make_layout(const pat_geometry* g) {
+  Layout L{};
+  L.nx = g->nx;
+  L.ny = g->ny;
+  L.nz = g->nz;
+  L.nt = g->nt;
+  L.px = g->px;
+  L.py = g->py;
+  L.max_batch = g->max_batch;
+  L.fp64 = (g->flags & PAT_FLAG_FP64) != 0;
+  L.rsize = L.fp64 ? 8 : 4;
+  L.K = (int64_t)(g->px / 2 + 1) * g->py;
+  L.Kpad = (L.K + 31) / 32 * 32;
+  L.nkb = L.Kpad / 32;
+  L.tstride = g->ny + (g->ny & 1);
+  L.tslice = (int64_t)(g->px / 2 + 1) * L.tstride;
+  set_representation(L, false);
+  return L;
+}
+
+void free_plan(pat_plan* pp) {
+  if (!pp) return;
+  Plan& p = pp->p;
+  PlanExt& x = pp->x;
+  for (Graph* g = p.graphs; g;) {
+    Graph* n = g->next;
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    delete g;
+    g = n;
+  }
+  void* bufs[] = {p.table, p.twx,    p.twy,     p.X,         p.Y,      p.T,       p.vol_a,
+                  p.vol_b, p.vol_c,  p.dat_a,   p.dat_b,     p.red,    p.betas,   p.iter_dev,
+                  p.r2_dev, x.io_obj[0], x.io_obj[1], x.io_dat, x.res, x.scal};
+  for (void* b : bufs) cudaFree(b);
+  if (x.cap) cudaStreamDestroy(x.cap);
+  delete pp;
+}
+
+int upload_twiddles(Plan& p) {
+  const double pi = 3.14159265358979323846;
+  for (int a = 0; a < 2; ++a) {
+    const int n = a == 0 ? p.L.px : p.L.py;
+    std::vector<double> w(2 * (size_t)n);
+    for (int k = 0; k < n; ++k) {
+      w[2 * k] = std::cos(-2.0 * pi * k / n);
+      w[2 * k + 1] = std::sin(-2.0 * pi * k / n);
+    }
+    void** dst = a == 0 ? &p.twx : &p.twy;
+    if (p.L.fp64) {
+      PAT_CUDA(cudaMalloc(dst, w.size() * 8));
+      PAT_CUDA(cudaMemcpy(*dst, w.data(), w.size() * 8, cudaMemcpyHostToDevice));
+    } else {
+      std::vector<float> f(w.begin(), w.end());
+      PAT_CUDA(cudaMalloc(dst, f.size() * 4));
+      PAT_CUDA(cudaMemcpy(*dst, f.data(), f.size() * 4, cudaMemcpyHostToDevice));
+    }
+  }
+  return PAT_OK;
+}
+
+// Upper bound of the blocks of the stage-iii row kernel (its residual partials).
+int c2r_partials_bound(const Layout& L) {
+  const int64_t smax = (int64_t)L.max_batch * std::max(L.nz, L.nt);
+  return (int)(smax * ((L.ny + 1) / 2 + 1));
+}
+
+int alloc_workspace(pat_plan* pp) {
+  Plan& p = pp->p;
+  PlanExt& x = pp->x;
+  const Layout& L = p.L;
+  const size_t cs = 2 * L.rsize;
+  const int64_t smax = (int64_t)L.max_batch * std::max(L.nz, L.nt);
+  const size_t xy = (size_t)smax * L.Kpad * cs;
+  const size_t tb = (size_t)smax * L.tslice * cs;
+  const size_t vol = (size_t)L.max_batch * L.nz * L.ny * L.nx * L.rsize;
+  const size_t dat = (size_t)L.max_batch * L.nt * L.ny * L.nx * L.rsize;
+  x.c2r_partials = std::max(kReduceBlocks, c2r_partials_bound(L));
+  PAT_CUDA(cudaMalloc(&p.X, xy));
+  PAT_CUDA(cudaMalloc(&p.Y, xy));
+  PAT_CUDA(cudaMalloc(&p.T, tb));
+  PAT_CUDA(cudaMalloc(&p.vol_a, vol));
+  PAT_CUDA(cudaMalloc(&p.vol_b, vol));
+  PAT_CUDA(cudaMalloc(&p.vol_c, vol));
+  PAT_CUDA(cudaMalloc(&p.dat_a, dat));
+  PAT_CUDA(cudaMalloc(&p.dat_b, dat));
+  PAT_CUDA(cudaMalloc(&p.red, sizeof(double) * x.c2r_partials));
+  PAT_CUDA(cudaMalloc(&x.res, sizeof(double) * 8));
+  PAT_CUDA(cudaMalloc(&x.scal, sizeof(double) * 2));
+  PAT_CUDA(cudaMalloc(&p.iter_dev, sizeof(int)));
+  PAT_CUDA(cudaStreamCreateWithFlags(&x.cap, cudaStreamNonBlocking));
+  p.ws_bytes = 2 * xy + tb + 3 * vol + 2 * dat + sizeof(double) * (x.c2r_partials + 10);
+  return PAT_OK;
+}
+
+int ensure_io(pat_plan* pp) {
+  PlanExt& x = pp->x;
+  if (x.io_dat) return PAT_OK;
+  const Layout& L = pp->p.L;
+  const size_t vol = (size_t)L.max_batch * L.nz * L.ny * L.nx * L.rsize;
+  const size_t dat = (size_t)L.max_batch * L.nt * L.ny * L.nx * L.rsize;
+  PAT_CUDA(cudaMalloc(&x.io_obj[0], vol));
+  PAT_CUDA(cudaMalloc(&x.io_obj[1], vol));
+  PAT_CUDA(cudaMalloc(&x.io_dat, dat));
+  return PAT_OK;
+}
+
+int create_common(const pat_geometry* g, pat_plan** out, pat_plan** pp_out) {
+  if (!out) return fail(PAT_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  int rc = validate(g);
+  if (rc != PAT_OK) return rc;
+  pat_plan* pp = new (std::nothrow) pat_plan();
+  if (!pp) return fail(PAT_ERR_OOM, "host allocation of the plan failed");
+  pp->p.L = make_layout(g);
+  if ((rc = upload_twiddles(pp->p)) != PAT_OK || (rc = alloc_workspace(pp)) != PAT_OK) {
+    free_plan(pp);
+    return rc;
+  }
+  *pp_out = pp;
+  return PAT_OK;
+}
+
+size_t obj_elems(const Layout& L, int batch) { return (size_t)batch * L.nz * L.ny * L.nx; }
+size_t dat_elems(const Layout& L, int batch) { return (size_t)batch * L.nt * L.ny * L.nx; }
+
+// d = H rho on device buffers; with `sub`, d = H rho - sub and ||d||^2 -> *sumsq.
+cudaError_t forward_dev(const Plan& p, const void* rho, void* d, int batch, cudaStream_t s,
+                        const void* sub = nullptr, double* sumsq = nullptr) {
+  const Layout& L = p.L;
+  const int64_t plane = (int64_t)L.ny * L.nx;
+  cudaError_t e = launch_spectrum(p, rho, plane, L.nx, L.ny, p.X, L.Kpad, batch * L.nz, s);
+  if (e != cudaSuccess) return e;
+  if ((e = launch_contract_fwd(p, p.X, p.Y, batch, s)) != cudaSuccess) return e;
+  return launch_image(p, p.Y, L.Kpad, d, plane, batch * L.nt, sub, sumsq, s);
+}
+
+// rho = H* d on device buffers.
+cudaError_t adjoint_dev(const Plan& p, const void* d, void* rho, int batch, cudaStream_t s) {
+  const Layout& L = p.L;
+  const int64_t plane = (int64_t)L.ny * L.nx;
+  cudaError_t e = launch_spectrum(p, d, plane, L.nx, L.ny, p.Y, L.Kpad, batch * L.nt, s);
+  if (e != cudaSuccess) return e;
+  if ((e = launch_contract_adj(p, p.Y, p.X, batch, s)) != cudaSuccess) return e;
+  return launch_image(p, p.X, L.Kpad, rho, plane, batch * L.nz, nullptr, nullptr, s);
+}
+
+int check_call(pat_plan* plan, int batch) {
+  if (!plan) return fail(PAT_ERR_ARG, "plan is NULL");
+  if (batch < 0 || batch > plan->p.L.max_batch)
+    return fail(PAT_ERR_ARG, "batch must be in [0, max_batch]");
+  return PAT_OK;
+}
+
+// Host-or-device argument: a device pointer is used as is; a host pointer is
+// staged (copied in for inputs) through `stage`.
+struct Arg {
+  const void* user;
+  void* dev;
+  bool host;
+};
+
+int stage_in(Arg& a, void* stage, size_t bytes, cudaStream_t s) {
+  a.host = !is_device_ptr(a.user);
+  a.dev = a.host ? stage : const_cast<void*>(a.user);
+  if (a.host && bytes) PAT_CUDA(cudaMemcpyAsync(stage, a.user, bytes, cudaMemcpyHostToDevice, s));
+  return PAT_OK;
+}
+
+int any_host(std::initializer_list<const void*> ptrs) {
+  for (const void* q : ptrs)
+    if (q && !is_device_ptr(q)) return 1;
+  return 0;
+}
+
+// Fixed-seed start vector of the internal step-size estimate (splitmix64 ->
+// uniform [-1, 1)); any start with a component along the top singular vector works.
+template <typename R>
+__global__ void k_fill_hash(R* v, int64_t n, unsigned long long seed) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    unsigned long long z = seed + 0x9E3779B97F4A7C15ull * (unsigned long long)(i + 1);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    v[i] = (R)((double)(z >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0);
+  }
+}
+
+__global__ void k_record_tick(int* iter, const double* r2_cur, double* r2_hist, int cap) {
+  const int k = *iter;
+  if (k < cap) r2_hist[k] = *r2_cur;
+  *iter = k + 1;
+}
+
+// Power iteration on the plan's buffers: v in vol_a (normalised here first).
+int power_dev(pat_plan* pp, int iters, double* L_out, cudaStream_t s) {
+  Plan& p = pp->p;
+  PlanExt& x = pp->x;
+  const Layout& L = p.L;
+  const int64_t n = (int64_t)obj_elems(L, 1);
+  PAT_CUDA(launch_dot(p, p.vol_a, p.vol_a, n, x.res + 2, s));
+  PAT_CUDA(launch_scale_by_inv_norm(p, p.vol_a, p.vol_a, n, x.res + 2, s));
+  for (int i = 0; i < iters; ++i) {
+    PAT_CUDA(forward_dev(p, p.vol_a, p.dat_a, 1, s));
+    PAT_CUDA(adjoint_dev(p, p.dat_a, p.vol_c, 1, s));
+    PAT_CUDA(launch_dot(p, p.vol_c, p.vol_c, n, x.res + 2, s));
+    PAT_CUDA(launch_scale_by_inv_norm(p, p.vol_c, p.vol_a, n, x.res + 2, s));
+  }
+  double h = 0;
+  PAT_CUDA(cudaMemcpyAsync(&h, x.res + 2, sizeof(double), cudaMemcpyDeviceToHost, s));
+  PAT_CUDA(cudaStreamSynchronize(s));
+  *L_out = std::sqrt(h);
+  return PAT_OK;
+}
+
+// One FISTA iteration on the plan's buffers (what the graph holds):
+// vol_a = y_k, vol_b = x_{k-1}, dat_b = measured data.
+cudaError_t fista_iter(pat_plan* pp, int batch, cudaStream_t s) {
+  Plan& p = pp->p;
+  PlanExt& x = pp->x;
+  const Layout& L = p.L;
+  cudaError_t e = forward_dev(p, p.vol_a, p.dat_a, batch, s, p.dat_b, x.res + 1);
+  if (e != cudaSuccess) return e;
+  if ((e = adjoint_dev(p, p.dat_a, p.vol_c, batch, s)) != cudaSuccess) return e;
+  if ((e = launch_fista_update(p, p.vol_a, p.vol_b, p.vol_c, (int64_t)obj_elems(L, batch),
+                                   x.scal, p.betas, p.iter_dev, s)) != cudaSuccess)
+    return e;
+  k_record_tick<<<1, 1, 0, s>>>(p.iter_dev, x.res + 1, p.r2_dev, p.r2_cap);
+  return cudaGetLastError();
+}
+
+Graph* graph_for(pat_plan* pp, int batch, int* rc) {
+  Plan& p = pp->p;
+  for (Graph* g = p.graphs; g; g = g->next)
+    if (g->batch == batch) return g;
+  cudaStream_t cs = pp->x.cap;
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
+  if (e == cudaSuccess) {
+    cudaError_t e2 = fista_iter(pp, batch, cs);
+    e = cudaStreamEndCapture(cs, &graph);
+    if (e2 != cudaSuccess) e = e2;
+  }
+  cudaGraphExec_t exec = nullptr;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    *rc = cuda_fail(e, "capturing the FISTA iteration graph");
+    return nullptr;
+  }
+  Graph* g = new (std::nothrow) Graph();
+  if (!g) {
+    cudaGraphExecDestroy(exec);
+    *rc = fail(PAT_ERR_OOM, "host allocation failed");
+    return nullptr;
+  }
+  g->batch = batch;
+  g->exec = exec;
+  g->next = p.graphs;
+  p.graphs = g;
+  return g;
+}
+
+}  // namespace
+
+
+#define PAT_GUARD_BEGIN try {
+#define PAT_GUARD_END                                                  \
+  }                                                                    \
+  catch (const std::bad_alloc&) {                                      \
+    return fail(PAT_ERR_OOM, "host allocation failed");                \
+  }                                                                    \
+  catch (...) {                                                        \
+    return fail(PAT_ERR_CUDA, "unexpected internal error");            \
+  }
+
+extern "C" {
+
+const char* pat_last_error(void) { return pat::g_err.c_str(); }
+
+int pat_plan_create(const pat_geometry* g, const void* table, pat_table_format fmt,
+                    pat_stream stream, pat_plan** out) {
+  PAT_GUARD_BEGIN
+  if (!table) return fail(PAT_ERR_ARG, "table is NULL");
+  if (fmt < PAT_TABLE_SPATIAL_F64 || fmt > PAT_TABLE_SPECTRAL_C64)
+    return fail(PAT_ERR_ARG, "unknown table format");
+  pat_plan* pp = nullptr;
+  int rc = create_common(g, out, &pp);
+  if (rc != PAT_OK) return rc;
+  rc = build_table_from_source(pp->p, table, fmt, (g->flags & PAT_FLAG_FORCE_COMPLEX) != 0,
+                               (cudaStream_t)stream);
+  if (rc != PAT_OK) {
+    free_plan(pp);
+    return rc;
+  }
+  *out = pp;
+  return PAT_OK;
+  PAT_GUARD_END
+}
+
+int pat_plan_create_kspace(const pat_geometry* g, const pat_medium* m, pat_stream stream,
+                           pat_plan** out) {
+  PAT_GUARD_BEGIN
+  if (!m) return fail(PAT_ERR_ARG, "medium is NULL");
+  if (!(m->c > 0 && m->dx > 0 && m->dy > 0 && m->dz > 0 && m->dt > 0))
+    return fail(PAT_ERR_ARG, "medium: c, dx, dy, dz, dt must be > 0");
+  if (m->z0 < 0 || !pow2_in(m->mz, 2, 1 << 16) || m->mz <= m->z0 + (g ? g->nz : 0))
+    return fail(PAT_ERR_ARG, "medium: mz must be a power of two > z0 + nz, z0 >= 0");
+  pat_plan* pp = nullptr;
+  int rc = create_common(g, out, &pp);
+  if (rc != PAT_OK) return rc;
+  rc = build_table_kspace(pp->p, *m, (g->flags & PAT_FLAG_FORCE_COMPLEX) != 0,
+                          (cudaStream_t)stream);
+  if (rc != PAT_OK) {
+    free_plan(pp);
+    return rc;
+  }
+  *out = pp;
+  return PAT_OK;
+  PAT_GUARD_END
+}
+
+int pat_plan_destroy(pat_plan* plan) {
+  PAT_GUARD_BEGIN
+  if (!plan) return PAT_OK;
+  cudaDeviceSynchronize();
+  free_plan(plan);
+  return PAT_OK;
+  PAT_GUARD_END
+}
+
+int pat_plan_info(const pat_plan* plan, pat_plan_info_t* info) {
+  if (!plan || !info) return fail(PAT_ERR_ARG, "plan or info is NULL");
+  const Plan& p = plan->p;
+  info->real_table = p.L.real ? 1 : 0;
+  info->fp64 = p.L.fp64 ? 1 : 0;
+  info->bins = p.L.K;
+  info->table_bytes = (int64_t)p.L.table_bytes;
+  info->workspace_bytes = (int64_t)p.ws_bytes;
+  info->table_max_abs = p.table_max_abs;
+  info->table_max_imag = p.table_max_imag;
+  return PAT_OK;
+}
+
+int pat_forward(pat_plan* plan, const void* rho, void* d, int batch, pat_stream stream) {
+  PAT_GUARD_BEGIN
+  int rc = check_call(plan, batch);
+  if (rc != PAT_OK) return rc;
+  if (batch == 0) return PAT_OK;
+  if (!rho || !d) return fail(PAT_ERR_ARG, "rho or d is NULL");
+  Plan& p = plan->p;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t ob = obj_elems(p.L, batch) * p.L.rsize, db = dat_elems(p.L, batch) * p.L.rsize;
+  if (any_host({rho, d}) && (rc = ensure_io(plan)) != PAT_OK) return rc;
+  Arg a{rho, nullptr, false};
+  if ((rc = stage_in(a, plan->x.io_obj[0], ob, s)) != PAT_OK) return rc;
+  const bool hout = !is_device_ptr(d);
+  void* dst = hout ? plan->x.io_dat : d;
+  PAT_CUDA(forward_dev(p, a.dev, dst, batch, s));
+  if (hout) {
+    PAT_CUDA(cudaMemcpyAsync(d, dst, db, cudaMemcpyDeviceToHost, s));
+    PAT_CUDA(cudaStreamSynchronize(s));
+  } else if (a.host) {
+    PAT_CUDA(cudaStreamSynchronize(s));
+  }
+  return PAT_OK;
+  PAT_GUARD_END
+}
+
+int pat_adjoint(pat_plan* plan, const void* d, void* rho, int batch, pat_stream stream) {
+  PAT_GUARD_BEGIN
+  int rc = check_call(plan, batch);
+  if (rc != PAT_OK) return rc;
+  if (batch == 0) return PAT_OK;
+  if (!rho || !d) return fail(PAT_ERR_ARG, "rho or d is NULL");
+  Plan& p = plan->p;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t ob = obj_elems(p.L, batch) * p.L.rsize, db = dat_elems(p.L, batch) * p.L.rsize;
+  if (any_host({rho, d}) && (rc = ensure_io(plan)) != PAT_OK) return rc;
+  Arg a{d, nullptr, false};
+  if ((rc = stage_in(a, plan->x.io_dat, db, s)) != PAT_OK) return rc;
+  const bool hout = !is_device_ptr(rho);
+  void* dst = hout ? plan->x.io_obj[0] : rho;
+  PAT_CUDA(adjoint_dev(p, a.dev, dst, batch, s));
+  if (hout) {
+    PAT_CUDA(cudaMemcpyAsync(rho, dst, ob, cudaMemcpyDeviceToHost, s));
+    PAT_CUDA(cudaStreamSynchronize(s));
+  } else if (a.host) {
+    PAT_CUDA(cudaStreamSynchronize(s));
+  }
+  return PAT_OK;
+  PAT_GUARD_END
+}
+
+int pat_gradient(pat_plan* plan, const void* xin, const void* y, void* grad, int batch,
+                 double* resid2, pat_stream stream) {
+  PAT_GUARD_BEGIN
+  int rc = check_call(plan, batch);
+  if (rc != PAT_OK) return rc;
+  if (batch == 0) {
+    if (resid2) *resid2 = 0.0;
+    return PAT_OK;
+  }
+  if (!xin || !y || !grad) return fail(PAT_ERR_ARG, "x, y or grad is NULL");
+  Plan& p = plan->p;
+  PlanExt& px = plan->x;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t ob = obj_elems(p.L, batch) * p.L.rsize, db = dat_elems(p.L, batch) * p.L.rsize;
+  if (any_host({xin, y, grad}) && (rc = ensure_io(plan)) != PAT_OK) return rc;
+  Arg ax{xin, nullptr, false}, ay{y, nullptr, false};
+  if ((rc = stage_in(ax, px.io_obj[0], ob, s)) != PAT_OK) return rc;
+  if ((rc = stage_in(ay, px.io_dat, db, s)) != PAT_OK) return rc;
+  const bool hout = !is_device_ptr(grad);
+  void* dst = hout ? px.io_obj[1] : grad;
+  PAT_CUDA(forward_dev(p, ax.dev, p.dat_a, batch, s, ay.dev, px.res + 1));
+  PAT_CUDA(adjoint_dev(p, p.dat_a, dst, batch, s));
+  if (hout) PAT_CUDA(cudaMemcpyAsync(grad, dst, ob, cudaMemcpyDeviceToHost, s));
+  if (resid2) PAT_CUDA(cudaMemcpyAsync(resid2, px.res + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
+  if (hout || resid2 || ax.host || ay.host) PAT_CUDA(cudaStreamSynchronize(s));
+  return PAT_OK;
+  PAT_GUARD_END
+}
+
+int pat_power_norm(pat_plan* plan, const void* v0, int iters, double* L_out, pat_stream stream) {
+  PAT_GUARD_BEGIN
+  int rc = check_call(plan, 1);
+  if (rc != PAT_OK) return rc;
+  if (!v0 || !L_out || iters < 1) return fail(PAT_ERR_ARG, "v0 / L_out NULL or iters < 1");
+  Plan& p = plan->p;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t ob = obj_elems(p.L, 1) * p.L.rsize;
+  PAT_CUDA(cudaMemcpyAsync(p.vol_a, v0, ob, cudaMemcpyDefault, s));
+  return power_dev(plan, iters, L_out, s);
+  PAT_GUARD_END
+}
+
+int pat_fista_solve(pat_plan* plan, const void* y, void* x, int batch,
+                    const pat_fista_params* prm, pat_fista_report* report, pat_stream stream) {
+  PAT_GUARD_BEGIN
+  int rc = check_call(plan, batch);
+  if (rc != PAT_OK) return rc;
+  if (!y || !x || !prm) return fail(PAT_ERR_ARG, "y, x or params is NULL");
+  if (prm->iters < 0 || !(prm->lambda >= 0) || (prm->L <= 0 && prm->power_iters < 1))
+    return fail(PAT_ERR_ARG, "need iters >= 0, lambda >= 0, and L > 0 or power_iters >= 1");
+  Plan& p = plan->p;
+  PlanExt& px = plan->x;
+  const Layout& L = p.L;
+  cudaStream_t s = (cudaStream_t)stream;
+  double Lc = prm->L;
+  if (Lc <= 0) {
+    const int64_t n = (int64_t)obj_elems(L, 1);
+    if (L.fp64)
+      k_fill_hash<double><<<64, 256, 0, s>>>(static_cast<double*>(p.vol_a), n, 0x5EEDull);
+    else
+      k_fill_hash<float><<<64, 256, 0, s>>>(static_cast<float*>(p.vol_a), n, 0x5EEDull);
+    PAT_CUDA(cudaGetLastError());
+    if ((rc = power_dev(plan, prm->power_iters, &Lc, s)) != PAT_OK) return rc;
+    Lc *= 1.01;
+  }
+  if (batch == 0) {
+    if (report) *report = pat_fista_report{Lc, 0, 0, 0, 0};
+    return PAT_OK;
+  }
+  const size_t ob = obj_elems(L, batch) * L.rsize, db = dat_elems(L, batch) * L.rsize;
+  // momentum coefficients beta_k = (t_k - 1) / t_{k+1} (FP64 on the host)
+  const int iters = prm->iters;
+  if (p.betas_cap < iters + 1) {
+    cudaFree(p.betas);
+    cudaFree(p.r2_dev);
+    p.betas = nullptr;
+    p.r2_dev = nullptr;
+    p.betas_cap = p.r2_cap = 0;
+    const int cap = std::max(iters + 1, 128);
+    PAT_CUDA(cudaMalloc(&p.betas, sizeof(double) * cap));
+    PAT_CUDA(cudaMalloc(&p.r2_dev, sizeof(double) * cap));
+    p.betas_cap = p.r2_cap = cap;
+    for (Graph* g = p.graphs; g;) {  // graphs captured the old pointers
+      Graph* n = g->next;
+      cudaGraphExecDestroy(g->exec);
+      delete g;
+      g = n;
+    }
+    p.graphs = nullptr;
+  }
+  std::vector<double> betas(iters + 1, 0.0);
+  double t = 1.0;
+  for (int k = 0; k < iters; ++k) {
+    const double tn = (1.0 + std::sqrt(1.0 + 4.0 * t * t)) / 2.0;
+    betas[k] = (t - 1.0) / tn;
+    t = tn;
+  }
+  const double scal[2] = {1.0 / Lc, prm->lambda / Lc};
+  PAT_CUDA(cudaMemcpyAsync(p.betas, betas.data(), sizeof(double) * (iters + 1),
+                           cudaMemcpyHostToDevice, s));
+  PAT_CUDA(cudaMemcpyAsync(px.scal, scal, sizeof(scal), cudaMemcpyHostToDevice, s));
+  PAT_CUDA(cudaMemsetAsync(p.iter_dev, 0, sizeof(int), s));
+  PAT_CUDA(cudaMemsetAsync(p.r2_dev, 0, sizeof(double) * p.r2_cap, s));
+  PAT_CUDA(cudaMemcpyAsync(p.dat_b, y, db, cudaMemcpyDefault, s));
+  if (prm->warm_start) {
+    PAT_CUDA(cudaMemcpyAsync(p.vol_b, x, ob, cudaMemcpyDefault, s));
+    PAT_CUDA(cudaMemcpyAsync(p.vol_a, p.vol_b, ob, cudaMemcpyDeviceToDevice, s));
+  } else {
+    PAT_CUDA(cudaMemsetAsync(p.vol_b, 0, ob, s));
+    PAT_CUDA(cudaMemsetAsync(p.vol_a, 0, ob, s));
+  }
+  if (iters > 0) {
+    Graph* g = graph_for(plan, batch, &rc);
+    if (!g) return rc;
+    for (int k = 0; k < iters; ++k) PAT_CUDA(cudaGraphLaunch(g->exec, s));
+  }
+  PAT_CUDA(cudaMemcpyAsync(x, p.vol_b, ob, cudaMemcpyDefault, s));
+  if (report) {
+    double r2[2] = {0, 0};
+    if (iters > 0) {
+      PAT_CUDA(cudaMemcpyAsync(&r2[0], p.r2_dev, sizeof(double), cudaMemcpyDeviceToHost, s));
+      PAT_CUDA(cudaMemcpyAsync(&r2[1], p.r2_dev + (iters - 1), sizeof(double),
+                               cudaMemcpyDeviceToHost, s));
+    }
+    PAT_CUDA(cudaStreamSynchronize(s));
+    *report = pat_fista_report{Lc, r2[0], r2[1], iters, 0};
+  } else if (!is_device_ptr(x)) {
+    PAT_CUDA(cudaStreamSynchronize(s));
+  }
+  return PAT_OK;
+  PAT_GUARD_END
+}
+
+int pat_dot_f64(pat_plan* plan, const void* a, const void* b, int64_t n, double* out,
+                pat_stream stream) {
+  PAT_GUARD_BEGIN
+  if (!plan || !a || !b || !out || n < 0) return fail(PAT_ERR_ARG, "bad dot arguments");
+  if (n > 0 && (!is_device_ptr(a) || !is_device_ptr(b)))
+    return fail(PAT_ERR_ARG, "pat_dot_f64 takes device arrays");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (n == 0) {
+    *out = 0.0;
+    return PAT_OK;
+  }
+  PAT_CUDA(launch_dot(plan->p, a, b, n, plan->x.res, s));
+  PAT_CUDA(cudaMemcpyAsync(out, plan->x.res, sizeof(double), cudaMemcpyDeviceToHost, s));
+  PAT_CUDA(cudaStreamSynchronize(s));
+  return PAT_OK;
+  PAT_GUARD_END
+}
+
+int pat_stage_spectrum(pat_plan* plan, const void* in, void* out, int slices, pat_stream stream) {
+  PAT_GUARD_BEGIN
+  if (!plan || !in || !out) return fail(PAT_ERR_ARG, "bad arguments");
+  const Layout& L = plan->p.L;
+  if (slices < 0 || slices > L.max_batch * std::max(L.nz, L.nt))
+    return fail(PAT_ERR_ARG, "slices must be in [0, max_batch * max(nz, nt)]");
+  PAT_CUDA(launch_spectrum(plan->p, in, (int64_t)L.ny * L.nx, L.nx, L.ny, out, L.K, slices,
+                           (cudaStream_t)stream));
+  return PAT_OK;
+  PAT_GUARD_END
+}
+
+int pat_stage_image(pat_plan* plan, const void* in, void* out, int slices, pat_stream stream) {
+  PAT_GUARD_BEGIN
+  if (!plan || !in || !out) return fail(PAT_ERR_ARG, "bad arguments");
+  const Layout& L = plan->p.L;
+  if (slices < 0 || slices > L.max_batch * std::max(L.nz, L.nt))
+    return fail(PAT_ERR_ARG, "slices must be in [0, max_batch * max(nz, nt)]");
+  PAT_CUDA(launch_image(plan->p, in, L.K, out, (int64_t)L.ny * L.nx, slices, nullptr, nullptr,
+                        (cudaStream_t)stream));
+  return PAT_OK;
+  PAT_GUARD_END
+}
+
+}  // extern "C"

@@ -1,0 +1,176 @@
+// Internal declarations shared by the CUDA translation units of libpat.
+// Not part of the public ABI (that is include/pat.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "pat.h"
+
+namespace pat {
+
+// ----------------------------------------------------------------------------
+// Complex numbers in registers / memory: (x = re, y = im), 8 or 16 bytes.
+// ----------------------------------------------------------------------------
+template <typename R>
+struct cx;
+template <>
+struct __align__(8) cx<float> {
+  float x, y;
+};
+template <>
+struct __align__(16) cx<double> {
+  double x, y;
+};
+
+template <typename R>
+__host__ __device__ __forceinline__ cx<R> mk(R a, R b) {
+  cx<R> c;
+  c.x = a;
+  c.y = b;
+  return c;
+}
+template <typename R>
+__host__ __device__ __forceinline__ cx<R> cadd(cx<R> a, cx<R> b) {
+  return mk<R>(a.x + b.x, a.y + b.y);
+}
+template <typename R>
+__host__ __device__ __forceinline__ cx<R> csub(cx<R> a, cx<R> b) {
+  return mk<R>(a.x - b.x, a.y - b.y);
+}
+template <typename R>
+__host__ __device__ __forceinline__ cx<R> cmul(cx<R> a, cx<R> b) {
+  return mk<R>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename R>
+__host__ __device__ __forceinline__ cx<R> conjg(cx<R> a) {
+  return mk<R>(a.x, -a.y);
+}
+
+// 16-byte vector of the table stream.
+template <typename R>
+struct vec16;
+template <>
+struct vec16<float> {
+  typedef float4 type;
+};
+template <>
+struct vec16<double> {
+  typedef double2 type;
+};
+
+// ----------------------------------------------------------------------------
+// Plan: geometry, resident table, workspace.
+// ----------------------------------------------------------------------------
+// Frequency bins: k = kx * py + ky with kx in [0, px/2], ky in [0, py)
+// ("kx-major half spectrum"); K = (px/2 + 1) py, padded to Kpad (multiple of 32).
+// Table: [kb = k / 32][t][zg][lane = k % 32][ZG] elements, 16 bytes per
+// (kb, t, zg, lane) group; ZG = z-planes per group (4 real f32, 2 complex f32
+// or real f64, 1 complex f64).
+struct Layout {
+  int nx, ny, nz, nt, px, py, max_batch;
+  bool fp64, real;
+  int64_t K, Kpad, nkb;
+  int zg, nzg;         // z per 16-byte group, number of groups
+  int tstride;         // ny rounded up to even (row stride of the FFT intermediate)
+  int64_t tslice;      // (px/2 + 1) * tstride
+  size_t rsize;        // sizeof(real_t)
+  size_t table_bytes;  // nkb * nt * nzg * 32 * 16
+};
+
+struct Graph;  // CUDA-graph cache (api.cu)
+
+struct Plan {
+  Layout L;
+  double table_max_abs = 0, table_max_imag = 0;
+  void* table = nullptr;  // device, blocked layout
+  void* twx = nullptr;    // device cx<real_t>[px]: exp(-2 pi i k / px)
+  void* twy = nullptr;    // device cx<real_t>[py]
+  // workspace (device)
+  void* X = nullptr;      // [max_batch][max(nz, nt)][Kpad] complex  (X or Z or D)
+  void* Y = nullptr;      // [max_batch][max(nz, nt)][Kpad] complex  (Y or D or Z)
+  void* T = nullptr;      // [max_batch * max(nz, nt)][tslice] complex
+  void* vol_a = nullptr;  // [max_batch][nz][ny][nx] real: FISTA momentum point y_k
+  void* vol_b = nullptr;  // [max_batch][nz][ny][nx] real: FISTA x_{k-1} / gradient
+  void* vol_c = nullptr;  // [max_batch][nz][ny][nx] real: gradient
+  void* dat_a = nullptr;  // [max_batch][nt][ny][nx] real: residual
+  void* dat_b = nullptr;  // [max_batch][nt][ny][nx] real: measured data copy
+  double* red = nullptr;  // reduction scratch: partials + results (see kReduce*)
+  unsigned int* red_counter = nullptr;
+  double* betas = nullptr;  // FISTA momentum coefficients per iteration
+  int betas_cap = 0;
+  int* iter_dev = nullptr;  // FISTA iteration counter (graph replay)
+  double* r2_dev = nullptr; // FISTA residual norms per iteration
+  int r2_cap = 0;
+  Graph* graphs = nullptr;
+  size_t ws_bytes = 0;
+};
+
+constexpr int kReduceBlocks = 1024;  // max blocks of the FP64 reductions
+// red[0 .. kReduceBlocks) partials, red[kReduceBlocks ..] results
+
+// ----------------------------------------------------------------------------
+// Error plumbing (thread-local message, status codes).
+// ----------------------------------------------------------------------------
+void set_error(const std::string& msg);
+int fail(int code, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+
+#define PAT_CUDA(call)                                   \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return pat::cuda_fail(e_, #call); \
+  } while (0)
+
+// ----------------------------------------------------------------------------
+// Launchers (each returns cudaError_t of the launch).
+// ----------------------------------------------------------------------------
+// FFT stages. `in`/`out` element type follows L.fp64.
+// Stage i: real slices [S][ny][nx] (slice stride in_stride elements, row
+// length nx_in valid of px, ny_in valid rows of py) -> spectra [S][px/2+1][py]
+// with slice stride out_stride complex elements.
+cudaError_t launch_spectrum(const Plan& p, const void* in, int64_t in_stride, int nx_in, int ny_in,
+                            void* out, int64_t out_stride, int S, cudaStream_t s);
+// Stage iii: spectra [S][px/2+1][py] -> real [S][ny][nx] (crop), optionally
+// out = image - sub (sub has out's layout) with sum of squares added to
+// *sumsq (FP64, via the plan's reduction scratch when sumsq != nullptr).
+cudaError_t launch_image(const Plan& p, const void* in, int64_t in_stride, void* out,
+                         int64_t out_stride, int S, const void* sub, double* sumsq,
+                         cudaStream_t s);
+// Contractions over the resident table.
+cudaError_t launch_contract_fwd(const Plan& p, const void* X, void* Y, int batch, cudaStream_t s);
+cudaError_t launch_contract_adj(const Plan& p, const void* D, void* Z, int batch, cudaStream_t s);
+
+// Table construction (table.cu). Both allocate p.table and set the
+// representation (real or complex) of p.L.
+int build_table_from_source(Plan& p, const void* table, pat_table_format fmt, bool force_complex,
+                            cudaStream_t s);
+int build_table_kspace(Plan& p, const pat_medium& m, bool force_complex, cudaStream_t s);
+bool is_device_ptr(const void* p);
+
+// Representation-dependent parts of the layout.
+inline void set_representation(Layout& L, bool real) {
+  L.real = real;
+  const size_t esz = (L.fp64 ? 8 : 4) * (real ? 1 : 2);
+  L.zg = (int)(16 / esz);
+  L.nzg = (L.nz + L.zg - 1) / L.zg;
+  L.table_bytes = (size_t)L.nkb * L.nt * L.nzg * 32 * 16;
+}
+
+// Vector kernels (vec.cu).
+cudaError_t launch_dot(const Plan& p, const void* a, const void* b, int64_t n, double* out_dev,
+                       cudaStream_t s);
+// Sums n per-block partials (in order, FP64) into *out (device).
+cudaError_t launch_partials_sum(const double* partials, int n, double* out, cudaStream_t s);
+// FISTA step; scal = {1/L, lambda/L}, beta_k = betas[*iter] (device memory).
+cudaError_t launch_fista_update(const Plan& p, void* y, void* xprev, const void* grad, int64_t n,
+                                const double* scal, const double* betas, const int* iter,
+                                cudaStream_t s);
+cudaError_t launch_scale_by_inv_norm(const Plan& p, const void* in, void* out, int64_t n,
+                                     const double* sumsq_dev, cudaStream_t s);
+cudaError_t launch_tick(int* counter, cudaStream_t s);
+cudaError_t launch_fill_zero(void* ptr, size_t bytes, cudaStream_t s);
+
+}  // namespace pat

@@ -1,0 +1,402 @@
+// Plan-time construction of the resident spectral table (Sec. 3.2: the
+// depth-indexed impulse-response library, stored once, applied every call).
+//
+// Sources:
+//   spatial h[nz][nt][py][px]        -> 2D real FFT per (z, t) on the device
+//   spectral Hh[nz][nt][py][px/2+1]  -> transposed to kx-major
+//   k-space medium                   -> generated here from the exact periodic
+//                                       solution of Eq. 1-2 (one point source,
+//                                       recorded on the depth planes)
+// Every value is scaled by 1/(px py) (the inverse FFT normalisation) and
+// scattered into the blocked layout [k/32][t][z-group][lane][z in group].
+// Pass 1 over a transformed source measures max |Hh| and max |Im Hh|; the
+// real layout is chosen when Im is negligible (even kernels), pass 2 fills it.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "pat_internal.h"
+
+namespace pat {
+namespace {
+
+// Table element store: real tables keep only the real part.
+template <typename RT, bool CPLX>
+struct Store;
+template <typename RT>
+struct Store<RT, false> {
+  __device__ static void put(void* table, int64_t idx, double re, double) {
+    static_cast<RT*>(table)[idx] = (RT)re;
+  }
+};
+template <typename RT>
+struct Store<RT, true> {
+  __device__ static void put(void* table, int64_t idx, double re, double im) {
+    cx<RT> v;
+    v.x = (RT)re;
+    v.y = (RT)im;
+    static_cast<cx<RT>*>(table)[idx] = v;
+  }
+};
+
+__device__ __forceinline__ int64_t table_index(int64_t k, int t, int z, int nt, int nzg, int ZG) {
+  const int64_t kb = k >> 5;
+  const int lane = (int)(k & 31);
+  const int zg = z / ZG, q = z % ZG;
+  return (((kb * nt + t) * nzg + zg) * 32 + lane) * ZG + q;
+}
+
+// src: complex (RS) values for nt_chunk time samples of one depth plane z.
+// rowmajor = 0: src[t][kx * py + ky] with slice stride sstride (FFT output)
+// rowmajor = 1: src[t][ky][kx] with kx in [0, px/2] (R2C layout)
+template <typename RS, typename RT, bool CPLX>
+__global__ void k_scatter(const cx<RS>* __restrict__ src, int64_t sstride, int rowmajor, int px,
+                          int py, int z, int t0, int nt_chunk, int nt, int nzg, int ZG,
+                          double scale, void* table) {
+  const int64_t K = (int64_t)(px / 2 + 1) * py;
+  const int64_t n = K * nt_chunk;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int tt = (int)(i / K);
+    const int64_t k = i % K;
+    const int kx = (int)(k / py), ky = (int)(k % py);
+    const cx<RS> v = rowmajor ? src[tt * sstride + (int64_t)ky * (px / 2 + 1) + kx]
+                              : src[tt * sstride + k];
+    Store<RT, CPLX>::put(table, table_index(k, t0 + tt, z, nt, nzg, ZG), (double)v.x * scale,
+                         (double)v.y * scale);
+  }
+}
+
+// max |v|^2 and max |Im v| over the same source indexing, as ordered bit
+// patterns of non-negative doubles (atomicMax on the integer image).
+template <typename RS>
+__global__ void k_stats(const cx<RS>* __restrict__ src, int64_t sstride, int rowmajor, int px,
+                        int py, int nt_chunk, unsigned long long* out) {
+  const int64_t K = (int64_t)(px / 2 + 1) * py;
+  const int64_t n = K * nt_chunk;
+  double m2 = 0.0, mi = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int tt = (int)(i / K);
+    const int64_t k = i % K;
+    const int kx = (int)(k / py), ky = (int)(k % py);
+    const cx<RS> v = rowmajor ? src[tt * sstride + (int64_t)ky * (px / 2 + 1) + kx]
+                              : src[tt * sstride + k];
+    const double re = v.x, im = v.y;
+    m2 = fmax(m2, re * re + im * im);
+    mi = fmax(mi, fabs(im));
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    m2 = fmax(m2, __shfl_xor_sync(0xffffffffu, m2, o));
+    mi = fmax(mi, __shfl_xor_sync(0xffffffffu, mi, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(&out[0], (unsigned long long)__double_as_longlong(m2));
+    atomicMax(&out[1], (unsigned long long)__double_as_longlong(mi));
+  }
+}
+
+// ---- k-space library generator ---------------------------------------------
+// One CTA per 32 bins (one per lane, the table's block). For each time sample
+// t the CTA evaluates c_m = cos(c t dt |k_m|) for m in [0, mz/2] (|k_m| only
+// depends on |kz|, so m and mz - m coincide), with the phase t * u_m (turns)
+// taken modulo 1 in 64-bit fixed point so large arguments keep full accuracy,
+// then contracts over m with W[m][j] = w_m cos(2 pi m (z0 + j) / mz) / (mz px py)
+// (w_m = 1 at m = 0 and mz/2, else 2) from shared memory.
+__global__ void k_kspace(int px, int py, int mz, int nz, int nt, int nzg, int ZG, int cplx,
+                         const unsigned long long* __restrict__ u_fix,  // [K][mz/2+1] phase/sample
+                         const float* __restrict__ W,                   // [mz/2+1][nz]
+                         void* table, int64_t K) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int M = mz / 2 + 1;
+  float* ws = reinterpret_cast<float*>(smem_raw);  // [M][nz]
+  float* cs = ws + (size_t)M * nz;                  // [M][32]
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  const int64_t k = (int64_t)blockIdx.x * 32 + lane;
+  for (int i = threadIdx.x; i < M * nz; i += blockDim.x) ws[i] = W[i];
+  for (int t = 0; t < nt; ++t) {
+    __syncthreads();
+    for (int m = warp; m < M; m += nwarp) {
+      float c = 0.f;
+      if (k < K) {
+        const unsigned long long ph = (unsigned long long)t * u_fix[k * M + m];  // mod 2^64
+        const float turns = (float)(ph >> 40) * (1.0f / 16777216.0f);          // [0, 1)
+        c = cospif(2.0f * turns);
+      }
+      cs[m * 32 + lane] = c;
+    }
+    __syncthreads();
+    for (int j = warp; j < nz; j += nwarp) {
+      float acc = 0.f;
+      for (int m = 0; m < M; ++m) acc = fmaf(cs[m * 32 + lane], ws[m * nz + j], acc);
+      if (k < K) {
+        const int64_t idx = table_index(k, t, j, nt, nzg, ZG);
+        if (cplx) {
+          cx<float> v;
+          v.x = acc;
+          v.y = 0.f;
+          static_cast<cx<float>*>(table)[idx] = v;
+        } else {
+          static_cast<float*>(table)[idx] = acc;
+        }
+      }
+    }
+  }
+}
+
+int grid_for(int64_t n) {
+  int64_t b = (n + 255) / 256;
+  if (b > 152 * 32) b = 152 * 32;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+template <typename RT, bool CPLX>
+cudaError_t scatter_launch(const void* src, bool src64, int64_t sstride, int rowmajor,
+                           const Layout& L, int z, int t0, int ntc, double scale, void* table,
+                           cudaStream_t s) {
+  const int64_t n = L.K * ntc;
+  if (src64)
+    k_scatter<double, RT, CPLX><<<grid_for(n), 256, 0, s>>>(
+        static_cast<const cx<double>*>(src), sstride, rowmajor, L.px, L.py, z, t0, ntc, L.nt,
+        L.nzg, L.zg, scale, table);
+  else
+    k_scatter<float, RT, CPLX><<<grid_for(n), 256, 0, s>>>(
+        static_cast<const cx<float>*>(src), sstride, rowmajor, L.px, L.py, z, t0, ntc, L.nt,
+        L.nzg, L.zg, scale, table);
+  return cudaGetLastError();
+}
+
+cudaError_t scatter_any(const void* src, bool src64, int64_t sstride, int rowmajor, const Layout& L,
+                        int z, int t0, int ntc, double scale, void* table, cudaStream_t s) {
+  if (L.fp64)
+    return L.real ? scatter_launch<double, false>(src, src64, sstride, rowmajor, L, z, t0, ntc, scale, table, s)
+                  : scatter_launch<double, true>(src, src64, sstride, rowmajor, L, z, t0, ntc, scale, table, s);
+  return L.real ? scatter_launch<float, false>(src, src64, sstride, rowmajor, L, z, t0, ntc, scale, table, s)
+                : scatter_launch<float, true>(src, src64, sstride, rowmajor, L, z, t0, ntc, scale, table, s);
+}
+
+std::vector<double> twiddles(int n) {
+  std::vector<double> w(2 * (size_t)n);
+  const double pi = 3.14159265358979323846;
+  for (int k = 0; k < n; ++k) {
+    w[2 * k] = std::cos(-2.0 * pi * k / n);
+    w[2 * k + 1] = std::sin(-2.0 * pi * k / n);
+  }
+  return w;
+}
+
+}  // namespace
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int build_table_from_source(Plan& p, const void* table, pat_table_format fmt, bool force_complex,
+                            cudaStream_t s) {
+  Layout& L = p.L;
+  const bool spatial = fmt == PAT_TABLE_SPATIAL_F64 || fmt == PAT_TABLE_SPATIAL_F32;
+  const bool src64 = fmt == PAT_TABLE_SPATIAL_F64 || fmt == PAT_TABLE_SPECTRAL_C128;
+  const bool on_dev = is_device_ptr(table);
+  const int64_t plane_src = spatial ? (int64_t)L.px * L.py : (int64_t)L.py * (L.px / 2 + 1);
+  const size_t esz_src = spatial ? (src64 ? 8 : 4) : (src64 ? 16 : 8);
+  const size_t csz = src64 ? 16 : 8;  // complex size of the transform precision
+  const int64_t Kfull = (int64_t)(L.px / 2 + 1) * L.py;
+
+  // Time samples per chunk: source staging plus transform buffers stay
+  // below ~1 GiB.
+  const size_t per_t = plane_src * esz_src + (spatial ? (size_t)Kfull * csz * 2 : 0);
+  const int ntc = (int)std::min<int64_t>(L.nt, std::max<int64_t>(1, (1ll << 30) / (int64_t)per_t));
+
+  void *stage = nullptr, *spec = nullptr, *Tprep = nullptr, *twx = nullptr, *twy = nullptr;
+  unsigned long long* stats = nullptr;
+  auto cleanup = [&]() {
+    cudaFree(stage);
+    cudaFree(spec);
+    cudaFree(Tprep);
+    cudaFree(twx);
+    cudaFree(twy);
+    cudaFree(stats);
+  };
+#define PREP_CUDA(call)               \
+  do {                                \
+    cudaError_t e_ = (call);          \
+    if (e_ != cudaSuccess) {          \
+      int rc_ = cuda_fail(e_, #call); \
+      cleanup();                      \
+      return rc_;                     \
+    }                                 \
+  } while (0)
+
+  if (!on_dev) PREP_CUDA(cudaMalloc(&stage, (size_t)ntc * plane_src * esz_src));
+  PREP_CUDA(cudaMalloc(&stats, 2 * sizeof(unsigned long long)));
+  PREP_CUDA(cudaMemsetAsync(stats, 0, 2 * sizeof(unsigned long long), s));
+
+  // A transform-only view of the plan in the source precision: the same
+  // grid with its own twiddles and intermediate buffer (all py rows).
+  Plan prep;
+  prep.L = L;
+  prep.L.fp64 = src64;
+  if (spatial) {
+    PREP_CUDA(cudaMalloc(&spec, (size_t)ntc * Kfull * csz));
+    PREP_CUDA(cudaMalloc(&Tprep, (size_t)ntc * (L.px / 2 + 1) * L.py * csz));
+    std::vector<double> wx = twiddles(L.px), wy = twiddles(L.py);
+    if (src64) {
+      PREP_CUDA(cudaMalloc(&twx, wx.size() * 8));
+      PREP_CUDA(cudaMalloc(&twy, wy.size() * 8));
+      PREP_CUDA(cudaMemcpy(twx, wx.data(), wx.size() * 8, cudaMemcpyHostToDevice));
+      PREP_CUDA(cudaMemcpy(twy, wy.data(), wy.size() * 8, cudaMemcpyHostToDevice));
+    } else {
+      std::vector<float> fx(wx.begin(), wx.end()), fy(wy.begin(), wy.end());
+      PREP_CUDA(cudaMalloc(&twx, fx.size() * 4));
+      PREP_CUDA(cudaMalloc(&twy, fy.size() * 4));
+      PREP_CUDA(cudaMemcpy(twx, fx.data(), fx.size() * 4, cudaMemcpyHostToDevice));
+      PREP_CUDA(cudaMemcpy(twy, fy.data(), fy.size() * 4, cudaMemcpyHostToDevice));
+    }
+    prep.T = Tprep;
+    prep.twx = twx;
+    prep.twy = twy;
+  }
+
+  // Spectra of depth z, samples [t0, t0 + n): pointer, slice stride, layout.
+  auto transform = [&](int z, int t0, int n, const void** out, int64_t* out_stride,
+                       int* rowmajor) -> cudaError_t {
+    const char* base = static_cast<const char*>(table) +
+                       ((int64_t)z * L.nt + t0) * plane_src * (int64_t)esz_src;
+    const void* src = base;
+    if (!on_dev) {
+      cudaError_t e = cudaMemcpyAsync(stage, base, (size_t)n * plane_src * esz_src,
+                                      cudaMemcpyHostToDevice, s);
+      if (e != cudaSuccess) return e;
+      src = stage;
+    }
+    if (!spatial) {
+      *out = src;
+      *out_stride = plane_src;
+      *rowmajor = 1;
+      return cudaSuccess;
+    }
+    *out = spec;
+    *out_stride = Kfull;
+    *rowmajor = 0;
+    return launch_spectrum(prep, src, (int64_t)L.px * L.py, L.px, L.py, spec, Kfull, n, s);
+  };
+
+  // Pass 1: statistics of the whole library.
+  for (int z = 0; z < L.nz; ++z)
+    for (int t0 = 0; t0 < L.nt; t0 += ntc) {
+      const int n = std::min(ntc, L.nt - t0);
+      const void* src;
+      int64_t sstride;
+      int rowmajor;
+      PREP_CUDA(transform(z, t0, n, &src, &sstride, &rowmajor));
+      if (src64)
+        k_stats<double><<<grid_for(Kfull * n), 256, 0, s>>>(
+            static_cast<const cx<double>*>(src), sstride, rowmajor, L.px, L.py, n, stats);
+      else
+        k_stats<float><<<grid_for(Kfull * n), 256, 0, s>>>(
+            static_cast<const cx<float>*>(src), sstride, rowmajor, L.px, L.py, n, stats);
+      PREP_CUDA(cudaGetLastError());
+    }
+  unsigned long long hs[2];
+  PREP_CUDA(cudaMemcpyAsync(hs, stats, sizeof(hs), cudaMemcpyDeviceToHost, s));
+  PREP_CUDA(cudaStreamSynchronize(s));
+  double m2, mi;
+  memcpy(&m2, &hs[0], 8);
+  memcpy(&mi, &hs[1], 8);
+  p.table_max_abs = std::sqrt(m2);
+  p.table_max_imag = mi;
+  set_representation(L, !force_complex && mi <= 1e-6 * p.table_max_abs);
+
+  // Pass 2: fill the resident table.
+  PREP_CUDA(cudaMalloc(&p.table, L.table_bytes));
+  PREP_CUDA(cudaMemsetAsync(p.table, 0, L.table_bytes, s));
+  const double scale = 1.0 / ((double)L.px * (double)L.py);
+  for (int z = 0; z < L.nz; ++z)
+    for (int t0 = 0; t0 < L.nt; t0 += ntc) {
+      const int n = std::min(ntc, L.nt - t0);
+      const void* src;
+      int64_t sstride;
+      int rowmajor;
+      PREP_CUDA(transform(z, t0, n, &src, &sstride, &rowmajor));
+      PREP_CUDA(scatter_any(src, src64, sstride, rowmajor, L, z, t0, n, scale, p.table, s));
+    }
+  PREP_CUDA(cudaStreamSynchronize(s));
+  cleanup();
+  return PAT_OK;
+#undef PREP_CUDA
+}
+
+int build_table_kspace(Plan& p, const pat_medium& m, bool force_complex, cudaStream_t s) {
+  Layout& L = p.L;
+  if (L.fp64) return fail(PAT_ERR_UNSUPPORTED, "k-space generation builds single-precision tables");
+  set_representation(L, !force_complex);
+  const int M = m.mz / 2 + 1;
+  const double pi = 3.14159265358979323846;
+  // u_m(k) = c dt |k_m| / (2 pi) turns per sample, as 64-bit fixed-point fractions.
+  std::vector<unsigned long long> u((size_t)L.K * M);
+  for (int64_t k = 0; k < L.K; ++k) {
+    const int kx = (int)(k / L.py), kyi = (int)(k % L.py);
+    const int ky = kyi < L.py / 2 ? kyi : kyi - L.py;
+    const double wx = 2.0 * pi * kx / (L.px * m.dx), wy = 2.0 * pi * ky / (L.py * m.dy);
+    for (int mm = 0; mm < M; ++mm) {
+      const double wz = 2.0 * pi * mm / (m.mz * m.dz);
+      const double turns = m.c * m.dt * std::sqrt(wx * wx + wy * wy + wz * wz) / (2.0 * pi);
+      const double frac = turns - std::floor(turns);
+      u[(size_t)k * M + mm] = (unsigned long long)std::ldexp(frac, 64);
+    }
+  }
+  std::vector<float> W((size_t)M * L.nz);
+  const double scale = 1.0 / ((double)m.mz * L.px * L.py);
+  for (int mm = 0; mm < M; ++mm)
+    for (int j = 0; j < L.nz; ++j) {
+      const double wgt = (mm == 0 || mm == m.mz / 2) ? 1.0 : 2.0;
+      const long q = ((long)mm * (m.z0 + j)) % m.mz;
+      W[(size_t)mm * L.nz + j] = (float)(wgt * std::cos(2.0 * pi * q / m.mz) * scale);
+    }
+  unsigned long long* u_d = nullptr;
+  float* W_d = nullptr;
+  auto cleanup = [&]() {
+    cudaFree(u_d);
+    cudaFree(W_d);
+  };
+#define GEN_CUDA(call)                \
+  do {                                \
+    cudaError_t e_ = (call);          \
+    if (e_ != cudaSuccess) {          \
+      int rc_ = cuda_fail(e_, #call); \
+      cleanup();                      \
+      return rc_;                     \
+    }                                 \
+  } while (0)
+  GEN_CUDA(cudaMalloc(&u_d, u.size() * sizeof(unsigned long long)));
+  GEN_CUDA(cudaMalloc(&W_d, W.size() * sizeof(float)));
+  GEN_CUDA(cudaMemcpy(u_d, u.data(), u.size() * sizeof(unsigned long long), cudaMemcpyHostToDevice));
+  GEN_CUDA(cudaMemcpy(W_d, W.data(), W.size() * sizeof(float), cudaMemcpyHostToDevice));
+  GEN_CUDA(cudaMalloc(&p.table, L.table_bytes));
+  GEN_CUDA(cudaMemsetAsync(p.table, 0, L.table_bytes, s));
+  const size_t smem = sizeof(float) * ((size_t)M * L.nz + (size_t)M * 32);
+  if (smem > 227 * 1024) {
+    cleanup();
+    return fail(PAT_ERR_UNSUPPORTED, "k-space generator: (mz/2 + 1) * (nz + 32) floats exceed shared memory");
+  }
+  GEN_CUDA(cudaFuncSetAttribute((const void*)k_kspace, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem));
+  k_kspace<<<(unsigned)L.nkb, 256, smem, s>>>(L.px, L.py, m.mz, L.nz, L.nt, L.nzg, L.zg,
+                                              L.real ? 0 : 1, u_d, W_d, p.table, L.K);
+  GEN_CUDA(cudaGetLastError());
+  GEN_CUDA(cudaStreamSynchronize(s));
+  cleanup();
+  p.table_max_abs = 0;
+  p.table_max_imag = 0;
+  return PAT_OK;
+#undef GEN_CUDA
+}
+
+}  // namespace pat

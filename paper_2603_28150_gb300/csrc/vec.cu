@@ -1,0 +1,143 @@
+// Vector kernels around the operator: FP64 inner products and norms (the
+// adjoint test of Eq. 9, FISTA residuals, the power iteration for ||H*H||),
+// the FISTA proximal/momentum update (Eq. 14-15), and small helpers.
+// Reductions are deterministic: fixed grid, per-block tree sums, then one
+// block sums the partials in index order.
+#include "pat_internal.h"
+
+namespace pat {
+namespace {
+
+constexpr int kBlock = 256;
+
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double ws[32];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = (blockDim.x + 31) >> 5;
+  __syncthreads();
+  if (l == 0) ws[w] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (w == 0) {
+    r = l < nw ? ws[l] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+  }
+  return r;  // valid in thread 0
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kBlock) k_dot(const R* __restrict__ a, const R* __restrict__ b,
+                                                int64_t n, double* __restrict__ partials) {
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)kBlock + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * kBlock)
+    acc = fma((double)a[i], (double)b[i], acc);
+  const double s = block_sum(acc);
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(1024) k_sum_partials(const double* __restrict__ partials, int n,
+                                                       double* __restrict__ out) {
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < n; i += 1024) acc += partials[i];
+  const double s = block_sum(acc);
+  if (threadIdx.x == 0) *out = s;
+}
+
+// x_k = max(y - g/L - lambda/L, 0) (prox of Eq. 14 after the gradient step of
+// Eq. 15); y <- x_k + beta_k (x_k - x_{k-1}); xprev <- x_k. The scalars 1/L,
+// lambda/L (scal) and beta_k = betas[*iter] are read from device memory so one
+// captured graph serves every iteration.
+template <typename R>
+__global__ void __launch_bounds__(kBlock) k_fista_update(R* __restrict__ y, R* __restrict__ xprev,
+                                                         const R* __restrict__ grad, int64_t n,
+                                                         const double* __restrict__ scal,
+                                                         const double* __restrict__ betas,
+                                                         const int* __restrict__ iter) {
+  const R invL = (R)scal[0], lamL = (R)scal[1];
+  const R beta = (R)betas[*iter];
+  for (int64_t i = blockIdx.x * (int64_t)kBlock + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * kBlock) {
+    const R yv = y[i], g = grad[i], xp = xprev[i];
+    R x = yv - g * invL - lamL;
+    x = x > (R)0 ? x : (R)0;
+    y[i] = x + beta * (x - xp);
+    xprev[i] = x;
+  }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kBlock) k_scale(const R* __restrict__ in, R* __restrict__ out,
+                                                  int64_t n, const double* __restrict__ sumsq) {
+  const R s = (R)(1.0 / sqrt(*sumsq));
+  for (int64_t i = blockIdx.x * (int64_t)kBlock + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * kBlock)
+    out[i] = in[i] * s;
+}
+
+__global__ void k_tick(int* c) { *c += 1; }
+
+int grid_for(int64_t n, int cap) {
+  int64_t b = (n + kBlock - 1) / kBlock;
+  if (b > cap) b = cap;
+  return b < 1 ? 1 : (int)b;
+}
+
+}  // namespace
+
+cudaError_t launch_partials_sum(const double* partials, int n, double* out, cudaStream_t s) {
+  k_sum_partials<<<1, 1024, 0, s>>>(partials, n, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dot(const Plan& p, const void* a, const void* b, int64_t n, double* out_dev,
+                       cudaStream_t s) {
+  const int g = grid_for(n, kReduceBlocks);
+  if (p.L.fp64)
+    k_dot<double><<<g, kBlock, 0, s>>>(static_cast<const double*>(a), static_cast<const double*>(b),
+                                        n, p.red);
+  else
+    k_dot<float><<<g, kBlock, 0, s>>>(static_cast<const float*>(a), static_cast<const float*>(b), n,
+                                       p.red);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_partials_sum(p.red, g, out_dev, s);
+}
+
+cudaError_t launch_fista_update(const Plan& p, void* y, void* xprev, const void* grad, int64_t n,
+                                const double* scal, const double* betas, const int* iter,
+                                cudaStream_t s) {
+  const int g = grid_for(n, 152 * 16);
+  if (p.L.fp64)
+    k_fista_update<double><<<g, kBlock, 0, s>>>(static_cast<double*>(y), static_cast<double*>(xprev),
+                                                 static_cast<const double*>(grad), n, scal, betas,
+                                                 iter);
+  else
+    k_fista_update<float><<<g, kBlock, 0, s>>>(static_cast<float*>(y), static_cast<float*>(xprev),
+                                                static_cast<const float*>(grad), n, scal, betas,
+                                                iter);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale_by_inv_norm(const Plan& p, const void* in, void* out, int64_t n,
+                                     const double* sumsq_dev, cudaStream_t s) {
+  const int g = grid_for(n, 152 * 16);
+  if (p.L.fp64)
+    k_scale<double><<<g, kBlock, 0, s>>>(static_cast<const double*>(in), static_cast<double*>(out),
+                                          n, sumsq_dev);
+  else
+    k_scale<float><<<g, kBlock, 0, s>>>(static_cast<const float*>(in), static_cast<float*>(out), n,
+                                         sumsq_dev);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tick(int* counter, cudaStream_t s) {
+  k_tick<<<1, 1, 0, s>>>(counter);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fill_zero(void* ptr, size_t bytes, cudaStream_t s) {
+  return cudaMemsetAsync(ptr, 0, bytes, s);
+}
+
+}  // namespace pat

@@ -1,0 +1,382 @@
+"""Python binding of libpat (include/pat.h): argument marshalling only.
+
+Every computation runs in the CUDA kernels of libpat.so; this module passes
+pointers, sizes and the current torch CUDA stream through ctypes. There is no
+CPU fallback: if the library or a GPU is missing, the calls raise.
+
+Arrays are torch tensors: CUDA tensors are used in place (asynchronous on the
+current stream); CPU tensors / numpy arrays are host buffers that the library
+stages through the device (synchronous). Shapes, x fastest:
+  object rho [batch][nz][ny][nx] (or [nz][ny][nx]); data d [batch][nt][ny][nx].
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+PAT_OK = 0
+PAT_ERR_ARG = -1
+PAT_ERR_OOM = -2
+PAT_ERR_CUDA = -3
+PAT_ERR_TIMEOUT = -4
+PAT_ERR_UNSUPPORTED = -5
+
+FLAG_FP64 = 1
+FLAG_FORCE_COMPLEX = 2
+
+TABLE_SPATIAL_F64 = 0
+TABLE_SPATIAL_F32 = 1
+TABLE_SPECTRAL_C128 = 2
+TABLE_SPECTRAL_C64 = 3
+
+# Every symbol include/pat.h declares.
+EXPORTS = (
+    "pat_plan_create", "pat_plan_create_kspace", "pat_plan_destroy", "pat_plan_info",
+    "pat_last_error", "pat_forward", "pat_adjoint", "pat_gradient", "pat_power_norm",
+    "pat_fista_solve", "pat_dot_f64", "pat_stage_spectrum", "pat_stage_image",
+)
+
+
+class PatError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"libpat error {code}: {msg}")
+        self.code = code
+
+
+class Geometry(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+                ("nt", ctypes.c_int32), ("px", ctypes.c_int32), ("py", ctypes.c_int32),
+                ("max_batch", ctypes.c_int32), ("flags", ctypes.c_int32)]
+
+
+class MediumC(ctypes.Structure):
+    _fields_ = [("c", ctypes.c_double), ("dx", ctypes.c_double), ("dy", ctypes.c_double),
+                ("dz", ctypes.c_double), ("dt", ctypes.c_double), ("mz", ctypes.c_int32),
+                ("z0", ctypes.c_int32)]
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("real_table", ctypes.c_int32), ("fp64", ctypes.c_int32),
+                ("bins", ctypes.c_int64), ("table_bytes", ctypes.c_int64),
+                ("workspace_bytes", ctypes.c_int64), ("table_max_abs", ctypes.c_double),
+                ("table_max_imag", ctypes.c_double)]
+
+
+class FistaParams(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("power_iters", ctypes.c_int32),
+                ("warm_start", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("lam", ctypes.c_double), ("L", ctypes.c_double)]
+
+
+class FistaReport(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_double), ("resid2_first", ctypes.c_double),
+                ("resid2_last", ctypes.c_double), ("iters", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def lib(build_if_missing: bool = True):
+    """Loads libpat.so (building it in-tree first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing and not _build.up_to_date():
+        _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"libpat.so not found at {path}; run paper_2603_28150_gb300/build.py")
+    L = ctypes.CDLL(path)
+    P, I, V, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)
+    sig = {
+        "pat_plan_create": ([ctypes.POINTER(Geometry), V, I, P, ctypes.POINTER(P)], I),
+        "pat_plan_create_kspace": ([ctypes.POINTER(Geometry), ctypes.POINTER(MediumC), P,
+                                    ctypes.POINTER(P)], I),
+        "pat_plan_destroy": ([P], I),
+        "pat_plan_info": ([P, ctypes.POINTER(PlanInfo)], I),
+        "pat_last_error": ([], ctypes.c_char_p),
+        "pat_forward": ([P, V, V, I, P], I),
+        "pat_adjoint": ([P, V, V, I, P], I),
+        "pat_gradient": ([P, V, V, V, I, D, P], I),
+        "pat_power_norm": ([P, V, I, D, P], I),
+        "pat_fista_solve": ([P, V, V, I, ctypes.POINTER(FistaParams), ctypes.POINTER(FistaReport),
+                             P], I),
+        "pat_dot_f64": ([P, V, V, ctypes.c_int64, D, P], I),
+        "pat_stage_spectrum": ([P, V, V, I, P], I),
+        "pat_stage_image": ([P, V, V, I, P], I),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = L
+    return L
+
+
+def _check(rc: int) -> None:
+    if rc != PAT_OK:
+        raise PatError(rc, lib().pat_last_error().decode())
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream(stream=None) -> int:
+    torch = _torch()
+    if stream is not None:
+        return int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
+    if torch.cuda.is_available():
+        return int(torch.cuda.current_stream().cuda_stream)
+    return 0
+
+
+def _ptr(a) -> int:
+    """Data pointer of a contiguous torch tensor or numpy array."""
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"], "numpy array must be C-contiguous"
+        return a.ctypes.data
+    assert a.is_contiguous(), "tensor must be contiguous"
+    return a.data_ptr()
+
+
+@dataclass(frozen=True)
+class Medium:
+    """Homogeneous medium of a device-generated k-space library (see pat_medium)."""
+    c: float = 1500.0
+    dx: float = 100e-6
+    dy: float = 100e-6
+    dz: float = 100e-6
+    dt: float = 20e-9
+    mz: int = 64
+    z0: int = 1
+
+    def c_struct(self) -> MediumC:
+        return MediumC(self.c, self.dx, self.dy, self.dz, self.dt, self.mz, self.z0)
+
+
+class Plan:
+    """A resident operator: grid + impulse-response library on the device.
+
+    Build from a table (`table` = spatial h[nz][nt][py][px] real or spectral
+    Hh[nz][nt][py][px//2+1] complex; numpy / torch, host or device) or from a
+    `medium` (library generated on the device from the k-space solution)."""
+
+    def __init__(self, nx: int, ny: int, nz: int, nt: int, px: int | None = None,
+                 py: int | None = None, max_batch: int = 1, fp64: bool = False,
+                 force_complex: bool = False, table=None, medium: Medium | None = None,
+                 stream=None):
+        L = lib()
+        self.nx, self.ny, self.nz, self.nt = nx, ny, nz, nt
+        self.px = px if px is not None else _pow2_at_least(2 * nx)
+        self.py = py if py is not None else _pow2_at_least(2 * ny)
+        self.max_batch = max_batch
+        self.fp64 = fp64
+        flags = (FLAG_FP64 if fp64 else 0) | (FLAG_FORCE_COMPLEX if force_complex else 0)
+        self._geom = Geometry(nx, ny, nz, nt, self.px, self.py, max_batch, flags)
+        self._h = ctypes.c_void_p(0)
+        s = _stream(stream)
+        if (table is None) == (medium is None):
+            raise ValueError("give exactly one of table= or medium=")
+        if medium is not None:
+            _check(L.pat_plan_create_kspace(ctypes.byref(self._geom), ctypes.byref(medium.c_struct()),
+                                            s, ctypes.byref(self._h)))
+        else:
+            fmt, keep = _table_format(table, self)
+            _check(L.pat_plan_create(ctypes.byref(self._geom), _ptr(keep), fmt, s,
+                                     ctypes.byref(self._h)))
+        self.dtype_name = "float64" if fp64 else "float32"
+
+    # ------------------------------------------------------------------ helpers
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self) -> dict:
+        inf = PlanInfo()
+        _check(lib().pat_plan_info(self._h, ctypes.byref(inf)))
+        return {k: getattr(inf, k) for k, _ in PlanInfo._fields_}
+
+    def close(self) -> None:
+        if self._h and self._h.value:
+            lib().pat_plan_destroy(self._h)
+            self._h = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _torch_dtype(self):
+        torch = _torch()
+        return torch.float64 if self.fp64 else torch.float32
+
+    def obj_shape(self, batch: int = 1):
+        return (batch, self.nz, self.ny, self.nx)
+
+    def data_shape(self, batch: int = 1):
+        return (batch, self.nt, self.ny, self.nx)
+
+    def _batch_of(self, a, per) -> int:
+        n = int(np.prod(a.shape))
+        if n % per:
+            raise ValueError(f"array of {n} elements is not a whole number of {per}-element volumes")
+        return n // per
+
+    def _empty_like_device(self, shape, like):
+        torch = _torch()
+        dev = like.device if hasattr(like, "device") and like.device.type == "cuda" else "cpu"
+        return torch.empty(shape, dtype=self._torch_dtype(), device=dev)
+
+    def _check_dtype(self, *arrs):
+        want = np.float64 if self.fp64 else np.float32
+        for a in arrs:
+            dt = a.dtype if isinstance(a, np.ndarray) else _np_dtype(a.dtype)
+            if dt != want:
+                raise TypeError(f"plan works in {self.dtype_name}; got {dt}")
+
+    # ------------------------------------------------------------------ operators
+    def forward(self, rho, out=None, stream=None):
+        """d = H rho (Eq. 7-8)."""
+        self._check_dtype(rho)
+        b = self._batch_of(rho, self.nz * self.ny * self.nx)
+        if out is None:
+            out = self._empty_like_device(self.data_shape(b) if rho.ndim == 4 else
+                                          self.data_shape(1)[1:], rho)
+        _check(lib().pat_forward(self._h, _ptr(rho), _ptr(out), b, _stream(stream)))
+        return out
+
+    def adjoint(self, d, out=None, stream=None):
+        """rho = H* d (Eq. 11)."""
+        self._check_dtype(d)
+        b = self._batch_of(d, self.nt * self.ny * self.nx)
+        if out is None:
+            out = self._empty_like_device(self.obj_shape(b) if d.ndim == 4 else
+                                          self.obj_shape(1)[1:], d)
+        _check(lib().pat_adjoint(self._h, _ptr(d), _ptr(out), b, _stream(stream)))
+        return out
+
+    def gradient(self, x, y, out=None, resid: bool = True, stream=None):
+        """grad = H*(H x - y) (Eq. 15); returns (grad, ||H x - y||^2 or None)."""
+        self._check_dtype(x, y)
+        b = self._batch_of(x, self.nz * self.ny * self.nx)
+        if out is None:
+            out = self._empty_like_device(tuple(x.shape), x)
+        r2 = ctypes.c_double(0.0)
+        _check(lib().pat_gradient(self._h, _ptr(x), _ptr(y), _ptr(out), b,
+                                  ctypes.byref(r2) if resid else None, _stream(stream)))
+        return out, (r2.value if resid else None)
+
+    def power_norm(self, v0, iters: int, stream=None) -> float:
+        """L = ||H*H|| by power iteration from v0."""
+        self._check_dtype(v0)
+        Lout = ctypes.c_double(0.0)
+        _check(lib().pat_power_norm(self._h, _ptr(v0), iters, ctypes.byref(Lout), _stream(stream)))
+        return Lout.value
+
+    def fista(self, y, x=None, iters: int = 100, lam: float = 0.0, L: float = 0.0,
+              power_iters: int = 50, warm_start: bool = False, stream=None):
+        """FISTA for Eq. 12-14; returns (x, report dict)."""
+        self._check_dtype(y)
+        b = self._batch_of(y, self.nt * self.ny * self.nx)
+        if x is None:
+            x = self._empty_like_device(self.obj_shape(b) if y.ndim == 4 else
+                                        self.obj_shape(1)[1:], y)
+            warm_start = False
+        prm = FistaParams(iters, power_iters, 1 if warm_start else 0, 0, lam, L)
+        rep = FistaReport()
+        _check(lib().pat_fista_solve(self._h, _ptr(y), _ptr(x), b, ctypes.byref(prm),
+                                     ctypes.byref(rep), _stream(stream)))
+        return x, {"L": rep.L, "resid2_first": rep.resid2_first, "resid2_last": rep.resid2_last,
+                   "iters": rep.iters}
+
+    def dot(self, a, b, stream=None) -> float:
+        """<a, b> with FP64 products and sums (device arrays)."""
+        self._check_dtype(a, b)
+        out = ctypes.c_double(0.0)
+        n = int(np.prod(a.shape))
+        assert int(np.prod(b.shape)) == n
+        _check(lib().pat_dot_f64(self._h, _ptr(a), _ptr(b), n, ctypes.byref(out), _stream(stream)))
+        return out.value
+
+    # ------------------------------------------------------------------ stages
+    def stage_spectrum(self, x, out=None, stream=None):
+        """Zero-padded 2D real DFT of real [S][ny][nx] slices -> complex [S][px//2+1][py]."""
+        torch = _torch()
+        self._check_dtype(x)
+        S = self._batch_of(x, self.ny * self.nx)
+        cdt = torch.complex128 if self.fp64 else torch.complex64
+        if out is None:
+            out = torch.empty((S, self.px // 2 + 1, self.py), dtype=cdt, device=x.device)
+        _check(lib().pat_stage_spectrum(self._h, _ptr(x), _ptr(out), S, _stream(stream)))
+        return out
+
+    def stage_image(self, X, out=None, stream=None):
+        """Unnormalised inverse 2D DFT of [S][px//2+1][py] spectra, real part, cropped to [S][ny][nx]."""
+        S = int(np.prod(X.shape)) // ((self.px // 2 + 1) * self.py)
+        if out is None:
+            out = self._empty_like_device((S, self.ny, self.nx), X)
+        _check(lib().pat_stage_image(self._h, _ptr(X), _ptr(out), S, _stream(stream)))
+        return out
+
+
+def _pow2_at_least(n: int) -> int:
+    p = 16
+    while p < n:
+        p *= 2
+    return p
+
+
+def _np_dtype(tdt):
+    torch = _torch()
+    return {torch.float32: np.float32, torch.float64: np.float64,
+            torch.complex64: np.complex64, torch.complex128: np.complex128}.get(tdt, None)
+
+
+def _table_format(table, plan: Plan):
+    """(format code, contiguous array to pass) for a spatial or spectral table."""
+    shape = tuple(table.shape)
+    spatial = (plan.nz, plan.nt, plan.py, plan.px)
+    spectral = (plan.nz, plan.nt, plan.py, plan.px // 2 + 1)
+    dt = table.dtype if isinstance(table, np.ndarray) else _np_dtype(table.dtype)
+    if isinstance(table, np.ndarray):
+        table = np.ascontiguousarray(table)
+    else:
+        table = table.contiguous()
+    if shape == spatial and dt in (np.float64, np.float32):
+        return (TABLE_SPATIAL_F64 if dt == np.float64 else TABLE_SPATIAL_F32), table
+    if shape == spectral and dt in (np.complex128, np.complex64):
+        return (TABLE_SPECTRAL_C128 if dt == np.complex128 else TABLE_SPECTRAL_C64), table
+    raise ValueError(f"table of shape {shape} / {dt}: expected spatial {spatial} real or "
+                     f"spectral {spectral} complex")
+
+
+def _autograd_fn():
+    torch = _torch()
+
+    class PatOp(torch.autograd.Function):
+        """d = H x with backward H* (the hand-written adjoint kernels)."""
+
+        @staticmethod
+        def forward(ctx, x, plan: Plan):
+            ctx.plan = plan
+            return plan.forward(x.contiguous())
+
+        @staticmethod
+        def backward(ctx, g):
+            return ctx.plan.adjoint(g.contiguous()), None
+
+    return PatOp
+
+
+def apply(plan: Plan, x):
+    """Differentiable H x (torch.autograd): backward applies H*."""
+    return _autograd_fn().apply(x, plan)

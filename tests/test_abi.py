@@ -1,0 +1,71 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every symbol that
+include/pat.h declares; argument errors come back as status codes without
+touching a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2603_28150_gb300 import pat
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "pat.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(pat_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol():
+    L = pat.lib()
+    declared = _declared()
+    assert len(declared) >= 13
+    for name in declared:
+        assert hasattr(L, name), name
+    assert sorted(pat.EXPORTS) == declared
+
+
+def test_library_targets_sm103a():
+    from paper_2603_28150_gb300 import build
+    assert "arch=compute_103a,code=sm_103a" in " ".join(build.ARCH)
+    assert os.path.exists(build.LIB)
+
+
+def test_argument_errors_without_gpu():
+    L = pat.lib()
+    out = ctypes.c_void_p(0)
+    assert L.pat_plan_create(None, None, 0, None, ctypes.byref(out)) == pat.PAT_ERR_ARG
+    g = pat.Geometry(32, 32, 4, 8, 48, 64, 1, 0)  # px not a power of two
+    buf = (ctypes.c_double * 4)()
+    assert L.pat_plan_create(ctypes.byref(g), buf, 0, None, ctypes.byref(out)) == pat.PAT_ERR_UNSUPPORTED
+    assert b"power" in L.pat_last_error()
+    g = pat.Geometry(40, 32, 4, 8, 64, 64, 1, 0)  # 64 < 2*40-1: circular aliasing
+    assert L.pat_plan_create(ctypes.byref(g), buf, 0, None, ctypes.byref(out)) == pat.PAT_ERR_ARG
+    g = pat.Geometry(8, 8, 4, 8, 16, 16, 0, 0)  # max_batch 0
+    assert L.pat_plan_create(ctypes.byref(g), buf, 0, None, ctypes.byref(out)) == pat.PAT_ERR_ARG
+    g = pat.Geometry(8, 8, 4, 8, 16, 16, 1, 0)
+    assert L.pat_plan_create(ctypes.byref(g), buf, 7, None, ctypes.byref(out)) == pat.PAT_ERR_ARG
+    assert L.pat_forward(None, buf, buf, 1, None) == pat.PAT_ERR_ARG
+    assert L.pat_plan_destroy(None) == pat.PAT_OK
+
+
+def test_medium_validation_without_gpu():
+    L = pat.lib()
+    out = ctypes.c_void_p(0)
+    g = pat.Geometry(8, 8, 4, 8, 16, 16, 1, 0)
+    m = pat.MediumC(1500.0, 1e-4, 1e-4, 1e-4, 2e-8, 4, 1)  # mz <= z0 + nz
+    assert L.pat_plan_create_kspace(ctypes.byref(g), ctypes.byref(m), None, ctypes.byref(out)) == pat.PAT_ERR_ARG
+    m = pat.MediumC(-1.0, 1e-4, 1e-4, 1e-4, 2e-8, 16, 1)
+    assert L.pat_plan_create_kspace(ctypes.byref(g), ctypes.byref(m), None, ctypes.byref(out)) == pat.PAT_ERR_ARG
+
+
+def test_product_has_no_cpu_fallback():
+    """The binding never imports the oracle and has no numpy compute path."""
+    import paper_2603_28150_gb300 as pkg
+    for f in os.listdir(os.path.dirname(pkg.__file__)):
+        if f.endswith(".py"):
+            src = open(os.path.join(os.path.dirname(pkg.__file__), f)).read()
+            assert "import oracle" not in src and "from oracle" not in src, f
+            assert "np.fft" not in src and "torch.fft" not in src, f
