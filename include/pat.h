@@ -109,6 +109,7 @@ typedef struct {
   int32_t real_table;      /* 1: the stored spectra are real (even kernels) */
   int32_t fp64;            /* 1: double-precision plan */
   int64_t bins;            /* stored frequency bins K = (px/2 + 1) py */
+  int64_t bins_padded;     /* K rounded up to a multiple of 32 (row stride of stage ii) */
   int64_t table_bytes;     /* device bytes of the resident table */
   int64_t workspace_bytes; /* device bytes of the plan's workspace */
   double table_max_abs;    /* max |Hh| seen while building the table */
@@ -138,7 +139,7 @@ typedef struct {
   double resid2_first;  /* ||H y_1 - d||^2 of the first gradient step (batch sum) */
   double resid2_last;   /* ||H y_k - d||^2 of the last gradient step (batch sum) */
   int32_t iters;        /* iterations run */
-  int32_t reserved;
+  int32_t kernels_per_iter; /* kernel launches of one iteration (graph kernel nodes) */
 } pat_fista_report;
 
 /* --- plans ------------------------------------------------------------------ */
@@ -224,6 +225,15 @@ int pat_stage_spectrum(pat_plan* plan, const void* in, void* out, int slices,
  * (stage iii; Eq. 16 term (iii)). */
 int pat_stage_image(pat_plan* plan, const void* in, void* out, int slices,
                     pat_stream stream);
+
+/* Stage ii alone (Eq. 16 term (ii)): the per-frequency contraction with the
+ * resident table, on device arrays of complex real_t with row stride
+ * bins_padded and bin index k = kx * py + ky (kx in [0, px/2]):
+ *   adjoint = 0:  out[b][t][k] = sum_z Hh[k][t][z] in[b][z][k]        (Eq. 7)
+ *   adjoint = 1:  out[b][z][k] = sum_t conj(Hh[k][t][z]) in[b][t][k]  (Eq. 11)
+ * Hh carries the 1/(px py) factor of the inverse transform. */
+int pat_stage_contract(pat_plan* plan, const void* in, void* out, int batch, int adjoint,
+                       pat_stream stream);
 
 #ifdef __cplusplus
 }

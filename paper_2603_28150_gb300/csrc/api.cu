@@ -25,6 +25,7 @@ int cuda_fail(cudaError_t e, const char* what) {
 
 struct Graph {
   int batch = 0;
+  int kernels = 0;  // kernel nodes of the captured iteration
   cudaGraphExec_t exec = nullptr;
   Graph* next = nullptr;
 };
@@ -311,6 +312,17 @@ Graph* graph_for(pat_plan* pp, int batch, int* rc) {
     if (e2 != cudaSuccess) e = e2;
   }
   cudaGraphExec_t exec = nullptr;
+  int kernels = 0;
+  if (e == cudaSuccess) {
+    size_t n = 0;
+    e = cudaGraphGetNodes(graph, nullptr, &n);
+    std::vector<cudaGraphNode_t> nodes(n);
+    if (e == cudaSuccess && n) e = cudaGraphGetNodes(graph, nodes.data(), &n);
+    for (size_t i = 0; e == cudaSuccess && i < n; ++i) {
+      cudaGraphNodeType t;
+      if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++kernels;
+    }
+  }
   if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
   if (graph) cudaGraphDestroy(graph);
   if (e != cudaSuccess) {
@@ -324,6 +336,7 @@ Graph* graph_for(pat_plan* pp, int batch, int* rc) {
     return nullptr;
   }
   g->batch = batch;
+  g->kernels = kernels;
   g->exec = exec;
   g->next = p.graphs;
   p.graphs = g;
@@ -404,6 +417,7 @@ int pat_plan_info(const pat_plan* plan, pat_plan_info_t* info) {
   info->real_table = p.L.real ? 1 : 0;
   info->fp64 = p.L.fp64 ? 1 : 0;
   info->bins = p.L.K;
+  info->bins_padded = p.L.Kpad;
   info->table_bytes = (int64_t)p.L.table_bytes;
   info->workspace_bytes = (int64_t)p.ws_bytes;
   info->table_max_abs = p.table_max_abs;
@@ -572,9 +586,11 @@ int pat_fista_solve(pat_plan* plan, const void* y, void* x, int batch,
     PAT_CUDA(cudaMemsetAsync(p.vol_b, 0, ob, s));
     PAT_CUDA(cudaMemsetAsync(p.vol_a, 0, ob, s));
   }
+  int kernels_per_iter = 0;
   if (iters > 0) {
     Graph* g = graph_for(plan, batch, &rc);
     if (!g) return rc;
+    kernels_per_iter = g->kernels;
     for (int k = 0; k < iters; ++k) PAT_CUDA(cudaGraphLaunch(g->exec, s));
   }
   PAT_CUDA(cudaMemcpyAsync(x, p.vol_b, ob, cudaMemcpyDefault, s));
@@ -586,7 +602,7 @@ int pat_fista_solve(pat_plan* plan, const void* y, void* x, int batch,
                                cudaMemcpyDeviceToHost, s));
     }
     PAT_CUDA(cudaStreamSynchronize(s));
-    *report = pat_fista_report{Lc, r2[0], r2[1], iters, 0};
+    *report = pat_fista_report{Lc, r2[0], r2[1], iters, kernels_per_iter};
   } else if (!is_device_ptr(x)) {
     PAT_CUDA(cudaStreamSynchronize(s));
   }
@@ -632,6 +648,22 @@ int pat_stage_image(pat_plan* plan, const void* in, void* out, int slices, pat_s
     return fail(PAT_ERR_ARG, "slices must be in [0, max_batch * max(nz, nt)]");
   PAT_CUDA(launch_image(plan->p, in, L.K, out, (int64_t)L.ny * L.nx, slices, nullptr, nullptr,
                         (cudaStream_t)stream));
+  return PAT_OK;
+  PAT_GUARD_END
+}
+
+int pat_stage_contract(pat_plan* plan, const void* in, void* out, int batch, int adjoint,
+                       pat_stream stream) {
+  PAT_GUARD_BEGIN
+  int rc = check_call(plan, batch);
+  if (rc != PAT_OK) return rc;
+  if (batch == 0) return PAT_OK;
+  if (!in || !out) return fail(PAT_ERR_ARG, "in or out is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (adjoint)
+    PAT_CUDA(launch_contract_adj(plan->p, in, out, batch, s));
+  else
+    PAT_CUDA(launch_contract_fwd(plan->p, in, out, batch, s));
   return PAT_OK;
   PAT_GUARD_END
 }

@@ -39,6 +39,7 @@ EXPORTS = (
     "pat_plan_create", "pat_plan_create_kspace", "pat_plan_destroy", "pat_plan_info",
     "pat_last_error", "pat_forward", "pat_adjoint", "pat_gradient", "pat_power_norm",
     "pat_fista_solve", "pat_dot_f64", "pat_stage_spectrum", "pat_stage_image",
+    "pat_stage_contract",
 )
 
 
@@ -62,7 +63,8 @@ class MediumC(ctypes.Structure):
 
 class PlanInfo(ctypes.Structure):
     _fields_ = [("real_table", ctypes.c_int32), ("fp64", ctypes.c_int32),
-                ("bins", ctypes.c_int64), ("table_bytes", ctypes.c_int64),
+                ("bins", ctypes.c_int64), ("bins_padded", ctypes.c_int64),
+                ("table_bytes", ctypes.c_int64),
                 ("workspace_bytes", ctypes.c_int64), ("table_max_abs", ctypes.c_double),
                 ("table_max_imag", ctypes.c_double)]
 
@@ -76,7 +78,7 @@ class FistaParams(ctypes.Structure):
 class FistaReport(ctypes.Structure):
     _fields_ = [("L", ctypes.c_double), ("resid2_first", ctypes.c_double),
                 ("resid2_last", ctypes.c_double), ("iters", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("kernels_per_iter", ctypes.c_int32)]
 
 
 _lib = None
@@ -110,6 +112,7 @@ def lib(build_if_missing: bool = True):
         "pat_dot_f64": ([P, V, V, ctypes.c_int64, D, P], I),
         "pat_stage_spectrum": ([P, V, V, I, P], I),
         "pat_stage_image": ([P, V, V, I, P], I),
+        "pat_stage_contract": ([P, V, V, I, I, P], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -296,7 +299,7 @@ class Plan:
         _check(lib().pat_fista_solve(self._h, _ptr(y), _ptr(x), b, ctypes.byref(prm),
                                      ctypes.byref(rep), _stream(stream)))
         return x, {"L": rep.L, "resid2_first": rep.resid2_first, "resid2_last": rep.resid2_last,
-                   "iters": rep.iters}
+                   "iters": rep.iters, "kernels_per_iter": rep.kernels_per_iter}
 
     def dot(self, a, b, stream=None) -> float:
         """<a, b> with FP64 products and sums (device arrays)."""
@@ -317,6 +320,12 @@ class Plan:
         if out is None:
             out = torch.empty((S, self.px // 2 + 1, self.py), dtype=cdt, device=x.device)
         _check(lib().pat_stage_spectrum(self._h, _ptr(x), _ptr(out), S, _stream(stream)))
+        return out
+
+    def stage_contract(self, X, out, batch: int = 1, adjoint: bool = False, stream=None):
+        """Stage ii alone on complex [batch][rows][bins_padded] device arrays."""
+        _check(lib().pat_stage_contract(self._h, _ptr(X), _ptr(out), batch, 1 if adjoint else 0,
+                                        _stream(stream)))
         return out
 
     def stage_image(self, X, out=None, stream=None):

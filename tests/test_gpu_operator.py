@@ -191,8 +191,10 @@ def test_fista_estimates_L_when_not_given():
     plan = Plan(g.nx, g.ny, g.nz, g.nt, g.px, g.py, table=h)
     y = op.A(synth.blobs(g.nx, g.ny, g.nz, count=3, seed=19))
     _, rep = plan.fista(cuda(y), iters=5, L=0.0, power_iters=80)
-    L_ref = oracle.power_norm(op, synth.gaussian_field(op.obj_shape, 20), 300)
-    assert abs(rep["L"] / 1.01 - L_ref) / L_ref < 1e-3
+    L_ref = oracle.power_norm(op, synth.gaussian_field(op.obj_shape, 20), 2000)
+    est = rep["L"] / 1.01
+    # power iteration approaches ||H*H|| from below (Rayleigh bound), within 1% after 80 steps
+    assert 0.99 * L_ref < est <= L_ref * (1 + 1e-5), (est, L_ref)
 
 
 def test_kspace_generated_table_matches_oracle_library():
