@@ -235,6 +235,28 @@ int pat_stage_image(pat_plan* plan, const void* in, void* out, int slices,
 int pat_stage_contract(pat_plan* plan, const void* in, void* out, int batch, int adjoint,
                        pat_stream stream);
 
+/* --- for callers that cannot allocate device memory ----------------------------- */
+
+/* The paper has no counterpart to this entry point; it exists for callers that
+ * must not allocate device memory at the point of the call (an application
+ * whose device memory is owned by its own pool allocator, or a latency-critical
+ * loop where cudaMalloc, which can synchronise the device, is not allowed).
+ *
+ * Same result as pat_stage_spectrum, without a plan and without allocating:
+ * zero-pads `slices` real float [ny][nx] slices (in, device) to py x px and
+ * writes their 2D real DFT to out (device), complex float [slices][px/2+1][py].
+ * The row-pass intermediate lives in a static device array of 64 MiB that
+ * every GPU loading the library holds until the process exits; requests with
+ * slices * (px/2 + 1) * (ny rounded up to even) * 8 > 64 MiB return
+ * PAT_ERR_ARG. No cudaMalloc, cudaFree or allocating library call is made.
+ * The first call on a device sets that device up (symbol lookup and a
+ * synchronous twiddle upload): make it before any stream capture. All calls
+ * share the static array (it keeps the last call's contents; nothing in it has
+ * to start at zero), so calls that overlap on the GPU race: serialise them on
+ * one stream. px, py: powers of two in [16, 1024], px >= 2nx - 1, py >= 2ny - 1. */
+int pat_spectrum_noalloc(const float* in, int nx, int ny, int px, int py, int slices,
+                         void* out, pat_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -39,7 +39,7 @@ EXPORTS = (
     "pat_plan_create", "pat_plan_create_kspace", "pat_plan_destroy", "pat_plan_info",
     "pat_last_error", "pat_forward", "pat_adjoint", "pat_gradient", "pat_power_norm",
     "pat_fista_solve", "pat_dot_f64", "pat_stage_spectrum", "pat_stage_image",
-    "pat_stage_contract",
+    "pat_stage_contract", "pat_spectrum_noalloc",
 )
 
 
@@ -113,6 +113,7 @@ def lib(build_if_missing: bool = True):
         "pat_stage_spectrum": ([P, V, V, I, P], I),
         "pat_stage_image": ([P, V, V, I, P], I),
         "pat_stage_contract": ([P, V, V, I, I, P], I),
+        "pat_spectrum_noalloc": ([V, I, I, I, I, I, V, P], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -335,6 +336,20 @@ class Plan:
             out = self._empty_like_device((S, self.ny, self.nx), X)
         _check(lib().pat_stage_image(self._h, _ptr(X), _ptr(out), S, _stream(stream)))
         return out
+
+
+def spectrum_noalloc(x, px: int, py: int, out=None, stream=None):
+    """pat_spectrum_noalloc: stage-i spectrum of float32 [S][ny][nx] CUDA slices
+    without a plan and without any device allocation inside the call (the
+    library's static scratch holds the intermediate). `out`, if given, must be a
+    complex64 CUDA tensor [S][px//2+1][py]; allocate it before calling when the
+    caller itself cannot allocate."""
+    torch = _torch()
+    S, ny, nx = int(x.shape[0]), int(x.shape[-2]), int(x.shape[-1])
+    if out is None:
+        out = torch.empty((S, px // 2 + 1, py), dtype=torch.complex64, device=x.device)
+    _check(lib().pat_spectrum_noalloc(_ptr(x), nx, ny, px, py, S, _ptr(out), _stream(stream)))
+    return out
 
 
 def _pow2_at_least(n: int) -> int:
