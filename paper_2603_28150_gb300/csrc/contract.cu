@@ -132,9 +132,11 @@ __global__ void __launch_bounds__(kWarps * 32)
 }
 
 // grid (nkb, ceil(batch / VB), z-chunks); block kWarps * 32. Warp w of z-chunk c
-// owns the z-groups g = c * kWarps * GPW + w + j * kWarps, j < GPW.
+// owns the z-groups g = c * kWarps * GPW + w + j * kWarps, j < GPW. Single-
+// volume float variants are held to 32 registers so 8 CTAs (all 64 warp slots)
+// stay resident: the stream needs the warps more than the registers.
 template <typename R, bool CPLX, int VB, int GPW>
-__global__ void __launch_bounds__(kWarps * 32)
+__global__ void __launch_bounds__(kWarps * 32, (sizeof(R) == 4 && !CPLX && VB == 1 && GPW <= 2) ? 8 : 1)
     k_contract_adj(const typename vec16<R>::type* __restrict__ table,
                    const cx<R>* __restrict__ D, cx<R>* __restrict__ Z, int nz, int nt, int nzg,
                    int64_t K, int64_t Kpad, int batch) {
@@ -155,7 +157,7 @@ __global__ void __launch_bounds__(kWarps * 32)
       for (int v = 0; v < VB; ++v) acc[j][q][v] = mk<R>(0, 0);
   const bool kok = k < K;
   const V* tb = table + (kb * nt) * (int64_t)nzg * 32 + lane;
-#pragma unroll 2
+#pragma unroll 1
   for (int t = 0; t < nt; ++t) {
     cx<R> d[VB];
 #pragma unroll

@@ -1,10 +1,13 @@
 // Batched 2D real FFT stages of the operator (Sec. 3.2, Eq. 16 terms (i) and (iii)).
 //
 // A P-point complex DFT runs as a Stockham auto-sort FFT (Govindaraju et al.,
-// SC'08 formulation) over 2-3 passes of radix 8/16: each thread holds one
+// SC'08 formulation) over 1-3 passes of radix 4/8/16: each thread holds one
 // radix-R butterfly in registers, multiplies by exp(-2 pi i r k / (Ns R))
 // (twiddles from a host FP64 table staged in shared memory) and writes the
-// R outputs to their sorted positions; vectors live in shared memory between
+// R outputs to their sorted positions. The first pass can read its inputs
+// straight from global memory and the last pass can write its outputs
+// straight to global memory (in both cases a vector's consecutive threads touch
+// consecutive elements), so shared memory carries each element once between
 // passes. The 2D real transform of a zero-padded n x n slice is split in two
 // kernels so every global access is contiguous:
 //   row pass    two real rows packed as one complex row (a + i b), FFT over x,
@@ -24,19 +27,26 @@ constexpr int kThreads = 256;
 
 template <int P>
 struct RadixPlan;
-template <> struct RadixPlan<16>   { static constexpr int NST = 1, R0 = 16, R1 = 1, R2 = 1, RMAX = 16; };
-template <> struct RadixPlan<32>   { static constexpr int NST = 2, R0 = 8,  R1 = 4, R2 = 1, RMAX = 8; };
-template <> struct RadixPlan<64>   { static constexpr int NST = 2, R0 = 8,  R1 = 8, R2 = 1, RMAX = 8; };
-template <> struct RadixPlan<128>  { static constexpr int NST = 2, R0 = 16, R1 = 8, R2 = 1, RMAX = 16; };
-template <> struct RadixPlan<256>  { static constexpr int NST = 2, R0 = 16, R1 = 16, R2 = 1, RMAX = 16; };
-template <> struct RadixPlan<512>  { static constexpr int NST = 3, R0 = 8,  R1 = 8, R2 = 8, RMAX = 8; };
-template <> struct RadixPlan<1024> { static constexpr int NST = 3, R0 = 16, R1 = 8, R2 = 8, RMAX = 16; };
+template <> struct RadixPlan<16>   { static constexpr int NST = 1, RMAX = 16; static constexpr int R[3] = {16, 1, 1}; };
+template <> struct RadixPlan<32>   { static constexpr int NST = 2, RMAX = 8;  static constexpr int R[3] = {8, 4, 1}; };
+template <> struct RadixPlan<64>   { static constexpr int NST = 2, RMAX = 8;  static constexpr int R[3] = {8, 8, 1}; };
+template <> struct RadixPlan<128>  { static constexpr int NST = 2, RMAX = 16; static constexpr int R[3] = {16, 8, 1}; };
+template <> struct RadixPlan<256>  { static constexpr int NST = 2, RMAX = 16; static constexpr int R[3] = {16, 16, 1}; };
+template <> struct RadixPlan<512>  { static constexpr int NST = 3, RMAX = 8;  static constexpr int R[3] = {8, 8, 8}; };
+template <> struct RadixPlan<1024> { static constexpr int NST = 3, RMAX = 16; static constexpr int R[3] = {16, 8, 8}; };
 
 template <int P>
 struct Shape {
-  static constexpr int TPV = P / RadixPlan<P>::RMAX;             // threads per vector
-  static constexpr int VPB = kThreads / TPV;                      // vectors per block
-  static constexpr int VSTR = P + P / 16;                         // padded vector stride
+  static constexpr int TPV = P / RadixPlan<P>::RMAX;  // threads per vector
+  static constexpr int VPB = kThreads / TPV;           // vectors per block
+  static constexpr int VSTR = P + P / 16;              // padded vector stride
+};
+
+// Radix of pass S and the product of the radices before it.
+template <int P, int S>
+struct PassOf {
+  static constexpr int RAD = RadixPlan<P>::R[S];
+  static constexpr int NS = S == 0 ? 1 : (S == 1 ? RadixPlan<P>::R[0] : RadixPlan<P>::R[0] * RadixPlan<P>::R[1]);
 };
 
 // One padding slot per 16 elements keeps the radix-16 scatter of the first
@@ -107,20 +117,34 @@ __device__ __forceinline__ void dft_reg(cx<R>* a) {
   dit_passes<R, N, 2, INV>(a);
 }
 
-// One Stockham pass of radix RAD over a vector of P points held in shared
-// memory (`buf`, padded indexing); NS = product of the earlier radices.
-template <typename R, int P, int RAD, int NS, bool INV>
-__device__ __forceinline__ void stage(cx<R>* buf, const cx<R>* tw, int tid) {
+// Pass S of a Stockham FFT of P points on the vector `buf` (shared memory,
+// padded indexing). With FROM_LOAD the first pass reads element i as ld(i)
+// instead of from buf; with TO_STORE the last pass hands element i to st(i, v)
+// instead of writing buf (in the last pass the output index is j + r Ns, so a
+// vector's consecutive threads store consecutive elements). Every thread of the
+// block calls every pass (they hold __syncthreads).
+template <typename R, int P, int S, bool INV, bool FROM_LOAD, bool TO_STORE, class LD, class ST>
+__device__ __forceinline__ void run_passes(cx<R>* buf, const cx<R>* tw, int tid, LD& ld, ST& st) {
+  constexpr int NST = RadixPlan<P>::NST;
+  constexpr int RAD = PassOf<P, S>::RAD;
+  constexpr int NS = PassOf<P, S>::NS;
   constexpr int TPV = Shape<P>::TPV;
   constexpr int NB = P / RAD;
   constexpr int PER = NB / TPV;
+  constexpr bool first_ld = FROM_LOAD && S == 0;
+  constexpr bool last_st = TO_STORE && S == NST - 1;
   cx<R> v[PER][RAD];
 #pragma unroll
   for (int q = 0; q < PER; ++q) {
     const int j = tid + q * TPV;
 #pragma unroll
-    for (int r = 0; r < RAD; ++r) v[q][r] = buf[pidx(j + r * NB)];
-    if (NS > 1) {
+    for (int r = 0; r < RAD; ++r) {
+      if constexpr (first_ld)
+        v[q][r] = ld(j + r * NB);
+      else
+        v[q][r] = buf[pidx(j + r * NB)];
+    }
+    if constexpr (NS > 1) {
       const int k = j & (NS - 1);
 #pragma unroll
       for (int r = 1; r < RAD; ++r) {
@@ -131,25 +155,36 @@ __device__ __forceinline__ void stage(cx<R>* buf, const cx<R>* tw, int tid) {
     }
     dft_reg<R, RAD, INV>(v[q]);
   }
-  __syncthreads();
+  if constexpr (last_st) {
 #pragma unroll
-  for (int q = 0; q < PER; ++q) {
-    const int j = tid + q * TPV;
-    const int k = j & (NS - 1);
-    const int base = (j - k) * RAD + k;
+    for (int q = 0; q < PER; ++q) {
+      const int j = tid + q * TPV;  // j < NS in the last pass: base index = j
 #pragma unroll
-    for (int r = 0; r < RAD; ++r) buf[pidx(base + r * NS)] = v[q][r];
+      for (int r = 0; r < RAD; ++r) st(j + r * NS, v[q][r]);
+    }
+  } else {
+    if constexpr (!first_ld) __syncthreads();  // in place: every read before any write
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int j = tid + q * TPV;
+      const int k = j & (NS - 1);
+      const int base = (j - k) * RAD + k;
+#pragma unroll
+      for (int r = 0; r < RAD; ++r) buf[pidx(base + r * NS)] = v[q][r];
+    }
+    __syncthreads();
   }
-  __syncthreads();
+  if constexpr (S + 1 < NST) run_passes<R, P, S + 1, INV, FROM_LOAD, TO_STORE>(buf, tw, tid, ld, st);
 }
 
-template <typename R, int P, bool INV>
-__device__ __forceinline__ void fft_all(cx<R>* buf, const cx<R>* tw, int tid) {
-  using PL = RadixPlan<P>;
-  stage<R, P, PL::R0, 1, INV>(buf, tw, tid);
-  if constexpr (PL::NST >= 2) stage<R, P, PL::R1, PL::R0, INV>(buf, tw, tid);
-  if constexpr (PL::NST >= 3) stage<R, P, PL::R2, PL::R0 * PL::R1, INV>(buf, tw, tid);
-}
+template <typename R>
+struct SmemLoad {  // unused placeholder type for passes that read buf
+  __device__ cx<R> operator()(int) const { return mk<R>(0, 0); }
+};
+template <typename R>
+struct NoStore {
+  __device__ void operator()(int, cx<R>) const {}
+};
 
 template <typename R, int P>
 __device__ __forceinline__ cx<R>* setup_smem(const cx<R>* tw_g, cx<R>** tw_s) {
@@ -179,32 +214,33 @@ __global__ void __launch_bounds__(kThreads) k_row_r2c(const R* __restrict__ in, 
   const int v = threadIdx.x / SH::TPV, tid = threadIdx.x % SH::TPV;
   const int64_t s = blockIdx.y;
   const int pair0 = blockIdx.x * SH::VPB;
-  const R* src = in + s * in_stride;
-  for (int i = threadIdx.x; i < SH::VPB * P; i += kThreads) {
-    const int vv = i / P, x = i % P;
-    const int y0 = 2 * (pair0 + vv);
+  const int y0 = 2 * (pair0 + v);
+  const R* row0 = in + s * in_stride + (int64_t)y0 * nx_in;
+  const bool ok0 = y0 < ny_in, ok1 = y0 + 1 < ny_in;
+  __syncthreads();  // twiddles staged
+  auto ld = [&](int x) -> cx<R> {
     R a = 0, b = 0;
     if (x < nx_in) {
-      if (y0 < ny_in) a = src[(int64_t)y0 * nx_in + x];
-      if (y0 + 1 < ny_in) b = src[(int64_t)(y0 + 1) * nx_in + x];
+      if (ok0) a = row0[x];
+      if (ok1) b = row0[nx_in + x];
     }
-    bufs[vv * SH::VSTR + pidx(x)] = mk<R>(a, b);
-  }
-  __syncthreads();
-  fft_all<R, P, false>(bufs + v * SH::VSTR, tw, tid);
+    return mk<R>(a, b);
+  };
+  NoStore<R> st;
+  run_passes<R, P, 0, false, true, false>(bufs + v * SH::VSTR, tw, tid, ld, st);
   cx<R>* dst = T + s * tslice;
   for (int i = threadIdx.x; i < SH::VPB * (P / 2 + 1); i += kThreads) {
     const int vv = i % SH::VPB, kx = i / SH::VPB;
-    const int y0 = 2 * (pair0 + vv);
-    if (y0 >= ny_in) continue;
+    const int yy = 2 * (pair0 + vv);
+    if (yy >= ny_in) continue;
     const cx<R> Z = bufs[vv * SH::VSTR + pidx(kx)];
     const cx<R> Zm = bufs[vv * SH::VSTR + pidx((P - kx) & (P - 1))];
-    // A = (Z + conj Zm) / 2 (row y0), B = (Z - conj Zm) / (2i) (row y0 + 1)
+    // A = (Z + conj Zm) / 2 (row yy), B = (Z - conj Zm) / (2i) (row yy + 1)
     const cx<R> A = mk<R>((R)0.5 * (Z.x + Zm.x), (R)0.5 * (Z.y - Zm.y));
     const cx<R> B = mk<R>((R)0.5 * (Z.y + Zm.y), (R)-0.5 * (Z.x - Zm.x));
-    cx<R>* o = dst + (int64_t)kx * tstride + y0;
+    cx<R>* o = dst + (int64_t)kx * tstride + yy;
     o[0] = A;
-    o[1] = B;  // tstride is even, so y0 + 1 < tstride
+    o[1] = B;  // tstride is even, so yy + 1 < tstride
   }
 }
 
@@ -220,26 +256,17 @@ __global__ void __launch_bounds__(kThreads) k_col_fwd(const cx<R>* __restrict__ 
   cx<R>* tw;
   cx<R>* bufs = setup_smem<R, P>(tw_g, &tw);
   const int v = threadIdx.x / SH::TPV, tid = threadIdx.x % SH::TPV;
-  const int64_t g0 = (int64_t)blockIdx.x * SH::VPB;
-  for (int i = threadIdx.x; i < SH::VPB * P; i += kThreads) {
-    const int vv = i / P, y = i % P;
-    const int64_t g = g0 + vv;
-    cx<R> a = mk<R>(0, 0);
-    if (g < nvec && y < n_in) {
-      const int64_t s = g / ncols, kx = g % ncols;
-      a = T[s * tslice + kx * tstride + y];
-    }
-    bufs[vv * SH::VSTR + pidx(y)] = a;
-  }
+  const int64_t g = (int64_t)blockIdx.x * SH::VPB + v;
+  const bool ok = g < nvec;
+  const int64_t s = ok ? g / ncols : 0, kx = ok ? g % ncols : 0;
+  const cx<R>* src = T + s * tslice + kx * tstride;
+  cx<R>* dst = out + s * out_stride + kx * P;
   __syncthreads();
-  fft_all<R, P, false>(bufs + v * SH::VSTR, tw, tid);
-  for (int i = threadIdx.x; i < SH::VPB * P; i += kThreads) {
-    const int vv = i / P, y = i % P;
-    const int64_t g = g0 + vv;
-    if (g >= nvec) continue;
-    const int64_t s = g / ncols, kx = g % ncols;
-    out[s * out_stride + kx * P + y] = bufs[vv * SH::VSTR + pidx(y)];
-  }
+  auto ld = [&](int y) -> cx<R> { return (ok && y < n_in) ? src[y] : mk<R>(0, 0); };
+  auto st = [&](int y, cx<R> val) {
+    if (ok) dst[y] = val;
+  };
+  run_passes<R, P, 0, false, true, true>(bufs + v * SH::VSTR, tw, tid, ld, st);
 }
 
 // Stage iii, column pass: in[s][kx][0..P) inverse FFT over ky, rows
@@ -254,26 +281,17 @@ __global__ void __launch_bounds__(kThreads) k_col_inv(const cx<R>* __restrict__ 
   cx<R>* tw;
   cx<R>* bufs = setup_smem<R, P>(tw_g, &tw);
   const int v = threadIdx.x / SH::TPV, tid = threadIdx.x % SH::TPV;
-  const int64_t g0 = (int64_t)blockIdx.x * SH::VPB;
-  for (int i = threadIdx.x; i < SH::VPB * P; i += kThreads) {
-    const int vv = i / P, y = i % P;
-    const int64_t g = g0 + vv;
-    cx<R> a = mk<R>(0, 0);
-    if (g < nvec) {
-      const int64_t s = g / ncols, kx = g % ncols;
-      a = in[s * in_stride + kx * P + y];
-    }
-    bufs[vv * SH::VSTR + pidx(y)] = a;
-  }
+  const int64_t g = (int64_t)blockIdx.x * SH::VPB + v;
+  const bool ok = g < nvec;
+  const int64_t s = ok ? g / ncols : 0, kx = ok ? g % ncols : 0;
+  const cx<R>* src = in + s * in_stride + kx * P;
+  cx<R>* dst = T + s * tslice + kx * tstride;
   __syncthreads();
-  fft_all<R, P, true>(bufs + v * SH::VSTR, tw, tid);
-  for (int i = threadIdx.x; i < SH::VPB * P; i += kThreads) {
-    const int vv = i / P, y = i % P;
-    const int64_t g = g0 + vv;
-    if (g >= nvec || y >= n_out) continue;
-    const int64_t s = g / ncols, kx = g % ncols;
-    T[s * tslice + kx * tstride + y] = bufs[vv * SH::VSTR + pidx(y)];
-  }
+  auto ld = [&](int y) -> cx<R> { return ok ? src[y] : mk<R>(0, 0); };
+  auto st = [&](int y, cx<R> val) {
+    if (ok && y < n_out) dst[y] = val;
+  };
+  run_passes<R, P, 0, true, true, true>(bufs + v * SH::VSTR, tw, tid, ld, st);
 }
 
 // Stage iii, row pass: half spectra A = T[s][kx][y0], B = T[s][kx][y0 + 1]
@@ -297,11 +315,11 @@ __global__ void __launch_bounds__(kThreads) k_row_c2r(const cx<R>* __restrict__ 
   const cx<R>* src = T + s * tslice;
   for (int i = threadIdx.x; i < SH::VPB * (P / 2 + 1); i += kThreads) {
     const int vv = i % SH::VPB, kx = i / SH::VPB;
-    const int y0 = 2 * (pair0 + vv);
+    const int yy = 2 * (pair0 + vv);
     cx<R> A = mk<R>(0, 0), B = mk<R>(0, 0);
-    if (y0 < ny_out) {
-      A = src[(int64_t)kx * tstride + y0];
-      if (y0 + 1 < ny_out) B = src[(int64_t)kx * tstride + y0 + 1];
+    if (yy < ny_out) {
+      A = src[(int64_t)kx * tstride + yy];
+      if (yy + 1 < ny_out) B = src[(int64_t)kx * tstride + yy + 1];
     }
     if (kx == 0 || kx == P / 2) {  // spectra of real rows: real at DC and Nyquist
       A.y = 0;
@@ -312,30 +330,29 @@ __global__ void __launch_bounds__(kThreads) k_row_c2r(const cx<R>* __restrict__ 
     if (kx > 0 && kx < P / 2) b[pidx(P - kx)] = mk<R>(A.x + B.y, B.x - A.y);
   }
   __syncthreads();
-  fft_all<R, P, true>(bufs + v * SH::VSTR, tw, tid);
-  R* dst = out + s * out_stride;
-  const R* sb = sub ? sub + s * out_stride : nullptr;
+  const int y0 = 2 * (pair0 + v);
+  const bool ok0 = y0 < ny_out, ok1 = y0 + 1 < ny_out;
+  R* d0 = out + s * out_stride + (int64_t)y0 * nx_out;
+  const R* s0 = sub ? sub + s * out_stride + (int64_t)y0 * nx_out : nullptr;
   double acc = 0.0;
-  for (int i = threadIdx.x; i < SH::VPB * nx_out; i += kThreads) {
-    const int vv = i / nx_out, x = i % nx_out;
-    const int y0 = 2 * (pair0 + vv);
-    if (y0 >= ny_out) continue;
-    const cx<R> z = bufs[vv * SH::VSTR + pidx(x)];
+  auto st = [&](int x, cx<R> z) {
+    if (x >= nx_out || !ok0) return;
     R r0 = z.x, r1 = z.y;
-    const int64_t o0 = (int64_t)y0 * nx_out + x, o1 = o0 + nx_out;
-    if (sb) {
-      r0 -= sb[o0];
+    if (s0) {
+      r0 -= s0[x];
       acc += (double)r0 * (double)r0;
     }
-    dst[o0] = r0;
-    if (y0 + 1 < ny_out) {
-      if (sb) {
-        r1 -= sb[o1];
+    d0[x] = r0;
+    if (ok1) {
+      if (s0) {
+        r1 -= s0[nx_out + x];
         acc += (double)r1 * (double)r1;
       }
-      dst[o1] = r1;
+      d0[nx_out + x] = r1;
     }
-  }
+  };
+  SmemLoad<R> ld;
+  run_passes<R, P, 0, true, false, true>(bufs + v * SH::VSTR, tw, tid, ld, st);
   if (partials) {
     // deterministic block sum: warp shuffle tree, then warp 0 over the warps
     __shared__ double wsum[kThreads / 32];
@@ -411,16 +428,16 @@ cudaError_t row_c2r(const cx<R>* T, int tstride, int64_t tslice, int nx_out, int
   return cudaGetLastError();
 }
 
-#define PAT_P_SWITCH(PV, CALL)                         \
-  switch (PV) {                                        \
-    case 16: { constexpr int P_ = 16; return CALL; }   \
-    case 32: { constexpr int P_ = 32; return CALL; }   \
-    case 64: { constexpr int P_ = 64; return CALL; }   \
-    case 128: { constexpr int P_ = 128; return CALL; } \
-    case 256: { constexpr int P_ = 256; return CALL; } \
-    case 512: { constexpr int P_ = 512; return CALL; } \
+#define PAT_P_SWITCH(PV, CALL)                           \
+  switch (PV) {                                          \
+    case 16: { constexpr int P_ = 16; return CALL; }     \
+    case 32: { constexpr int P_ = 32; return CALL; }     \
+    case 64: { constexpr int P_ = 64; return CALL; }     \
+    case 128: { constexpr int P_ = 128; return CALL; }   \
+    case 256: { constexpr int P_ = 256; return CALL; }   \
+    case 512: { constexpr int P_ = 512; return CALL; }   \
     case 1024: { constexpr int P_ = 1024; return CALL; } \
-    default: return cudaErrorInvalidValue;             \
+    default: return cudaErrorInvalidValue;               \
   }
 
 template <typename R>
@@ -464,9 +481,7 @@ cudaError_t image_t(const Plan& p, const cx<R>* in, int64_t in_stride, R* out, i
                                         partials, twx, st, &nblocks)))
   };
   if ((e = row()) != cudaSuccess) return e;
-  if (sumsq) {
-    return launch_partials_sum(p.red, nblocks, sumsq, st);
-  }
+  if (sumsq) return launch_partials_sum(p.red, nblocks, sumsq, st);
   return cudaSuccess;
 }
 

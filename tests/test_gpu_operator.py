@@ -86,21 +86,24 @@ def test_adjoint_identity_on_gpu(fp64):
     torch.cuda.synchronize()
 
 
-def test_batch_equals_single_volumes():
+@pytest.mark.parametrize("kind", ["random", "even"])
+@pytest.mark.parametrize("fp64", [False, True])
+@pytest.mark.parametrize("B", [2, 3, 6])  # 2- and 4-volume groups and their tails
+def test_batch_equals_single_volumes(kind, fp64, B):
     g = RAGGED
-    h = _tables(g, "random", seed=8)
-    B = 6  # exercises the 4-volume and the tail group
-    plan = Plan(g.nx, g.ny, g.nz, g.nt, g.px, g.py, table=h, max_batch=B)
+    h = _tables(g, kind, seed=8)
+    plan = Plan(g.nx, g.ny, g.nz, g.nt, g.px, g.py, table=h, max_batch=B, fp64=fp64)
     xs = np.stack([synth.blobs(g.nx, g.ny, g.nz, count=3, seed=s) for s in range(B)])
     ys = np.stack([synth.gaussian_field((g.nt, g.ny, g.nx), 20 + s) for s in range(B)])
     A, AT = _ref_ops(h, g)
-    d = host(plan.forward(cuda(xs)))
-    a = host(plan.adjoint(cuda(ys)))
+    d = host(plan.forward(cuda(xs, fp64)))
+    a = host(plan.adjoint(cuda(ys, fp64)))
+    tol = 1e-12 if fp64 else 1e-5
     for b in range(B):
-        assert oracle.rel_l2(d[b], A(xs[b])) < 1e-5
-        assert oracle.rel_l2(a[b], AT(ys[b])) < 1e-5
-    one = host(plan.forward(cuda(xs[2:3])))
-    assert np.abs(one[0] - d[2]).max() <= 1e-6 * np.abs(d[2]).max()
+        assert oracle.rel_l2(d[b], A(xs[b])) < tol
+        assert oracle.rel_l2(a[b], AT(ys[b])) < tol
+    one = host(plan.forward(cuda(xs[1:2], fp64)))
+    assert np.abs(one[0] - d[1]).max() <= 10 * tol * np.abs(d[1]).max()
 
 
 def test_host_pointers_equal_device_pointers():
