@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="wall time of the CPU-oracle sample")
+    ap.add_argument("--serve-seconds", type=float, default=10.0,
+                    help="arrival window of the serving measurement (0 = skip)")
     return ap.parse_args()
 
 
@@ -288,9 +290,70 @@ def run_ours(args, world, rank, local):
         "resid2_last": rep["resid2_last"],
     }
     plan.close()
+    if args.serve_seconds > 0:
+        out["serve"] = run_serve(args.serve_seconds, seed=rank)
     if rank == 0:
         out["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     return out
+
+
+# ----------------------------------------------------------------------------- serving
+SERVE_GEOMS = [(64, 32, 128), (128, 64, 256), (256, 128, 512)]  # n, nz, nt; padded 2n
+SERVE_RATE, SERVE_ITERS, SERVE_BUDGET, SERVE_SLOTS = 20.0, 50, 150 << 30, 16
+
+
+def run_serve(seconds: float, seed: int = 0):
+    """Poisson arrivals (20/s) of FISTA-50 requests over the three grids, same
+    trace through the continuous-batching server (real-even tables, 16 slots per
+    grid, 150 GB budget) and through the plain path (complex64 tables, one
+    request at a time). Each arm gets `seconds` of arrivals plus 10 s to drain;
+    requests still open then are reported as unfinished (with a lower bound on
+    the p99 that includes them)."""
+    import numpy as np
+    import torch
+
+    from paper_2603_28150_gb300 import synth
+    from paper_2603_28150_gb300.serve import (CudaEngine, Geometry, Request, Server,
+                                              poisson_arrivals, serve_one_at_a_time)
+    geoms = [Geometry(n, nz, nt, 2 * n, C0, DX, DT) for n, nz, nt in SERVE_GEOMS]
+    srv = Server(geoms, SERVE_BUDGET, SERVE_SLOTS, engine_factory=CudaEngine)
+    engines = {g.key: srv._engine_for(g.key) for g in geoms}
+    pool = {}
+    for g in geoms:  # 3 noisy data sets per grid, reused round-robin
+        eng = engines[g.key]
+        pool[g.key] = []
+        for s in range(3):
+            p0 = torch.tensor(synth.vessel_phantom(g.n, g.nz, seed=seed * 10 + s),
+                              dtype=torch.float32, device="cuda")
+            d = eng.plan.forward(p0)
+            nz = torch.tensor(synth.gaussian_field(tuple(d.shape), 900 + s), dtype=torch.float32,
+                              device="cuda")
+            pool[g.key].append((d + 0.05 * d.pow(2).mean().sqrt() * nz).contiguous())
+    rng = np.random.default_rng(seed)
+    arr = poisson_arrivals(SERVE_RATE, seconds, seed=seed)
+    keys = [geoms[int(rng.integers(0, len(geoms)))].key for _ in arr]
+
+    def trace():
+        return [Request(i, k, pool[k][i % 3], SERVE_ITERS, 0.0, float(t))
+                for i, (t, k) in enumerate(zip(arr, keys))]
+
+    torch.cuda.synchronize()
+    rep = srv.run(trace(), drain_seconds=10.0)
+    rep["gpu_launches"] = sum(e.kernels for e in engines.values())
+    rep["memory_gb"] = srv.used / 1e9
+    srv.close()
+    # plain path: complex64 tables, one request at a time
+    plain = {}
+    for g in geoms:
+        e = CudaEngine(g, 1, force_complex=True)
+        plain[g.key] = (e.plan, e.L)
+    torch.cuda.synchronize()
+    base = serve_one_at_a_time(plain, trace(), drain_seconds=10.0)
+    for p, _ in plain.values():
+        p.close()
+    return {"workload": f"Poisson {SERVE_RATE:.0f} req/s for {seconds:.0f} s, FISTA-{SERVE_ITERS}, "
+                        "grids 64²x32x128 / 128²x64x256 / 256²x128x512 (padded 2x), uniform mix",
+            "batched": rep, "plain_one_at_a_time": base}
 
 
 # ----------------------------------------------------------------------------- CPU oracle

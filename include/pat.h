@@ -165,6 +165,13 @@ int pat_plan_destroy(pat_plan* plan);
 
 int pat_plan_info(const pat_plan* plan, pat_plan_info_t* info);
 
+/* Device bytes a plan for `g` would take, before creating it (admission
+ * control): *table_bytes for the real (real_table = 1) or complex
+ * representation of the library, *workspace for everything else (including
+ * the host-pointer staging buffers). No device call is made. */
+int pat_plan_estimate(const pat_geometry* g, int real_table, int64_t* table_bytes,
+                      int64_t* workspace);
+
 /* Message of the last failure on the calling thread ("" if none). */
 const char* pat_last_error(void);
 
@@ -210,6 +217,38 @@ int pat_fista_solve(pat_plan* plan, const void* y, void* x, int batch,
  * same inputs give the same bits. */
 int pat_dot_f64(pat_plan* plan, const void* a, const void* b, int64_t n, double* out,
                 pat_stream stream);
+
+/* --- continuous batching: FISTA requests in slots --------------------------------- */
+
+/* A plan's max_batch slots each hold one FISTA reconstruction in progress
+ * (Eq. 12-14): its measured data, x_{k-1}, momentum point y_k and its own
+ * t_k, beta_k, 1/L, lambda/L, iteration count and last residual norm. Requests
+ * enter and leave between steps, so the slots sit at different iterations.
+ * pat_slots_step(n) advances slots [0, n) by one FISTA iteration each: one
+ * batched H (the table is read once per group of volumes instead of once per
+ * request), one batched H*, and each slot's own prox/momentum update; every
+ * step is one CUDA graph, captured the first time this n is used. The
+ * iterates are those of pat_fista_solve run on the request alone.
+ * All calls are stream-ordered on `stream`. */
+
+/* Loads a request into `slot`: copies y (real_t[nt][ny][nx], host or device;
+ * a host y has been copied when the call returns), sets x_0 = y_1 = 0,
+ * t_1 = 1, and the step 1/L and weight lambda (L > 0, lambda >= 0). */
+int pat_slot_load(pat_plan* plan, int slot, const void* y, double lambda, double L,
+                  pat_stream stream);
+
+/* Copies the whole state of slot `src` into slot `dst` (to keep the active
+ * requests packed in [0, n) when one leaves). */
+int pat_slot_move(pat_plan* plan, int dst, int src, pat_stream stream);
+
+/* One FISTA iteration for slots [0, n), 0 <= n <= max_batch. If `kernels` is
+ * not NULL it receives the kernel launches of the step. */
+int pat_slots_step(pat_plan* plan, int n, int* kernels, pat_stream stream);
+
+/* Copies the current iterate x_k of `slot` (real_t[nz][ny][nx]) to x (host or
+ * device; may be NULL) and, if resid2 is not NULL, ||H y_k - d||^2 of its last
+ * step to *resid2 (host; the call then synchronises `stream`). */
+int pat_slot_read(pat_plan* plan, int slot, void* x, double* resid2, pat_stream stream);
 
 /* --- diagnostics: the FFT stages on their own ----------------------------------- */
 

@@ -23,29 +23,7 @@ int cuda_fail(cudaError_t e, const char* what) {
   return e == cudaErrorMemoryAllocation ? PAT_ERR_OOM : PAT_ERR_CUDA;
 }
 
-struct Graph {
-  int batch = 0;
-  int kernels = 0;  // kernel nodes of the captured iteration
-  cudaGraphExec_t exec = nullptr;
-  Graph* next = nullptr;
-};
-
-// Extra plan state that only this file touches.
-struct PlanExt {
-  void* io_obj[2] = {nullptr, nullptr};  // host-pointer staging (objects)
-  void* io_dat = nullptr;                // host-pointer staging (data)
-  double* res = nullptr;                 // device scalars: [0] dot, [1] r2 current, [2] norm
-  double* scal = nullptr;                // device scalars: [0] 1/L, [1] lambda/L
-  cudaStream_t cap = nullptr;            // private stream for graph capture
-  int c2r_partials = 0;
-};
-
 }  // namespace pat
-
-struct pat_plan {
-  pat::Plan p;
-  pat::PlanExt x;
-};
 
 using namespace pat;
 
@@ -100,7 +78,8 @@ void free_plan(pat_plan* pp) {
   }
   void* bufs[] = {p.table, p.twx,    p.twy,     p.X,         p.Y,      p.T,       p.vol_a,
                   p.vol_b, p.vol_c,  p.dat_a,   p.dat_b,     p.red,    p.betas,   p.iter_dev,
-                  p.r2_dev, x.io_obj[0], x.io_obj[1], x.io_dat, x.res, x.scal};
+                  p.r2_dev, x.io_obj[0], x.io_obj[1], x.io_dat, x.res, x.scal,
+                  x.slots.t, x.slots.beta, x.slots.invL, x.slots.lamL, x.slots.r2, x.slots.k};
   for (void* b : bufs) cudaFree(b);
   if (x.cap) cudaStreamDestroy(x.cap);
   delete pp;
@@ -134,6 +113,20 @@ int c2r_partials_bound(const Layout& L) {
   return (int)(smax * ((L.ny + 1) / 2 + 1));
 }
 
+// Device bytes of a plan's workspace, including the host-staging buffers
+// allocated on the first call with host pointers.
+int64_t workspace_bytes(const Layout& L) {
+  const size_t cs = 2 * L.rsize;
+  const int64_t smax = (int64_t)L.max_batch * std::max(L.nz, L.nt);
+  const int64_t xy = smax * L.Kpad * (int64_t)cs;
+  const int64_t tb = smax * L.tslice * (int64_t)cs;
+  const int64_t vol = (int64_t)L.max_batch * L.nz * L.ny * L.nx * (int64_t)L.rsize;
+  const int64_t dat = (int64_t)L.max_batch * L.nt * L.ny * L.nx * (int64_t)L.rsize;
+  const int64_t red = sizeof(double) * (int64_t)std::max(kReduceBlocks, c2r_partials_bound(L));
+  const int64_t twiddles = (int64_t)(L.px + L.py) * (int64_t)cs;
+  return 2 * xy + tb + 5 * vol + 3 * dat + red + twiddles + 6 * 8 * (int64_t)L.max_batch + 1024;
+}
+
 int alloc_workspace(pat_plan* pp) {
   Plan& p = pp->p;
   PlanExt& x = pp->x;
@@ -157,6 +150,13 @@ int alloc_workspace(pat_plan* pp) {
   PAT_CUDA(cudaMalloc(&x.res, sizeof(double) * 8));
   PAT_CUDA(cudaMalloc(&x.scal, sizeof(double) * 2));
   PAT_CUDA(cudaMalloc(&p.iter_dev, sizeof(int)));
+  const size_t sb = sizeof(double) * L.max_batch;
+  PAT_CUDA(cudaMalloc(&x.slots.t, sb));
+  PAT_CUDA(cudaMalloc(&x.slots.beta, sb));
+  PAT_CUDA(cudaMalloc(&x.slots.invL, sb));
+  PAT_CUDA(cudaMalloc(&x.slots.lamL, sb));
+  PAT_CUDA(cudaMalloc(&x.slots.r2, sb));
+  PAT_CUDA(cudaMalloc(&x.slots.k, sizeof(int) * L.max_batch));
   PAT_CUDA(cudaStreamCreateWithFlags(&x.cap, cudaStreamNonBlocking));
   p.ws_bytes = 2 * xy + tb + 3 * vol + 2 * dat + sizeof(double) * (x.c2r_partials + 10);
   return PAT_OK;
@@ -193,18 +193,20 @@ int create_common(const pat_geometry* g, pat_plan** out, pat_plan** pp_out) {
 size_t obj_elems(const Layout& L, int batch) { return (size_t)batch * L.nz * L.ny * L.nx; }
 size_t dat_elems(const Layout& L, int batch) { return (size_t)batch * L.nt * L.ny * L.nx; }
 
-// d = H rho on device buffers; with `sub`, d = H rho - sub and ||d||^2 -> *sumsq.
+}  // namespace
+
+namespace pat {
+
 cudaError_t forward_dev(const Plan& p, const void* rho, void* d, int batch, cudaStream_t s,
-                        const void* sub = nullptr, double* sumsq = nullptr) {
+                        const void* sub, double* sumsq, int groups, double* group_sums) {
   const Layout& L = p.L;
   const int64_t plane = (int64_t)L.ny * L.nx;
   cudaError_t e = launch_spectrum(p, rho, plane, L.nx, L.ny, p.X, L.Kpad, batch * L.nz, s);
   if (e != cudaSuccess) return e;
   if ((e = launch_contract_fwd(p, p.X, p.Y, batch, s)) != cudaSuccess) return e;
-  return launch_image(p, p.Y, L.Kpad, d, plane, batch * L.nt, sub, sumsq, s);
+  return launch_image(p, p.Y, L.Kpad, d, plane, batch * L.nt, sub, sumsq, s, groups, group_sums);
 }
 
-// rho = H* d on device buffers.
 cudaError_t adjoint_dev(const Plan& p, const void* d, void* rho, int batch, cudaStream_t s) {
   const Layout& L = p.L;
   const int64_t plane = (int64_t)L.ny * L.nx;
@@ -213,6 +215,25 @@ cudaError_t adjoint_dev(const Plan& p, const void* d, void* rho, int batch, cuda
   if ((e = launch_contract_adj(p, p.Y, p.X, batch, s)) != cudaSuccess) return e;
   return launch_image(p, p.X, L.Kpad, rho, plane, batch * L.nz, nullptr, nullptr, s);
 }
+
+cudaError_t instantiate_counted(cudaGraph_t graph, cudaGraphExec_t* exec, int* kernels) {
+  size_t n = 0;
+  *kernels = 0;
+  cudaError_t e = cudaGraphGetNodes(graph, nullptr, &n);
+  std::vector<cudaGraphNode_t> nodes(n);
+  if (e == cudaSuccess && n) e = cudaGraphGetNodes(graph, nodes.data(), &n);
+  for (size_t i = 0; e == cudaSuccess && i < n; ++i) {
+    cudaGraphNodeType t;
+    if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel)
+      ++*kernels;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(exec, graph, 0);
+  return e;
+}
+
+}  // namespace pat
+
+namespace {
 
 int check_call(pat_plan* plan, int batch) {
   if (!plan) return fail(PAT_ERR_ARG, "plan is NULL");
@@ -302,7 +323,7 @@ cudaError_t fista_iter(pat_plan* pp, int batch, cudaStream_t s) {
 Graph* graph_for(pat_plan* pp, int batch, int* rc) {
   Plan& p = pp->p;
   for (Graph* g = p.graphs; g; g = g->next)
-    if (g->batch == batch) return g;
+    if (g->kind == 0 && g->batch == batch) return g;
   cudaStream_t cs = pp->x.cap;
   cudaGraph_t graph = nullptr;
   cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
@@ -313,17 +334,7 @@ Graph* graph_for(pat_plan* pp, int batch, int* rc) {
   }
   cudaGraphExec_t exec = nullptr;
   int kernels = 0;
-  if (e == cudaSuccess) {
-    size_t n = 0;
-    e = cudaGraphGetNodes(graph, nullptr, &n);
-    std::vector<cudaGraphNode_t> nodes(n);
-    if (e == cudaSuccess && n) e = cudaGraphGetNodes(graph, nodes.data(), &n);
-    for (size_t i = 0; e == cudaSuccess && i < n; ++i) {
-      cudaGraphNodeType t;
-      if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++kernels;
-    }
-  }
-  if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+  if (e == cudaSuccess) e = instantiate_counted(graph, &exec, &kernels);
   if (graph) cudaGraphDestroy(graph);
   if (e != cudaSuccess) {
     *rc = cuda_fail(e, "capturing the FISTA iteration graph");
@@ -407,6 +418,20 @@ int pat_plan_destroy(pat_plan* plan) {
   if (!plan) return PAT_OK;
   cudaDeviceSynchronize();
   free_plan(plan);
+  return PAT_OK;
+  PAT_GUARD_END
+}
+
+int pat_plan_estimate(const pat_geometry* g, int real_table, int64_t* table_bytes,
+                      int64_t* workspace) {
+  PAT_GUARD_BEGIN
+  int rc = validate(g);
+  if (rc != PAT_OK) return rc;
+  if (!table_bytes || !workspace) return fail(PAT_ERR_ARG, "output pointer is NULL");
+  Layout L = make_layout(g);
+  set_representation(L, real_table != 0);
+  *table_bytes = (int64_t)L.table_bytes;
+  *workspace = workspace_bytes(L);
   return PAT_OK;
   PAT_GUARD_END
 }

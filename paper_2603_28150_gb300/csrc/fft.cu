@@ -463,7 +463,8 @@ cudaError_t spectrum_t(const Plan& p, const R* in, int64_t in_stride, int nx_in,
 
 template <typename R>
 cudaError_t image_t(const Plan& p, const cx<R>* in, int64_t in_stride, R* out, int64_t out_stride,
-                    int S, const R* sub, double* sumsq, cudaStream_t st) {
+                    int S, const R* sub, double* sumsq, cudaStream_t st, int groups,
+                    double* group_sums) {
   const Layout& L = p.L;
   cx<R>* T = static_cast<cx<R>*>(p.T);
   const cx<R>* twx = static_cast<const cx<R>*>(p.twx);
@@ -475,12 +476,16 @@ cudaError_t image_t(const Plan& p, const cx<R>* in, int64_t in_stride, R* out, i
   };
   if ((e = col()) != cudaSuccess) return e;
   int nblocks = 0;
-  double* partials = sumsq ? p.red : nullptr;
+  const bool grouped = groups > 0 && group_sums != nullptr;
+  double* partials = (sumsq || grouped) ? p.red : nullptr;
   auto row = [&]() -> cudaError_t {
     PAT_P_SWITCH(L.px, (row_c2r<R, P_>(T, L.tstride, L.tslice, L.nx, L.ny, out, out_stride, S, sub,
                                         partials, twx, st, &nblocks)))
   };
   if ((e = row()) != cudaSuccess) return e;
+  // partials are slice-major, so each group of S / groups slices owns a
+  // contiguous run of nblocks / groups partials
+  if (grouped) return launch_group_sums(p.red, nblocks / groups, groups, group_sums, st);
   if (sumsq) return launch_partials_sum(p.red, nblocks, sumsq, st);
   return cudaSuccess;
 }
@@ -499,14 +504,15 @@ cudaError_t launch_spectrum(const Plan& p, const void* in, int64_t in_stride, in
 
 cudaError_t launch_image(const Plan& p, const void* in, int64_t in_stride, void* out,
                          int64_t out_stride, int S, const void* sub, double* sumsq,
-                         cudaStream_t s) {
+                         cudaStream_t s, int groups, double* group_sums) {
   if (S <= 0) return cudaSuccess;
   if (p.L.fp64)
     return image_t<double>(p, static_cast<const cx<double>*>(in), in_stride,
                            static_cast<double*>(out), out_stride, S,
-                           static_cast<const double*>(sub), sumsq, s);
+                           static_cast<const double*>(sub), sumsq, s, groups, group_sums);
   return image_t<float>(p, static_cast<const cx<float>*>(in), in_stride, static_cast<float*>(out),
-                        out_stride, S, static_cast<const float*>(sub), sumsq, s);
+                        out_stride, S, static_cast<const float*>(sub), sumsq, s, groups,
+                        group_sums);
 }
 
 }  // namespace pat

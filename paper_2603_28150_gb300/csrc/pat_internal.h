@@ -109,7 +109,55 @@ struct Plan {
 };
 
 constexpr int kReduceBlocks = 1024;  // max blocks of the FP64 reductions
-// red[0 .. kReduceBlocks) partials, red[kReduceBlocks ..] results
+
+// A captured iteration: FISTA (kind 0) or a slot step (kind 1) for `batch` volumes.
+struct Graph {
+  int kind = 0;
+  int batch = 0;
+  int kernels = 0;  // kernel nodes of the captured iteration
+  cudaGraphExec_t exec = nullptr;
+  Graph* next = nullptr;
+};
+
+// Per-slot FISTA state for continuous batching (device arrays of max_batch).
+struct Slots {
+  double* t = nullptr;     // t_k of the next iteration
+  double* beta = nullptr;  // (t_k - 1) / t_{k+1}
+  double* invL = nullptr;  // 1 / L
+  double* lamL = nullptr;  // lambda / L
+  double* r2 = nullptr;    // ||H y_k - d||^2 of the last step
+  int* k = nullptr;        // iterations done
+};
+
+// Plan state beyond the operator: host-pointer staging, scalars, capture stream.
+struct PlanExt {
+  void* io_obj[2] = {nullptr, nullptr};  // host-pointer staging (objects)
+  void* io_dat = nullptr;                // host-pointer staging (data)
+  double* res = nullptr;                 // device scalars: [0] dot, [1] r2 current, [2] norm
+  double* scal = nullptr;                // device scalars: [0] 1/L, [1] lambda/L
+  cudaStream_t cap = nullptr;            // private stream for graph capture
+  int c2r_partials = 0;
+  Slots slots;
+};
+
+// d = H rho / rho = H* d on device buffers of the plan's precision; with `sub`,
+// the forward writes H rho - sub and sums its squares (FP64) into *sumsq, or,
+// with groups > 0, per group of nt slices into group_sums[groups].
+cudaError_t forward_dev(const Plan& p, const void* rho, void* d, int batch, cudaStream_t s,
+                        const void* sub = nullptr, double* sumsq = nullptr, int groups = 0,
+                        double* group_sums = nullptr);
+cudaError_t adjoint_dev(const Plan& p, const void* d, void* rho, int batch, cudaStream_t s);
+// Records the kernel nodes of `graph`; instantiates it.
+cudaError_t instantiate_counted(cudaGraph_t graph, cudaGraphExec_t* exec, int* kernels);
+
+}  // namespace pat
+
+struct pat_plan {
+  pat::Plan p;
+  pat::PlanExt x;
+};
+
+namespace pat {
 
 // ----------------------------------------------------------------------------
 // Error plumbing (thread-local message, status codes).
@@ -138,7 +186,7 @@ cudaError_t launch_spectrum(const Plan& p, const void* in, int64_t in_stride, in
 // *sumsq (FP64, via the plan's reduction scratch when sumsq != nullptr).
 cudaError_t launch_image(const Plan& p, const void* in, int64_t in_stride, void* out,
                          int64_t out_stride, int S, const void* sub, double* sumsq,
-                         cudaStream_t s);
+                         cudaStream_t s, int groups = 0, double* group_sums = nullptr);
 // Contractions over the resident table.
 cudaError_t launch_contract_fwd(const Plan& p, const void* X, void* Y, int batch, cudaStream_t s);
 cudaError_t launch_contract_adj(const Plan& p, const void* D, void* Z, int batch, cudaStream_t s);
@@ -164,6 +212,9 @@ cudaError_t launch_dot(const Plan& p, const void* a, const void* b, int64_t n, d
                        cudaStream_t s);
 // Sums n per-block partials (in order, FP64) into *out (device).
 cudaError_t launch_partials_sum(const double* partials, int n, double* out, cudaStream_t s);
+// out[g] = sum of partials[g * per, (g + 1) * per) for g < groups (in order, FP64).
+cudaError_t launch_group_sums(const double* partials, int per, int groups, double* out,
+                              cudaStream_t s);
 // FISTA step; scal = {1/L, lambda/L}, beta_k = betas[*iter] (device memory).
 cudaError_t launch_fista_update(const Plan& p, void* y, void* xprev, const void* grad, int64_t n,
                                 const double* scal, const double* betas, const int* iter,

@@ -44,6 +44,16 @@ __global__ void __launch_bounds__(1024) k_sum_partials(const double* __restrict_
   if (threadIdx.x == 0) *out = s;
 }
 
+// One block per group: out[blockIdx.x] = sum of its `per` partials.
+__global__ void __launch_bounds__(256) k_group_sums(const double* __restrict__ partials, int per,
+                                                    double* __restrict__ out) {
+  const double* p = partials + (int64_t)blockIdx.x * per;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < per; i += 256) acc += p[i];
+  const double s = block_sum(acc);
+  if (threadIdx.x == 0) out[blockIdx.x] = s;
+}
+
 // x_k = max(y - g/L - lambda/L, 0) (prox of Eq. 14 after the gradient step of
 // Eq. 15); y <- x_k + beta_k (x_k - x_{k-1}); xprev <- x_k. The scalars 1/L,
 // lambda/L (scal) and beta_k = betas[*iter] are read from device memory so one
@@ -87,6 +97,12 @@ int grid_for(int64_t n, int cap) {
 
 cudaError_t launch_partials_sum(const double* partials, int n, double* out, cudaStream_t s) {
   k_sum_partials<<<1, 1024, 0, s>>>(partials, n, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_group_sums(const double* partials, int per, int groups, double* out,
+                              cudaStream_t s) {
+  k_group_sums<<<groups, 256, 0, s>>>(partials, per, out);
   return cudaGetLastError();
 }
 

@@ -39,7 +39,8 @@ EXPORTS = (
     "pat_plan_create", "pat_plan_create_kspace", "pat_plan_destroy", "pat_plan_info",
     "pat_last_error", "pat_forward", "pat_adjoint", "pat_gradient", "pat_power_norm",
     "pat_fista_solve", "pat_dot_f64", "pat_stage_spectrum", "pat_stage_image",
-    "pat_stage_contract", "pat_spectrum_noalloc",
+    "pat_stage_contract", "pat_spectrum_noalloc", "pat_plan_estimate", "pat_slot_load",
+    "pat_slot_move", "pat_slots_step", "pat_slot_read",
 )
 
 
@@ -114,6 +115,12 @@ def lib(build_if_missing: bool = True):
         "pat_stage_image": ([P, V, V, I, P], I),
         "pat_stage_contract": ([P, V, V, I, I, P], I),
         "pat_spectrum_noalloc": ([V, I, I, I, I, I, V, P], I),
+        "pat_plan_estimate": ([ctypes.POINTER(Geometry), I, ctypes.POINTER(ctypes.c_int64),
+                               ctypes.POINTER(ctypes.c_int64)], I),
+        "pat_slot_load": ([P, I, V, ctypes.c_double, ctypes.c_double, P], I),
+        "pat_slot_move": ([P, I, I, P], I),
+        "pat_slots_step": ([P, I, ctypes.POINTER(ctypes.c_int), P], I),
+        "pat_slot_read": ([P, I, V, D, P], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -311,6 +318,32 @@ class Plan:
         _check(lib().pat_dot_f64(self._h, _ptr(a), _ptr(b), n, ctypes.byref(out), _stream(stream)))
         return out.value
 
+    # ------------------------------------------------------------------ slots
+    def slot_load(self, slot: int, y, lam: float, L: float, stream=None) -> None:
+        """Loads one FISTA request (data y [nt][ny][nx]) into `slot`."""
+        self._check_dtype(y)
+        _check(lib().pat_slot_load(self._h, slot, _ptr(y), lam, L, _stream(stream)))
+
+    def slot_move(self, dst: int, src: int, stream=None) -> None:
+        _check(lib().pat_slot_move(self._h, dst, src, _stream(stream)))
+
+    def slots_step(self, n: int, stream=None) -> int:
+        """One FISTA iteration for slots [0, n); returns the kernel launches."""
+        k = ctypes.c_int(0)
+        _check(lib().pat_slots_step(self._h, n, ctypes.byref(k), _stream(stream)))
+        return k.value
+
+    def slot_read(self, slot: int, out=None, resid: bool = False, stream=None):
+        """Copies the slot's current x_k into `out` (allocated on the device if
+        None); returns (out, ||H y_k - d||^2 or None)."""
+        if out is None:
+            torch = _torch()
+            out = torch.empty((self.nz, self.ny, self.nx), dtype=self._torch_dtype(), device="cuda")
+        r2 = ctypes.c_double(0.0)
+        _check(lib().pat_slot_read(self._h, slot, _ptr(out), ctypes.byref(r2) if resid else None,
+                                   _stream(stream)))
+        return out, (r2.value if resid else None)
+
     # ------------------------------------------------------------------ stages
     def stage_spectrum(self, x, out=None, stream=None):
         """Zero-padded 2D real DFT of real [S][ny][nx] slices -> complex [S][px//2+1][py]."""
@@ -336,6 +369,18 @@ class Plan:
             out = self._empty_like_device((S, self.ny, self.nx), X)
         _check(lib().pat_stage_image(self._h, _ptr(X), _ptr(out), S, _stream(stream)))
         return out
+
+
+def plan_estimate(nx: int, ny: int, nz: int, nt: int, px: int | None = None, py: int | None = None,
+                  max_batch: int = 1, fp64: bool = False, real_table: bool = True):
+    """(table bytes, workspace bytes) a plan would take on the device."""
+    px = px if px is not None else _pow2_at_least(2 * nx)
+    py = py if py is not None else _pow2_at_least(2 * ny)
+    g = Geometry(nx, ny, nz, nt, px, py, max_batch, FLAG_FP64 if fp64 else 0)
+    tb, ws = ctypes.c_int64(0), ctypes.c_int64(0)
+    _check(lib().pat_plan_estimate(ctypes.byref(g), 1 if real_table else 0, ctypes.byref(tb),
+                                   ctypes.byref(ws)))
+    return tb.value, ws.value
 
 
 def spectrum_noalloc(x, px: int, py: int, out=None, stream=None):
