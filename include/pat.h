@@ -61,7 +61,13 @@ typedef enum {
 
 enum {
   PAT_FLAG_FP64 = 1,          /* table, workspace and arrays in double precision */
-  PAT_FLAG_FORCE_COMPLEX = 2  /* keep the complex table even when it is real     */
+  PAT_FLAG_FORCE_COMPLEX = 2, /* keep the complex table even when it is real     */
+  PAT_FLAG_BF16_SPLIT = 4     /* also build the split-BF16 tensor-core tables: calls
+                                 with batch >= 2 contract 16 volumes per table pass on
+                                 tcgen05 (BF16 hi/lo operands, FP32 accumulation).
+                                 Needs a real table, nz = 128, nt in {128, 256, 384, 512},
+                                 single precision; else pat_plan_create fails with
+                                 PAT_ERR_UNSUPPORTED. */
 };
 
 /* Grid of one plan.
@@ -114,6 +120,9 @@ typedef struct {
   int64_t workspace_bytes; /* device bytes of the plan's workspace */
   double table_max_abs;    /* max |Hh| seen while building the table */
   double table_max_imag;   /* max |Im Hh| seen while building the table */
+  int64_t tensor_table_bytes; /* device bytes of the split-BF16 tables (0 if not built) */
+  int32_t tensor_min_batch;   /* batches >= this use the tensor-core contraction (0: never) */
+  int32_t reserved;
 } pat_plan_info_t;
 
 /* FISTA settings (Eq. 12-14; Beck & Teboulle's constant-step scheme).
@@ -174,6 +183,15 @@ int pat_plan_estimate(const pat_geometry* g, int real_table, int64_t* table_byte
 
 /* Message of the last failure on the calling thread ("" if none). */
 const char* pat_last_error(void);
+
+/* Sets the smallest batch that uses the tensor-core contraction of a plan
+ * built with PAT_FLAG_BF16_SPLIT (default 2; 0 = always the CUDA-core path). */
+int pat_plan_set_tensor_batch(pat_plan* plan, int min_batch);
+
+/* Synchronises the device and reports whether any bounded device-side wait of
+ * the plan's kernels gave up since the last check (PAT_ERR_TIMEOUT; the flag
+ * is cleared), else PAT_OK. */
+int pat_plan_check(pat_plan* plan);
 
 /* --- operators ----------------------------------------------------------------- */
 

@@ -40,7 +40,8 @@ int validate(const pat_geometry* g) {
   if (g->px < 2 * g->nx - 1 || g->py < 2 * g->ny - 1)
     return fail(PAT_ERR_ARG, "padding too small for linear convolution: need px >= 2nx-1, py >= 2ny-1");
   if (g->max_batch < 1) return fail(PAT_ERR_ARG, "max_batch must be >= 1");
-  if (g->flags & ~(PAT_FLAG_FP64 | PAT_FLAG_FORCE_COMPLEX)) return fail(PAT_ERR_ARG, "unknown flags");
+  if (g->flags & ~(PAT_FLAG_FP64 | PAT_FLAG_FORCE_COMPLEX | PAT_FLAG_BF16_SPLIT))
+    return fail(PAT_ERR_ARG, "unknown flags");
   const int64_t smax = (int64_t)g->max_batch * std::max(g->nz, g->nt);
   if (smax > 65535) return fail(PAT_ERR_UNSUPPORTED, "max_batch * max(nz, nt) must be <= 65535");
   return PAT_OK;
@@ -79,6 +80,7 @@ void free_plan(pat_plan* pp) {
   void* bufs[] = {p.table, p.twx,    p.twy,     p.X,         p.Y,      p.T,       p.vol_a,
                   p.vol_b, p.vol_c,  p.dat_a,   p.dat_b,     p.red,    p.betas,   p.iter_dev,
                   p.r2_dev, x.io_obj[0], x.io_obj[1], x.io_dat, x.res, x.scal,
+                  p.tc_fwd, p.tc_adj, p.tc_err,
                   x.slots.t, x.slots.beta, x.slots.invL, x.slots.lamL, x.slots.r2, x.slots.k};
   for (void* b : bufs) cudaFree(b);
   if (x.cap) cudaStreamDestroy(x.cap);
@@ -187,6 +189,26 @@ int create_common(const pat_geometry* g, pat_plan** out, pat_plan** pp_out) {
     return rc;
   }
   *pp_out = pp;
+  return PAT_OK;
+}
+
+// Split-BF16 tensor-core tables (PAT_FLAG_BF16_SPLIT), from the real table.
+int build_tensor_tables(pat_plan* pp, int flags, cudaStream_t s) {
+  if (!(flags & PAT_FLAG_BF16_SPLIT)) return PAT_OK;
+  Plan& p = pp->p;
+  if (!tc_supported(p.L))
+    return fail(PAT_ERR_UNSUPPORTED,
+                "PAT_FLAG_BF16_SPLIT needs a real single-precision table, nz = 128 and nt a "
+                "multiple of 128 up to 512");
+  const size_t one = tc_table_bytes(p.L);
+  PAT_CUDA(cudaMalloc(&p.tc_fwd, one));
+  PAT_CUDA(cudaMalloc(&p.tc_adj, one));
+  PAT_CUDA(cudaMalloc(&p.tc_err, sizeof(int)));
+  PAT_CUDA(cudaMemsetAsync(p.tc_err, 0, sizeof(int), s));
+  PAT_CUDA(tc_build_tables(p, p.tc_fwd, p.tc_adj, s));
+  PAT_CUDA(cudaStreamSynchronize(s));
+  p.tc_bytes = 2 * one;
+  p.tc_min_batch = 2;
   return PAT_OK;
 }
 
@@ -382,6 +404,7 @@ int pat_plan_create(const pat_geometry* g, const void* table, pat_table_format f
   if (rc != PAT_OK) return rc;
   rc = build_table_from_source(pp->p, table, fmt, (g->flags & PAT_FLAG_FORCE_COMPLEX) != 0,
                                (cudaStream_t)stream);
+  if (rc == PAT_OK) rc = build_tensor_tables(pp, g->flags, (cudaStream_t)stream);
   if (rc != PAT_OK) {
     free_plan(pp);
     return rc;
@@ -404,6 +427,7 @@ int pat_plan_create_kspace(const pat_geometry* g, const pat_medium* m, pat_strea
   if (rc != PAT_OK) return rc;
   rc = build_table_kspace(pp->p, *m, (g->flags & PAT_FLAG_FORCE_COMPLEX) != 0,
                           (cudaStream_t)stream);
+  if (rc == PAT_OK) rc = build_tensor_tables(pp, g->flags, (cudaStream_t)stream);
   if (rc != PAT_OK) {
     free_plan(pp);
     return rc;
@@ -447,7 +471,33 @@ int pat_plan_info(const pat_plan* plan, pat_plan_info_t* info) {
   info->workspace_bytes = (int64_t)p.ws_bytes;
   info->table_max_abs = p.table_max_abs;
   info->table_max_imag = p.table_max_imag;
+  info->tensor_table_bytes = (int64_t)p.tc_bytes;
+  info->tensor_min_batch = p.tc_fwd ? p.tc_min_batch : 0;
+  info->reserved = 0;
   return PAT_OK;
+}
+
+int pat_plan_set_tensor_batch(pat_plan* plan, int min_batch) {
+  if (!plan || min_batch < 0) return fail(PAT_ERR_ARG, "plan is NULL or min_batch < 0");
+  if (!plan->p.tc_fwd && min_batch > 0)
+    return fail(PAT_ERR_UNSUPPORTED, "plan has no split-BF16 tables (PAT_FLAG_BF16_SPLIT)");
+  plan->p.tc_min_batch = min_batch;
+  return PAT_OK;
+}
+
+int pat_plan_check(pat_plan* plan) {
+  PAT_GUARD_BEGIN
+  if (!plan) return fail(PAT_ERR_ARG, "plan is NULL");
+  PAT_CUDA(cudaDeviceSynchronize());
+  if (!plan->p.tc_err) return PAT_OK;
+  int h = 0;
+  PAT_CUDA(cudaMemcpy(&h, plan->p.tc_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (h) {
+    PAT_CUDA(cudaMemset(plan->p.tc_err, 0, sizeof(int)));
+    return fail(PAT_ERR_TIMEOUT, "a bounded wait of the tensor-core contraction gave up");
+  }
+  return PAT_OK;
+  PAT_GUARD_END
 }
 
 int pat_forward(pat_plan* plan, const void* rho, void* d, int batch, pat_stream stream) {

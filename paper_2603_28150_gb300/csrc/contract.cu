@@ -251,12 +251,16 @@ cudaError_t adj_vb(const Plan& p, const void* D, void* Z, int batch, cudaStream_
 }  // namespace
 
 cudaError_t launch_contract_fwd(const Plan& p, const void* X, void* Y, int batch, cudaStream_t s) {
+  if (p.tc_fwd && p.tc_min_batch > 0 && batch >= p.tc_min_batch)
+    return tc_contract(p, p.tc_fwd, p.tc_adj, X, Y, batch, false, p.tc_err, s);
   if (p.L.fp64)
     return p.L.real ? fwd_vb<double, false>(p, X, Y, batch, s) : fwd_vb<double, true>(p, X, Y, batch, s);
   return p.L.real ? fwd_vb<float, false>(p, X, Y, batch, s) : fwd_vb<float, true>(p, X, Y, batch, s);
 }
 
 cudaError_t launch_contract_adj(const Plan& p, const void* D, void* Z, int batch, cudaStream_t s) {
+  if (p.tc_adj && p.tc_min_batch > 0 && batch >= p.tc_min_batch)
+    return tc_contract(p, p.tc_fwd, p.tc_adj, D, Z, batch, true, p.tc_err, s);
   if (p.L.fp64)
     return p.L.real ? adj_vb<double, false>(p, D, Z, batch, s) : adj_vb<double, true>(p, D, Z, batch, s);
   return p.L.real ? adj_vb<float, false>(p, D, Z, batch, s) : adj_vb<float, true>(p, D, Z, batch, s);

@@ -106,6 +106,12 @@ struct Plan {
   int r2_cap = 0;
   Graph* graphs = nullptr;
   size_t ws_bytes = 0;
+  // split-BF16 tensor-core tables (tc_contract.cu)
+  void* tc_fwd = nullptr;
+  void* tc_adj = nullptr;
+  size_t tc_bytes = 0;   // both directions
+  int* tc_err = nullptr; // device flag of timed-out waits
+  int tc_min_batch = 0;
 };
 
 constexpr int kReduceBlocks = 1024;  // max blocks of the FP64 reductions
@@ -187,9 +193,18 @@ cudaError_t launch_spectrum(const Plan& p, const void* in, int64_t in_stride, in
 cudaError_t launch_image(const Plan& p, const void* in, int64_t in_stride, void* out,
                          int64_t out_stride, int S, const void* sub, double* sumsq,
                          cudaStream_t s, int groups = 0, double* group_sums = nullptr);
-// Contractions over the resident table.
+// Contractions over the resident table (tensor cores when the plan has the
+// split tables and batch >= tc_min_batch).
 cudaError_t launch_contract_fwd(const Plan& p, const void* X, void* Y, int batch, cudaStream_t s);
 cudaError_t launch_contract_adj(const Plan& p, const void* D, void* Z, int batch, cudaStream_t s);
+
+// Split-BF16 tensor-core contraction (tc_contract.cu).
+bool tc_supported(const Layout& L);
+size_t tc_table_bytes(const Layout& L);  // one direction
+cudaError_t tc_build_tables(const Plan& p, void* fwd, void* adj, cudaStream_t s);
+cudaError_t tc_contract(const Plan& p, const void* tables_fwd, const void* tables_adj,
+                        const void* in, void* out, int batch, bool adjoint, int* err,
+                        cudaStream_t s);
 
 // Table construction (table.cu). Both allocate p.table and set the
 // representation (real or complex) of p.L.

@@ -1,0 +1,475 @@
+// Batched depth contraction on the tcgen05 tensor cores (Sec. 3.2, Eq. 16
+// term (ii)) for 16 volumes sharing one real (even-kernel) table:
+//   forward  Y_k (nt x 2B) = H_k (nt x nz) X_k (nz x 2B)            (Eq. 7)
+//   adjoint  Z_k (nz x 2B) = H_k^T (nz x nt) D_k (nt x 2B)          (Eq. 11)
+// per frequency bin k, with the 2B columns = real and imaginary parts of the
+// B = 16 volumes. Operands are split into BF16 hi + lo (h = hi + lo to ~2^-16
+// relative) and the product is hi.hi + hi.lo + lo.hi with FP32 accumulation in
+// tensor memory (the dropped lo.lo term is ~2^-16 of the others).
+//
+// Layout: the split table is stored per bin as 32 KB tiles of 128 x 128 BF16
+// in the no-swizzle K-major core-matrix layout (8 rows x 16 B per core
+// matrix; cores adjacent along K are 128 B apart, along M/N 2048 B apart), one
+// copy per direction (forward: rows t, K = z; adjoint: rows z, K = t chunks),
+// so each tile is one contiguous bulk copy. The X / D operand of a bin is
+// converted to the same layout in shared memory by all threads.
+//
+// Per CTA (persistent, one per SM, 128 threads): groups of G bins; thread 0
+// streams the group's table tiles through an S-slot mbarrier pipeline
+// (cp.async.bulk), issues the MMAs (M=128, N=32, K=16) and commits them to
+// the slot's "empty" barrier; after a group all four warps read the
+// accumulators with tcgen05.ld and write Y / Z (G consecutive bins per row).
+// Every wait is bounded: on timeout the kernel records an error, drains its
+// own copies, frees tensor memory and returns.
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "pat_internal.h"
+
+namespace pat {
+namespace tc {
+
+constexpr int kThreads = 128;
+constexpr int kVB = 16;                  // volumes per pass
+constexpr int kN = 2 * kVB;              // MMA N: re and im of each volume
+constexpr int kTile = 128;               // M rows and K columns per table tile
+constexpr int kTileBytes = kTile * kTile * 2;  // 32 KB of BF16
+constexpr int kLBO = 128;                // bytes between K-adjacent core matrices
+constexpr int kSBO = (kTile / 8) * 128;  // bytes between M/N-adjacent core matrices (2048)
+constexpr int kBBytes = kN * kTile * 2;  // one 32 x 128 B-operand chunk (8 KB)
+constexpr uint32_t kSpinLimit = 1u << 26;
+
+// -------------------------------------------------------------------- PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for the phase with the given parity; false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (uint32_t i = 0; i < kSpinLimit; ++i) {
+    if (mbar_test(bar, parity)) return true;
+    if (i > 64) __nanosleep(64);
+  }
+  return false;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+// Shared-memory matrix descriptor: no swizzle, K-major core matrices.
+__device__ __forceinline__ uint64_t smem_desc(const void* p) {
+  const uint64_t addr = smem_u32(p);
+  uint64_t d = 0;
+  d |= (addr >> 4) & 0x3FFFull;                // start address
+  d |= (uint64_t)((kLBO >> 4) & 0x3FFF) << 16;  // leading (K) byte offset
+  d |= (uint64_t)((kSBO >> 4) & 0x3FFF) << 32;  // stride (M/N) byte offset
+  d |= 1ull << 46;                             // descriptor version for tcgen05
+  return d;                                    // base offset 0, layout type 0 (no swizzle)
+}
+// Instruction descriptor: BF16 x BF16 -> FP32, A and B K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+// 32 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Byte offset of element (row, k) inside a no-swizzle K-major tile.
+__host__ __device__ __forceinline__ uint32_t core_off(int row, int k) {
+  return (uint32_t)((row >> 3) * kSBO + (k >> 3) * kLBO + (row & 7) * 16 + (k & 7) * 2);
+}
+
+// hi = bf16(v), lo = bf16(v - hi), packed pairs for 8 consecutive K.
+__device__ __forceinline__ void split8(const float* v, uint4* hi, uint4* lo) {
+  uint32_t h[4], l[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const __nv_bfloat16 h0 = __float2bfloat16_rn(v[2 * i]), h1 = __float2bfloat16_rn(v[2 * i + 1]);
+    const __nv_bfloat16 l0 = __float2bfloat16_rn(v[2 * i] - __bfloat162float(h0));
+    const __nv_bfloat16 l1 = __float2bfloat16_rn(v[2 * i + 1] - __bfloat162float(h1));
+    h[i] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+    l[i] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+  }
+  *hi = make_uint4(h[0], h[1], h[2], h[3]);
+  *lo = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+struct Params {
+  const unsigned char* table;  // split tiles of this direction
+  const float2* in;            // X [b][nz][Kpad] (fwd) or D [b][nt][Kpad] (adj)
+  float2* out;                 // Y [b][nt][Kpad] (fwd) or Z [b][nz][Kpad] (adj)
+  int64_t K, Kpad;
+  int nz, nt, batch;
+  int rows_out;      // nt (fwd) or nz (adj)
+  int rows_in;       // nz (fwd) or nt (adj)
+  int mtiles;        // output row tiles: nt/128 (fwd) or 1 (adj)
+  int kchunks;       // K chunks of 128: 1 (fwd) or nt/128 (adj)
+  int* err;          // set to 1 on a timed-out wait
+};
+
+// G bins per group, S pipeline slots.
+template <int G, int S>
+__global__ void __launch_bounds__(kThreads, 1) k_tc_contract(Params p) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  // [S table slots][G * kchunks * 2 B chunks][barriers]
+  unsigned char* slots = smem;
+  unsigned char* bops = smem + (size_t)S * kTileBytes;
+  const int kc_n = p.kchunks;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(bops + (size_t)G * kc_n * 2 * kBBytes);
+  uint64_t* full = bars;          // [S]
+  uint64_t* empty = bars + S;     // [S]
+  uint64_t* accb = bars + 2 * S;  // [1] accumulators of a group complete
+  uint64_t* drainb = accb + 1;    // [1] used only when aborting
+  uint32_t* tmem_base_s = reinterpret_cast<uint32_t*>(bars + 2 * S + 2);
+  volatile int* abort_s = reinterpret_cast<volatile int*>(tmem_base_s + 1);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t ngroups = (p.K + G - 1) / G;
+  const int tiles_per_bin = p.mtiles * kc_n * 2;
+  const int tiles_per_group = G * tiles_per_bin;
+  // this CTA's groups: blockIdx.x, blockIdx.x + gridDim.x, ...
+  const int64_t my_groups =
+      blockIdx.x < ngroups ? (ngroups - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int64_t total_tiles = my_groups * tiles_per_group;
+  constexpr int kCols = 512;
+
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(accb, 1);
+    mbar_init(drainb, 1);
+    *abort_s = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_base_s)),
+                 "r"(kCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_base_s;
+  constexpr uint32_t idesc = idesc_bf16(kTile, kN);
+
+  // global tile j of this CTA -> (group, bin in group, row tile, K chunk, part)
+  auto tile_src = [&](int64_t j) -> const unsigned char* {
+    const int64_t gi = j / tiles_per_group;
+    const int r = (int)(j % tiles_per_group);
+    const int g = r / tiles_per_bin, rr = r % tiles_per_bin;
+    const int64_t k = (blockIdx.x + gi * gridDim.x) * G + g;
+    const int64_t kk = k < p.K ? k : p.K - 1;  // ragged last group: any valid tile
+    return p.table + ((kk * tiles_per_bin) + rr) * (int64_t)kTileBytes;
+  };
+  int64_t issued = 0, consumed = 0;
+  auto issue = [&](int64_t j) -> bool {
+    const int s = (int)(j % S);
+    if (j >= S && !mbar_wait(&empty[s], (uint32_t)(((j / S) - 1) & 1))) return false;
+    mbar_arrive_expect_tx(&full[s], kTileBytes);
+    bulk_g2s(slots + (size_t)s * kTileBytes, tile_src(j), kTileBytes, &full[s]);
+    return true;
+  };
+  if (tid == 0) {
+    while (issued < total_tiles && issued < S) {
+      if (!issue(issued)) {
+        *abort_s = 1;
+        break;
+      }
+      ++issued;
+    }
+  }
+
+  for (int64_t gi = 0; gi < my_groups && !*abort_s; ++gi) {
+    const int64_t k0 = (blockIdx.x + gi * gridDim.x) * G;
+    // ---- B operands of the group's bins: complex64 -> BF16 hi / lo, K-major
+    // chunk (g, kc, part) at bops + ((g * kc_n + kc) * 2 + part) * kBBytes;
+    // rows n = b (real part) and kVB + b (imaginary part), K = input row.
+    const int octs = p.rows_in / 8;
+    for (int it = tid; it < kVB * octs; it += kThreads) {
+      const int b = it / octs, o = it % octs;
+      float re[G][8], im[G][8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int row = o * 8 + q;
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+          float2 v = make_float2(0.f, 0.f);
+          if (b < p.batch && k0 + g < p.K)
+            v = p.in[((int64_t)b * p.rows_in + row) * p.Kpad + k0 + g];
+          re[g][q] = v.x;
+          im[g][q] = v.y;
+        }
+      }
+      const int kc = (o * 8) / kTile, kin = (o * 8) % kTile;
+#pragma unroll
+      for (int g = 0; g < G; ++g) {
+        unsigned char* base = bops + (size_t)((g * kc_n + kc) * 2) * kBBytes;
+        uint4 h, l;
+        split8(re[g], &h, &l);
+        *reinterpret_cast<uint4*>(base + core_off(b, kin)) = h;
+        *reinterpret_cast<uint4*>(base + kBBytes + core_off(b, kin)) = l;
+        split8(im[g], &h, &l);
+        *reinterpret_cast<uint4*>(base + core_off(kVB + b, kin)) = h;
+        *reinterpret_cast<uint4*>(base + kBBytes + core_off(kVB + b, kin)) = l;
+      }
+    }
+    fence_proxy_async();
+    __syncthreads();
+
+    // ---- MMAs of the group (thread 0), table tiles streamed through the slots
+    if (tid == 0) {
+      tc_fence_after();
+      for (int r = 0; r < tiles_per_group; ++r) {
+        const int64_t j = gi * tiles_per_group + r;
+        const int s = (int)(j % S);
+        if (!mbar_wait(&full[s], (uint32_t)((j / S) & 1))) {
+          *abort_s = 1;
+          break;
+        }
+        tc_fence_after();
+        const int g = r / tiles_per_bin, rr = r % tiles_per_bin;
+        const int part = rr & 1, kc = (rr >> 1) % kc_n, mt = (rr >> 1) / kc_n;
+        const unsigned char* a = slots + (size_t)s * kTileBytes;
+        const unsigned char* bh = bops + (size_t)((g * kc_n + kc) * 2) * kBBytes;
+        const unsigned char* bl = bh + kBBytes;
+        const uint32_t d = tmem + (uint32_t)((g * p.mtiles + mt) * kN);
+#pragma unroll
+        for (int ks = 0; ks < kTile / 16; ++ks) {
+          const uint32_t off = ks * 2 * kLBO;
+          const uint64_t ad = smem_desc(a + off);
+          // hi tile: hi.hi and hi.lo; lo tile: lo.hi
+          const uint32_t first = (part == 0 && kc == 0 && ks == 0) ? 0u : 1u;
+          mma_bf16(d, ad, smem_desc(bh + off), idesc, first);
+          if (part == 0) mma_bf16(d, ad, smem_desc(bl + off), idesc, 1u);
+        }
+        mma_commit(&empty[s]);
+        ++consumed;
+        if (issued < total_tiles) {
+          if (!issue(issued)) {
+            *abort_s = 1;
+            break;
+          }
+          ++issued;
+        }
+      }
+      mma_commit(accb);
+    }
+    // ---- epilogue: accumulators -> Y / Z rows of this warp's TMEM lanes
+    // warp-uniform, since tcgen05.ld below is a warp-collective instruction
+    const bool ok = __all_sync(0xffffffffu, mbar_wait(accb, (uint32_t)(gi & 1)));
+    if (!ok) *abort_s = 1;
+    tc_fence_after();
+    __syncwarp();
+    if (ok) {
+      for (int mt = 0; mt < p.mtiles; ++mt) {
+        const int row = mt * kTile + warp * 32 + lane;
+        float v[G][kN];
+#pragma unroll
+        for (int g = 0; g < G; ++g)
+          tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)((g * p.mtiles + mt) * kN),
+                    v[g]);
+        if (row < p.rows_out) {
+          for (int b = 0; b < p.batch && b < kVB; ++b) {
+            float2* o = p.out + ((int64_t)b * p.rows_out + row) * p.Kpad + k0;
+#pragma unroll
+            for (int g = 0; g < G; ++g)
+              if (k0 + g < p.K) o[g] = make_float2(v[g][b], v[g][kVB + b]);
+          }
+        }
+      }
+    }
+    tc_fence_before();
+    __syncthreads();
+  }
+
+  // ---- teardown (also after a timeout): drain our copies, free tensor memory
+  if (tid == 0 && *abort_s) {
+    atomicExch(p.err, 1);
+    for (int64_t j = consumed; j < issued; ++j) mbar_wait(&full[j % S], (uint32_t)((j / S) & 1));
+    mma_commit(drainb);  // arrives once every MMA issued so far has completed
+    mbar_wait(drainb, 0);
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols)
+                 : "memory");
+}
+
+template <int G, int S>
+size_t smem_for(int kchunks) {
+  return (size_t)S * kTileBytes + (size_t)G * kchunks * 2 * kBBytes + 8 * (2 * S + 2) + 16;
+}
+
+// Forward-direction tile of bin k, row tile mt (t rows), part, from the real
+// blocked FP32 table; adjoint tile of bin k, K chunk kc (t columns), part.
+__global__ void k_split_tables(const float* __restrict__ table, int nz, int nt, int nzg,
+                               int64_t K, unsigned char* __restrict__ fwd,
+                               unsigned char* __restrict__ adj) {
+  const int64_t n = K * nt * nz;
+  const int mtiles = nt / kTile;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int z = (int)(i % nz);
+    const int t = (int)((i / nz) % nt);
+    const int64_t k = i / ((int64_t)nz * nt);
+    const int64_t kb = k >> 5, l = k & 31;
+    const float h = table[(((kb * nt + t) * nzg + z / 4) * 32 + l) * 4 + z % 4];
+    const __nv_bfloat16 hi = __float2bfloat16_rn(h);
+    const __nv_bfloat16 lo = __float2bfloat16_rn(h - __bfloat162float(hi));
+    // forward: tile (k, mt = t / 128), rows t % 128, K = z
+    {
+      const int64_t tb = (k * mtiles + t / kTile) * 2;
+      const uint32_t off = core_off(t % kTile, z);
+      *reinterpret_cast<__nv_bfloat16*>(fwd + tb * kTileBytes + off) = hi;
+      *reinterpret_cast<__nv_bfloat16*>(fwd + (tb + 1) * kTileBytes + off) = lo;
+    }
+    // adjoint: tile (k, kc = t / 128), rows z, K = t % 128
+    {
+      const int64_t tb = (k * mtiles + t / kTile) * 2;
+      const uint32_t off = core_off(z, t % kTile);
+      *reinterpret_cast<__nv_bfloat16*>(adj + tb * kTileBytes + off) = hi;
+      *reinterpret_cast<__nv_bfloat16*>(adj + (tb + 1) * kTileBytes + off) = lo;
+    }
+  }
+}
+
+}  // namespace tc
+
+bool tc_supported(const Layout& L) {
+  return !L.fp64 && L.real && L.nz == tc::kTile && L.nt % tc::kTile == 0 && L.nt <= 4 * tc::kTile;
+}
+
+size_t tc_table_bytes(const Layout& L) {
+  return (size_t)L.K * (L.nt / tc::kTile) * 2 * tc::kTileBytes;  // one direction
+}
+
+cudaError_t tc_build_tables(const Plan& p, void* fwd, void* adj, cudaStream_t s) {
+  const Layout& L = p.L;
+  int64_t n = L.K * L.nt * L.nz;
+  int64_t g = (n + 255) / 256;
+  if (g > 152 * 64) g = 152 * 64;
+  tc::k_split_tables<<<(int)g, 256, 0, s>>>(static_cast<const float*>(p.table), L.nz, L.nt,
+                                            L.nzg, L.K, static_cast<unsigned char*>(fwd),
+                                            static_cast<unsigned char*>(adj));
+  return cudaGetLastError();
+}
+
+// Forward (adjoint = false) or adjoint contraction of `batch` volumes in
+// passes of 16 through the tensor cores.
+cudaError_t tc_contract(const Plan& p, const void* tables_fwd, const void* tables_adj,
+                        const void* in, void* out, int batch, bool adjoint, int* err,
+                        cudaStream_t s) {
+  const Layout& L = p.L;
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  for (int b0 = 0; b0 < batch; b0 += tc::kVB) {
+    tc::Params q;
+    q.K = L.K;
+    q.Kpad = L.Kpad;
+    q.nz = L.nz;
+    q.nt = L.nt;
+    q.batch = std::min(tc::kVB, batch - b0);
+    q.err = err;
+    if (!adjoint) {
+      q.table = static_cast<const unsigned char*>(tables_fwd);
+      q.in = static_cast<const float2*>(in) + (int64_t)b0 * L.nz * L.Kpad;
+      q.out = static_cast<float2*>(out) + (int64_t)b0 * L.nt * L.Kpad;
+      q.rows_out = L.nt;
+      q.rows_in = L.nz;
+      q.mtiles = L.nt / tc::kTile;
+      q.kchunks = 1;
+      constexpr int G = 4, S = 4;
+      const size_t smem = tc::smem_for<G, S>(1);
+      e = cudaFuncSetAttribute((const void*)tc::k_tc_contract<G, S>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      const int64_t groups = (L.K + G - 1) / G;
+      const int grid = (int)std::min<int64_t>(groups, sms);
+      tc::k_tc_contract<G, S><<<grid, tc::kThreads, smem, s>>>(q);
+    } else {
+      q.table = static_cast<const unsigned char*>(tables_adj);
+      q.in = static_cast<const float2*>(in) + (int64_t)b0 * L.nt * L.Kpad;
+      q.out = static_cast<float2*>(out) + (int64_t)b0 * L.nz * L.Kpad;
+      q.rows_out = L.nz;
+      q.rows_in = L.nt;
+      q.mtiles = 1;
+      q.kchunks = L.nt / tc::kTile;
+      constexpr int G = 2, S = 3;
+      const size_t smem = tc::smem_for<G, S>(q.kchunks);
+      e = cudaFuncSetAttribute((const void*)tc::k_tc_contract<G, S>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      const int64_t groups = (L.K + G - 1) / G;
+      const int grid = (int)std::min<int64_t>(groups, sms);
+      tc::k_tc_contract<G, S><<<grid, tc::kThreads, smem, s>>>(q);
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace pat

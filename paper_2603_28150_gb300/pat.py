@@ -28,6 +28,7 @@ PAT_ERR_UNSUPPORTED = -5
 
 FLAG_FP64 = 1
 FLAG_FORCE_COMPLEX = 2
+FLAG_BF16_SPLIT = 4
 
 TABLE_SPATIAL_F64 = 0
 TABLE_SPATIAL_F32 = 1
@@ -40,7 +41,8 @@ EXPORTS = (
     "pat_last_error", "pat_forward", "pat_adjoint", "pat_gradient", "pat_power_norm",
     "pat_fista_solve", "pat_dot_f64", "pat_stage_spectrum", "pat_stage_image",
     "pat_stage_contract", "pat_spectrum_noalloc", "pat_plan_estimate", "pat_slot_load",
-    "pat_slot_move", "pat_slots_step", "pat_slot_read",
+    "pat_slot_move", "pat_slots_step", "pat_slot_read", "pat_plan_set_tensor_batch",
+    "pat_plan_check",
 )
 
 
@@ -67,7 +69,8 @@ class PlanInfo(ctypes.Structure):
                 ("bins", ctypes.c_int64), ("bins_padded", ctypes.c_int64),
                 ("table_bytes", ctypes.c_int64),
                 ("workspace_bytes", ctypes.c_int64), ("table_max_abs", ctypes.c_double),
-                ("table_max_imag", ctypes.c_double)]
+                ("table_max_imag", ctypes.c_double), ("tensor_table_bytes", ctypes.c_int64),
+                ("tensor_min_batch", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class FistaParams(ctypes.Structure):
@@ -121,6 +124,8 @@ def lib(build_if_missing: bool = True):
         "pat_slot_move": ([P, I, I, P], I),
         "pat_slots_step": ([P, I, ctypes.POINTER(ctypes.c_int), P], I),
         "pat_slot_read": ([P, I, V, D, P], I),
+        "pat_plan_set_tensor_batch": ([P, I], I),
+        "pat_plan_check": ([P], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -183,14 +188,15 @@ class Plan:
     def __init__(self, nx: int, ny: int, nz: int, nt: int, px: int | None = None,
                  py: int | None = None, max_batch: int = 1, fp64: bool = False,
                  force_complex: bool = False, table=None, medium: Medium | None = None,
-                 stream=None):
+                 bf16_split: bool = False, stream=None):
         L = lib()
         self.nx, self.ny, self.nz, self.nt = nx, ny, nz, nt
         self.px = px if px is not None else _pow2_at_least(2 * nx)
         self.py = py if py is not None else _pow2_at_least(2 * ny)
         self.max_batch = max_batch
         self.fp64 = fp64
-        flags = (FLAG_FP64 if fp64 else 0) | (FLAG_FORCE_COMPLEX if force_complex else 0)
+        flags = ((FLAG_FP64 if fp64 else 0) | (FLAG_FORCE_COMPLEX if force_complex else 0)
+                 | (FLAG_BF16_SPLIT if bf16_split else 0))
         self._geom = Geometry(nx, ny, nz, nt, self.px, self.py, max_batch, flags)
         self._h = ctypes.c_void_p(0)
         s = _stream(stream)
@@ -214,6 +220,14 @@ class Plan:
         inf = PlanInfo()
         _check(lib().pat_plan_info(self._h, ctypes.byref(inf)))
         return {k: getattr(inf, k) for k, _ in PlanInfo._fields_}
+
+    def set_tensor_batch(self, min_batch: int) -> None:
+        """Batches >= min_batch use the tensor-core contraction (0 = never)."""
+        _check(lib().pat_plan_set_tensor_batch(self._h, min_batch))
+
+    def check(self) -> None:
+        """Raises PatError(PAT_ERR_TIMEOUT) if a bounded device wait gave up."""
+        _check(lib().pat_plan_check(self._h))
 
     def close(self) -> None:
         if self._h and self._h.value:
