@@ -62,6 +62,8 @@ typedef enum {
 enum {
   PAT_FLAG_FP64 = 1,          /* table, workspace and arrays in double precision */
   PAT_FLAG_FORCE_COMPLEX = 2, /* keep the complex table even when it is real     */
+  PAT_FLAG_NO_FOLD = 8,       /* keep one table row per bin even when the spectra have
+                                 the D4 symmetry of radially symmetric kernels */
   PAT_FLAG_BF16_SPLIT = 4     /* also build the split-BF16 tensor-core tables: calls
                                  with batch >= 2 contract 16 volumes per table pass on
                                  tcgen05 (BF16 hi/lo operands, FP32 accumulation).
@@ -122,7 +124,8 @@ typedef struct {
   double table_max_imag;   /* max |Im Hh| seen while building the table */
   int64_t tensor_table_bytes; /* device bytes of the split-BF16 tables (0 if not built) */
   int32_t tensor_min_batch;   /* batches >= this use the tensor-core contraction (0: never) */
-  int32_t reserved;
+  int32_t folded;             /* 1: one table row per D4 representative {|kx|, |ky|} */
+  int64_t table_rows;         /* stored frequency rows: representatives if folded, else bins */
 } pat_plan_info_t;
 
 /* FISTA settings (Eq. 12-14; Beck & Teboulle's constant-step scheme).
@@ -160,7 +163,12 @@ typedef struct {
  * (kernels even under (x, y) -> (-x, -y), e.g. the radially symmetric
  * kernels of Eq. 5) and PAT_FLAG_FORCE_COMPLEX is not set, the imaginary part
  * is dropped and the real-spectrum contraction is used (half the bytes).
- * Synchronises `stream` before returning. Table source: Sec. 3.2. */
+ * A real table on a square padded grid whose spectra also agree (to 1e-6 of
+ * max |Hh|) under ky -> -ky and kx <-> ky -- kernels with the radial symmetry
+ * of Eq. 5 -- is stored once per representative {|kx|, |ky|} ("folded", ~4x
+ * fewer bytes; the bins of a representative share its row) unless
+ * PAT_FLAG_NO_FOLD is set. Synchronises `stream` before returning.
+ * Table source: Sec. 3.2. */
 int pat_plan_create(const pat_geometry* g, const void* table, pat_table_format fmt,
                     pat_stream stream, pat_plan** out);
 

@@ -40,7 +40,7 @@ int validate(const pat_geometry* g) {
   if (g->px < 2 * g->nx - 1 || g->py < 2 * g->ny - 1)
     return fail(PAT_ERR_ARG, "padding too small for linear convolution: need px >= 2nx-1, py >= 2ny-1");
   if (g->max_batch < 1) return fail(PAT_ERR_ARG, "max_batch must be >= 1");
-  if (g->flags & ~(PAT_FLAG_FP64 | PAT_FLAG_FORCE_COMPLEX | PAT_FLAG_BF16_SPLIT))
+  if (g->flags & ~(PAT_FLAG_FP64 | PAT_FLAG_FORCE_COMPLEX | PAT_FLAG_BF16_SPLIT | PAT_FLAG_NO_FOLD))
     return fail(PAT_ERR_ARG, "unknown flags");
   const int64_t smax = (int64_t)g->max_batch * std::max(g->nz, g->nt);
   if (smax > 65535) return fail(PAT_ERR_UNSUPPORTED, "max_batch * max(nz, nt) must be <= 65535");
@@ -80,7 +80,7 @@ void free_plan(pat_plan* pp) {
   void* bufs[] = {p.table, p.twx,    p.twy,     p.X,         p.Y,      p.T,       p.vol_a,
                   p.vol_b, p.vol_c,  p.dat_a,   p.dat_b,     p.red,    p.betas,   p.iter_dev,
                   p.r2_dev, x.io_obj[0], x.io_obj[1], x.io_dat, x.res, x.scal,
-                  p.tc_fwd, p.tc_adj, p.tc_err,
+                  p.tc_fwd, p.tc_adj, p.tc_err, p.fold_members, p.fold_rep,
                   x.slots.t, x.slots.beta, x.slots.invL, x.slots.lamL, x.slots.r2, x.slots.k};
   for (void* b : bufs) cudaFree(b);
   if (x.cap) cudaStreamDestroy(x.cap);
@@ -403,7 +403,7 @@ int pat_plan_create(const pat_geometry* g, const void* table, pat_table_format f
   int rc = create_common(g, out, &pp);
   if (rc != PAT_OK) return rc;
   rc = build_table_from_source(pp->p, table, fmt, (g->flags & PAT_FLAG_FORCE_COMPLEX) != 0,
-                               (cudaStream_t)stream);
+                               (g->flags & PAT_FLAG_NO_FOLD) == 0, (cudaStream_t)stream);
   if (rc == PAT_OK) rc = build_tensor_tables(pp, g->flags, (cudaStream_t)stream);
   if (rc != PAT_OK) {
     free_plan(pp);
@@ -426,7 +426,7 @@ int pat_plan_create_kspace(const pat_geometry* g, const pat_medium* m, pat_strea
   int rc = create_common(g, out, &pp);
   if (rc != PAT_OK) return rc;
   rc = build_table_kspace(pp->p, *m, (g->flags & PAT_FLAG_FORCE_COMPLEX) != 0,
-                          (cudaStream_t)stream);
+                          (g->flags & PAT_FLAG_NO_FOLD) == 0, (cudaStream_t)stream);
   if (rc == PAT_OK) rc = build_tensor_tables(pp, g->flags, (cudaStream_t)stream);
   if (rc != PAT_OK) {
     free_plan(pp);
@@ -455,6 +455,8 @@ int pat_plan_estimate(const pat_geometry* g, int real_table, int64_t* table_byte
   Layout L = make_layout(g);
   set_representation(L, real_table != 0);
   *table_bytes = (int64_t)L.table_bytes;
+  if ((g->flags & PAT_FLAG_BF16_SPLIT) && tc_supported(L))
+    *table_bytes += 2 * (int64_t)tc_table_bytes(L);
   *workspace = workspace_bytes(L);
   return PAT_OK;
   PAT_GUARD_END
@@ -473,7 +475,8 @@ int pat_plan_info(const pat_plan* plan, pat_plan_info_t* info) {
   info->table_max_imag = p.table_max_imag;
   info->tensor_table_bytes = (int64_t)p.tc_bytes;
   info->tensor_min_batch = p.tc_fwd ? p.tc_min_batch : 0;
-  info->reserved = 0;
+  info->folded = p.L.fold ? 1 : 0;
+  info->table_rows = p.L.fold ? p.L.U : p.L.K;
   return PAT_OK;
 }
 

@@ -194,6 +194,181 @@ __global__ void __launch_bounds__(kWarps * 32, (sizeof(R) == 4 && !CPLX && VB ==
   }
 }
 
+// ---- D4-folded real tables ----------------------------------------------------
+// A CTA owns 32 representatives {|kx|, |ky|} (one per lane); the table row of
+// a representative is read once and applied to each of its (up to 4) bins,
+// whose bin indices come from `members` (-1 = absent). One volume per
+// blockIdx.y; every volume streams the (folded) table once.
+constexpr int kRT = 4;   // forward: time samples per register block
+constexpr int kTC = 32;  // adjoint: time samples per shared D tile
+
+// Forward: warp w takes the time blocks w, w + 8, ... of kRT samples; per
+// z-group it loads kRT table float4s and the 4 members' X from shared memory.
+__global__ void __launch_bounds__(kWarps * 32, 2)
+    k_fold_fwd(const float4* __restrict__ table, const int4* __restrict__ members,
+               const cx<float>* __restrict__ X, cx<float>* __restrict__ Y, int nz, int nt,
+               int nzg, int64_t U, int64_t Kpad) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<float>* xs = reinterpret_cast<cx<float>*>(smem_raw);  // [4][nzp][32]
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t ub = blockIdx.x, u = ub * 32 + lane;
+  const int b = blockIdx.y, nzp = nzg * 4;
+  const int4 mem = u < U ? members[u] : make_int4(-1, -1, -1, -1);
+  const int bins[4] = {mem.x, mem.y, mem.z, mem.w};
+  const cx<float>* Xb = X + (int64_t)b * nz * Kpad;
+  for (int z = warp; z < nzp; z += kWarps) {
+#pragma unroll
+    for (int m = 0; m < 4; ++m)
+      xs[(m * nzp + z) * 32 + lane] =
+          (bins[m] >= 0 && z < nz) ? Xb[(int64_t)z * Kpad + bins[m]] : mk<float>(0.f, 0.f);
+  }
+  __syncthreads();
+  const float4* tb = table + ub * nt * (int64_t)nzg * 32 + lane;
+  for (int t0 = warp * kRT; t0 < nt; t0 += kWarps * kRT) {
+    cx<float> acc[kRT][4];
+#pragma unroll
+    for (int r = 0; r < kRT; ++r)
+#pragma unroll
+      for (int m = 0; m < 4; ++m) acc[r][m] = mk<float>(0.f, 0.f);
+#pragma unroll 2
+    for (int g = 0; g < nzg; ++g) {
+      float hv[kRT][4];
+#pragma unroll
+      for (int r = 0; r < kRT; ++r) {
+        float4 h = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (t0 + r < nt) h = ld_stream(tb + ((int64_t)(t0 + r) * nzg + g) * 32);
+        hv[r][0] = h.x;
+        hv[r][1] = h.y;
+        hv[r][2] = h.z;
+        hv[r][3] = h.w;
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        cx<float> x[4];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) x[m] = xs[(m * nzp + g * 4 + q) * 32 + lane];
+#pragma unroll
+        for (int r = 0; r < kRT; ++r)
+#pragma unroll
+          for (int m = 0; m < 4; ++m) mac(acc[r][m], hv[r][q], x[m]);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < kRT; ++r) {
+      const int t = t0 + r;
+      if (t >= nt) break;
+#pragma unroll
+      for (int m = 0; m < 4; ++m)
+        if (bins[m] >= 0) Y[((int64_t)b * nt + t) * Kpad + bins[m]] = acc[r][m];
+    }
+  }
+}
+
+// Adjoint: warp w of z-chunk c owns z-groups c*8*GPW + w + j*8; the 4 members'
+// D values of kTC samples are staged in shared memory and reused by all warps.
+template <int GPW>
+__global__ void __launch_bounds__(kWarps * 32, 2)
+    k_fold_adj(const float4* __restrict__ table, const int4* __restrict__ members,
+               const cx<float>* __restrict__ D, cx<float>* __restrict__ Z, int nz, int nt,
+               int nzg, int64_t U, int64_t Kpad) {
+  __shared__ cx<float> ds[kTC][4][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t ub = blockIdx.x, u = ub * 32 + lane;
+  const int b = blockIdx.y;
+  const int gbase = blockIdx.z * kWarps * GPW + warp;
+  const int4 mem = u < U ? members[u] : make_int4(-1, -1, -1, -1);
+  const int bins[4] = {mem.x, mem.y, mem.z, mem.w};
+  const cx<float>* Db = D + (int64_t)b * nt * Kpad;
+  const float4* tb = table + ub * nt * (int64_t)nzg * 32 + lane;
+  cx<float> acc[GPW][4][4];
+#pragma unroll
+  for (int j = 0; j < GPW; ++j)
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int m = 0; m < 4; ++m) acc[j][q][m] = mk<float>(0.f, 0.f);
+  for (int t0 = 0; t0 < nt; t0 += kTC) {
+    __syncthreads();
+    for (int tt = warp; tt < kTC; tt += kWarps) {
+      const int t = t0 + tt;
+#pragma unroll
+      for (int m = 0; m < 4; ++m)
+        ds[tt][m][lane] =
+            (bins[m] >= 0 && t < nt) ? Db[(int64_t)t * Kpad + bins[m]] : mk<float>(0.f, 0.f);
+    }
+    __syncthreads();
+    const int tn = min(kTC, nt - t0);
+    // 4 samples per step: their GPW x 4 table loads are issued together
+    for (int tt = 0; tt < tn; tt += 4) {
+      float4 h[4][GPW];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int j = 0; j < GPW; ++j) {
+          const int g = gbase + j * kWarps;
+          h[r][j] = (g < nzg && tt + r < tn)
+                        ? ld_stream(tb + ((int64_t)(t0 + tt + r) * nzg + g) * 32)
+                        : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        cx<float> d[4];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) d[m] = ds[(tt + r) & (kTC - 1)][m][lane];
+#pragma unroll
+        for (int j = 0; j < GPW; ++j) {
+          const float hq[4] = {h[r][j].x, h[r][j].y, h[r][j].z, h[r][j].w};
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int m = 0; m < 4; ++m) mac(acc[j][q][m], hq[q], d[m]);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < GPW; ++j) {
+    const int g = gbase + j * kWarps;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int z = g * 4 + q;
+      if (g < nzg && z < nz) {
+#pragma unroll
+        for (int m = 0; m < 4; ++m)
+          if (bins[m] >= 0) Z[((int64_t)b * nz + z) * Kpad + bins[m]] = acc[j][q][m];
+      }
+    }
+  }
+}
+
+cudaError_t fold_fwd(const Plan& p, const void* X, void* Y, int batch, cudaStream_t s) {
+  const Layout& L = p.L;
+  const size_t smem = sizeof(cx<float>) * 4 * (size_t)L.nzg * 4 * 32;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute((const void*)k_fold_fwd,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  dim3 grid((unsigned)L.nub, (unsigned)batch);
+  k_fold_fwd<<<grid, kWarps * 32, smem, s>>>(
+      static_cast<const float4*>(p.table), reinterpret_cast<const int4*>(p.fold_members),
+      static_cast<const cx<float>*>(X), static_cast<cx<float>*>(Y), L.nz, L.nt, L.nzg, L.U,
+      L.Kpad);
+  return cudaGetLastError();
+}
+
+cudaError_t fold_adj(const Plan& p, const void* D, void* Z, int batch, cudaStream_t s) {
+  const Layout& L = p.L;
+  constexpr int GPW = 2;
+  dim3 grid((unsigned)L.nub, (unsigned)batch,
+            (unsigned)((L.nzg + kWarps * GPW - 1) / (kWarps * GPW)));
+  k_fold_adj<GPW><<<grid, kWarps * 32, 0, s>>>(
+      static_cast<const float4*>(p.table), reinterpret_cast<const int4*>(p.fold_members),
+      static_cast<const cx<float>*>(D), static_cast<cx<float>*>(Z), L.nz, L.nt, L.nzg, L.U,
+      L.Kpad);
+  return cudaGetLastError();
+}
+
 template <typename R, bool CPLX, int VB>
 cudaError_t fwd_t(const Plan& p, const void* X, void* Y, int batch, cudaStream_t s) {
   const Layout& L = p.L;
@@ -253,6 +428,7 @@ cudaError_t adj_vb(const Plan& p, const void* D, void* Z, int batch, cudaStream_
 cudaError_t launch_contract_fwd(const Plan& p, const void* X, void* Y, int batch, cudaStream_t s) {
   if (p.tc_fwd && p.tc_min_batch > 0 && batch >= p.tc_min_batch)
     return tc_contract(p, p.tc_fwd, p.tc_adj, X, Y, batch, false, p.tc_err, s);
+  if (p.L.fold) return fold_fwd(p, X, Y, batch, s);
   if (p.L.fp64)
     return p.L.real ? fwd_vb<double, false>(p, X, Y, batch, s) : fwd_vb<double, true>(p, X, Y, batch, s);
   return p.L.real ? fwd_vb<float, false>(p, X, Y, batch, s) : fwd_vb<float, true>(p, X, Y, batch, s);
@@ -261,6 +437,7 @@ cudaError_t launch_contract_fwd(const Plan& p, const void* X, void* Y, int batch
 cudaError_t launch_contract_adj(const Plan& p, const void* D, void* Z, int batch, cudaStream_t s) {
   if (p.tc_adj && p.tc_min_batch > 0 && batch >= p.tc_min_batch)
     return tc_contract(p, p.tc_fwd, p.tc_adj, D, Z, batch, true, p.tc_err, s);
+  if (p.L.fold) return fold_adj(p, D, Z, batch, s);
   if (p.L.fp64)
     return p.L.real ? adj_vb<double, false>(p, D, Z, batch, s) : adj_vb<double, true>(p, D, Z, batch, s);
   return p.L.real ? adj_vb<float, false>(p, D, Z, batch, s) : adj_vb<float, true>(p, D, Z, batch, s);

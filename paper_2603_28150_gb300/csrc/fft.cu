@@ -39,7 +39,9 @@ template <int P>
 struct Shape {
   static constexpr int TPV = P / RadixPlan<P>::RMAX;  // threads per vector
   static constexpr int VPB = kThreads / TPV;           // vectors per block
-  static constexpr int VSTR = P + P / 16;              // padded vector stride
+  // padded vector stride: the extra element puts consecutive vectors in
+  // different banks for the transposed (vector-major) accesses of the row kernels
+  static constexpr int VSTR = P + P / 16 + 1;
 };
 
 // Radix of pass S and the product of the radices before it.
@@ -229,6 +231,7 @@ __global__ void __launch_bounds__(kThreads) k_row_r2c(const R* __restrict__ in, 
   NoStore<R> st;
   run_passes<R, P, 0, false, true, false>(bufs + v * SH::VSTR, tw, tid, ld, st);
   cx<R>* dst = T + s * tslice;
+#pragma unroll 4
   for (int i = threadIdx.x; i < SH::VPB * (P / 2 + 1); i += kThreads) {
     const int vv = i % SH::VPB, kx = i / SH::VPB;
     const int yy = 2 * (pair0 + vv);
@@ -313,21 +316,40 @@ __global__ void __launch_bounds__(kThreads) k_row_c2r(const cx<R>* __restrict__ 
   const int64_t s = blockIdx.y;
   const int pair0 = blockIdx.x * SH::VPB;
   const cx<R>* src = T + s * tslice;
-  for (int i = threadIdx.x; i < SH::VPB * (P / 2 + 1); i += kThreads) {
-    const int vv = i % SH::VPB, kx = i / SH::VPB;
-    const int yy = 2 * (pair0 + vv);
-    cx<R> A = mk<R>(0, 0), B = mk<R>(0, 0);
-    if (yy < ny_out) {
-      A = src[(int64_t)kx * tstride + yy];
-      if (yy + 1 < ny_out) B = src[(int64_t)kx * tstride + yy + 1];
+  // all global loads first (independent, in flight together), then the
+  // Hermitian packing into shared memory
+  constexpr int NH = SH::VPB * (P / 2 + 1);
+  constexpr int NIT = (NH + kThreads - 1) / kThreads;
+  constexpr int CH = 4;  // loads in flight per thread (bounded to keep occupancy)
+#pragma unroll
+  for (int c0 = 0; c0 < NIT; c0 += CH) {
+    cx<R> Av[CH], Bv[CH];
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+      const int i = threadIdx.x + (c0 + c) * kThreads;
+      const int vv = i % SH::VPB, kx = i / SH::VPB;
+      const int yy = 2 * (pair0 + vv);
+      Av[c] = mk<R>(0, 0);
+      Bv[c] = mk<R>(0, 0);
+      if (c0 + c < NIT && i < NH && yy < ny_out) {
+        Av[c] = src[(int64_t)kx * tstride + yy];
+        if (yy + 1 < ny_out) Bv[c] = src[(int64_t)kx * tstride + yy + 1];
+      }
     }
-    if (kx == 0 || kx == P / 2) {  // spectra of real rows: real at DC and Nyquist
-      A.y = 0;
-      B.y = 0;
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+      const int i = threadIdx.x + (c0 + c) * kThreads;
+      if (c0 + c >= NIT || i >= NH) break;
+      const int vv = i % SH::VPB, kx = i / SH::VPB;
+      cx<R> A = Av[c], B = Bv[c];
+      if (kx == 0 || kx == P / 2) {  // spectra of real rows: real at DC and Nyquist
+        A.y = 0;
+        B.y = 0;
+      }
+      cx<R>* b = bufs + vv * SH::VSTR;
+      b[pidx(kx)] = mk<R>(A.x - B.y, A.y + B.x);
+      if (kx > 0 && kx < P / 2) b[pidx(P - kx)] = mk<R>(A.x + B.y, B.x - A.y);
     }
-    cx<R>* b = bufs + vv * SH::VSTR;
-    b[pidx(kx)] = mk<R>(A.x - B.y, A.y + B.x);
-    if (kx > 0 && kx < P / 2) b[pidx(P - kx)] = mk<R>(A.x + B.y, B.x - A.y);
   }
   __syncthreads();
   const int y0 = 2 * (pair0 + v);

@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "pat.h"
 
@@ -77,7 +78,11 @@ struct Layout {
   int tstride;         // ny rounded up to even (row stride of the FFT intermediate)
   int64_t tslice;      // (px/2 + 1) * tstride
   size_t rsize;        // sizeof(real_t)
-  size_t table_bytes;  // nkb * nt * nzg * 32 * 16
+  size_t table_bytes;  // (fold ? nub : nkb) * nt * nzg * 32 * 16
+  // D4 folding: the spectra depend only on {|kx|, |ky|}; one table row per
+  // representative (a, b), 0 <= a <= b <= P/2, shared by up to 4 bins.
+  bool fold = false;
+  int64_t U = 0, Upad = 0, nub = 0;  // representatives, padded to 32, blocks of 32
 };
 
 struct Graph;  // CUDA-graph cache (api.cu)
@@ -106,6 +111,11 @@ struct Plan {
   int r2_cap = 0;
   Graph* graphs = nullptr;
   size_t ws_bytes = 0;
+  // D4 folding maps (device): bins of each representative (-1 = none), and
+  // the representative of each bin
+  int* fold_members = nullptr;  // [Upad][4]
+  int* fold_rep = nullptr;      // [K]
+  double fold_deviation = 0;    // max |Hh(bin) - Hh(representative)| seen (stored scale)
   // split-BF16 tensor-core tables (tc_contract.cu)
   void* tc_fwd = nullptr;
   void* tc_adj = nullptr;
@@ -209,18 +219,27 @@ cudaError_t tc_contract(const Plan& p, const void* tables_fwd, const void* table
 // Table construction (table.cu). Both allocate p.table and set the
 // representation (real or complex) of p.L.
 int build_table_from_source(Plan& p, const void* table, pat_table_format fmt, bool force_complex,
-                            cudaStream_t s);
-int build_table_kspace(Plan& p, const pat_medium& m, bool force_complex, cudaStream_t s);
+                            bool allow_fold, cudaStream_t s);
+int build_table_kspace(Plan& p, const pat_medium& m, bool force_complex, bool allow_fold,
+                       cudaStream_t s);
 bool is_device_ptr(const void* p);
 
 // Representation-dependent parts of the layout.
-inline void set_representation(Layout& L, bool real) {
+inline void set_representation(Layout& L, bool real, bool fold = false) {
   L.real = real;
+  L.fold = fold;
   const size_t esz = (L.fp64 ? 8 : 4) * (real ? 1 : 2);
   L.zg = (int)(16 / esz);
   L.nzg = (L.nz + L.zg - 1) / L.zg;
-  L.table_bytes = (size_t)L.nkb * L.nt * L.nzg * 32 * 16;
+  L.table_bytes = (size_t)(fold ? L.nub : L.nkb) * L.nt * L.nzg * 32 * 16;
 }
+
+// D4 folding is possible for real single-precision tables on square padded
+// grids (the symmetry itself is checked or guaranteed by the table builder).
+inline bool fold_possible(const Layout& L) { return L.real && !L.fp64 && L.px == L.py; }
+// Builds the folding maps of p (host enumeration, device copies) and sets
+// L.U / Upad / nub; rep_bins (optional) receives each representative's own bin.
+int build_fold_maps(Plan& p, std::vector<int>* rep_bins);
 
 // Vector kernels (vec.cu).
 cudaError_t launch_dot(const Plan& p, const void* a, const void* b, int64_t n, double* out_dev,

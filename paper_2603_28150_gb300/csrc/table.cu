@@ -145,6 +145,47 @@ __global__ void k_kspace(int px, int py, int mz, int nz, int nt, int nzg, int ZG
   }
 }
 
+// max |T[k] - T[rep(k)]| over a real blocked table (bits of a non-negative double).
+__global__ void k_fold_check(const float* __restrict__ table, const int* __restrict__ rep,
+                             const int* __restrict__ members, int64_t K, int nt, int nzg,
+                             unsigned long long* out) {
+  const int64_t n = K * nt * nzg * 4;
+  double m = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int q = (int)(i & 3);
+    const int64_t r = i >> 2;
+    const int g = (int)(r % nzg);
+    const int t = (int)((r / nzg) % nt);
+    const int64_t k = r / ((int64_t)nzg * nt);
+    const int64_t kr = members[4 * (int64_t)rep[k]];  // the representative's own bin
+    const float a = table[(((k >> 5) * nt + t) * nzg + g) * 128 + (k & 31) * 4 + q];
+    const float b = table[(((kr >> 5) * nt + t) * nzg + g) * 128 + (kr & 31) * 4 + q];
+    m = fmax(m, fabs((double)a - (double)b));
+  }
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
+}
+
+// folded[u] = full[bin of representative u] for every (t, z-group), real tables.
+__global__ void k_fold_gather(const float4* __restrict__ full, float4* __restrict__ folded,
+                              const int* __restrict__ members, int64_t U, int64_t Upad, int nt,
+                              int nzg) {
+  const int64_t n = Upad * nt * nzg;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int g = (int)(i % nzg);
+    const int t = (int)((i / nzg) % nt);
+    const int64_t u = i / ((int64_t)nzg * nt);
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (u < U) {
+      const int64_t k = members[4 * u];
+      v = full[(((k >> 5) * nt + t) * nzg + g) * 32 + (k & 31)];
+    }
+    folded[(((u >> 5) * nt + t) * nzg + g) * 32 + (u & 31)] = v;
+  }
+}
+
 int grid_for(int64_t n) {
   int64_t b = (n + 255) / 256;
   if (b > 152 * 32) b = 152 * 32;
@@ -189,6 +230,45 @@ std::vector<double> twiddles(int n) {
 
 }  // namespace
 
+int build_fold_maps(Plan& p, std::vector<int>* rep_bins) {
+  Layout& L = p.L;
+  const int P = L.px, half = P / 2;
+  std::vector<int> members, rep((size_t)L.K, -1);
+  for (int a = 0; a <= half; ++a)
+    for (int b = a; b <= half; ++b) {
+      // bins (kx, ky) of the half spectrum with {kx, |ky|} = {a, b}
+      const int cand[4][2] = {{a, b}, {a, (P - b) % P}, {b, a}, {b, (P - a) % P}};
+      int out[4] = {-1, -1, -1, -1}, n = 0;
+      for (auto& c : cand) {
+        const int k = c[0] * P + c[1];
+        bool dup = false;
+        for (int i = 0; i < n; ++i) dup |= out[i] == k;
+        if (!dup) out[n++] = k;
+      }
+      const int u = (int)(members.size() / 4);
+      for (int i = 0; i < 4; ++i) {
+        members.push_back(out[i]);
+        if (out[i] >= 0) rep[out[i]] = u;
+      }
+    }
+  L.U = (int64_t)members.size() / 4;
+  L.Upad = (L.U + 31) / 32 * 32;
+  L.nub = L.Upad / 32;
+  members.resize((size_t)L.Upad * 4, -1);
+  for (int64_t k = 0; k < L.K; ++k)
+    if (rep[k] < 0) return fail(PAT_ERR_CUDA, "internal: a bin without representative");
+  if (rep_bins) {
+    rep_bins->resize((size_t)L.U);
+    for (int64_t u = 0; u < L.U; ++u) (*rep_bins)[u] = members[4 * u];
+  }
+  PAT_CUDA(cudaMalloc(&p.fold_members, members.size() * sizeof(int)));
+  PAT_CUDA(cudaMalloc(&p.fold_rep, rep.size() * sizeof(int)));
+  PAT_CUDA(cudaMemcpy(p.fold_members, members.data(), members.size() * sizeof(int),
+                      cudaMemcpyHostToDevice));
+  PAT_CUDA(cudaMemcpy(p.fold_rep, rep.data(), rep.size() * sizeof(int), cudaMemcpyHostToDevice));
+  return PAT_OK;
+}
+
 bool is_device_ptr(const void* p) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
@@ -199,7 +279,7 @@ bool is_device_ptr(const void* p) {
 }
 
 int build_table_from_source(Plan& p, const void* table, pat_table_format fmt, bool force_complex,
-                            cudaStream_t s) {
+                            bool allow_fold, cudaStream_t s) {
   Layout& L = p.L;
   const bool spatial = fmt == PAT_TABLE_SPATIAL_F64 || fmt == PAT_TABLE_SPATIAL_F32;
   const bool src64 = fmt == PAT_TABLE_SPATIAL_F64 || fmt == PAT_TABLE_SPECTRAL_C128;
@@ -329,19 +409,79 @@ int build_table_from_source(Plan& p, const void* table, pat_table_format fmt, bo
     }
   PREP_CUDA(cudaStreamSynchronize(s));
   cleanup();
+
+  // D4 folding when every bin equals its representative (to 1e-6 of max |Hh|).
+  if (allow_fold && fold_possible(L)) {
+    int rc = build_fold_maps(p, nullptr);
+    if (rc != PAT_OK) return rc;
+    unsigned long long* dev_max = nullptr;
+    PAT_CUDA(cudaMalloc(&dev_max, sizeof(unsigned long long)));
+    cudaError_t e = cudaMemsetAsync(dev_max, 0, sizeof(unsigned long long), s);
+    if (e == cudaSuccess) {
+      k_fold_check<<<grid_for(L.K * L.nt * L.nzg * 4), 256, 0, s>>>(
+          static_cast<const float*>(p.table), p.fold_rep, p.fold_members, L.K, L.nt, L.nzg,
+          dev_max);
+      e = cudaGetLastError();
+    }
+    unsigned long long hm = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hm, dev_max, sizeof(hm), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(dev_max);
+    if (e != cudaSuccess) return cuda_fail(e, "checking the D4 symmetry of the table");
+    double dmax;
+    memcpy(&dmax, &hm, 8);
+    p.fold_deviation = dmax;
+    if (dmax <= 1e-6 * p.table_max_abs / ((double)L.px * (double)L.py)) {
+      Layout F = L;
+      set_representation(F, true, true);
+      void* folded = nullptr;
+      PAT_CUDA(cudaMalloc(&folded, F.table_bytes));
+      k_fold_gather<<<grid_for(F.Upad * F.nt * F.nzg), 256, 0, s>>>(
+          static_cast<const float4*>(p.table), static_cast<float4*>(folded), p.fold_members, F.U,
+          F.Upad, F.nt, F.nzg);
+      e = cudaGetLastError();
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) {
+        cudaFree(folded);
+        return cuda_fail(e, "folding the table");
+      }
+      cudaFree(p.table);
+      p.table = folded;
+      L = F;
+    } else {
+      cudaFree(p.fold_members);
+      cudaFree(p.fold_rep);
+      p.fold_members = p.fold_rep = nullptr;
+    }
+  }
   return PAT_OK;
 #undef PREP_CUDA
 }
 
-int build_table_kspace(Plan& p, const pat_medium& m, bool force_complex, cudaStream_t s) {
+int build_table_kspace(Plan& p, const pat_medium& m, bool force_complex, bool allow_fold,
+                       cudaStream_t s) {
   Layout& L = p.L;
   if (L.fp64) return fail(PAT_ERR_UNSUPPORTED, "k-space generation builds single-precision tables");
   set_representation(L, !force_complex);
+  // |k| depends on kx^2 + ky^2 only, so with dx = dy on a square grid the
+  // library is exactly D4-symmetric: generate one row per representative.
+  std::vector<int> bins;
+  const bool fold = allow_fold && fold_possible(L) && m.dx == m.dy;
+  if (fold) {
+    int rc = build_fold_maps(p, &bins);
+    if (rc != PAT_OK) return rc;
+    set_representation(L, true, true);
+  } else {
+    bins.resize((size_t)L.K);
+    for (int64_t k = 0; k < L.K; ++k) bins[k] = (int)k;
+  }
+  const int64_t npos = (int64_t)bins.size();
   const int M = m.mz / 2 + 1;
   const double pi = 3.14159265358979323846;
   // u_m(k) = c dt |k_m| / (2 pi) turns per sample, as 64-bit fixed-point fractions.
-  std::vector<unsigned long long> u((size_t)L.K * M);
-  for (int64_t k = 0; k < L.K; ++k) {
+  std::vector<unsigned long long> u((size_t)npos * M);
+  for (int64_t pos = 0; pos < npos; ++pos) {
+    const int64_t k = bins[pos];
     const int kx = (int)(k / L.py), kyi = (int)(k % L.py);
     const int ky = kyi < L.py / 2 ? kyi : kyi - L.py;
     const double wx = 2.0 * pi * kx / (L.px * m.dx), wy = 2.0 * pi * ky / (L.py * m.dy);
@@ -349,7 +489,7 @@ int build_table_kspace(Plan& p, const pat_medium& m, bool force_complex, cudaStr
       const double wz = 2.0 * pi * mm / (m.mz * m.dz);
       const double turns = m.c * m.dt * std::sqrt(wx * wx + wy * wy + wz * wz) / (2.0 * pi);
       const double frac = turns - std::floor(turns);
-      u[(size_t)k * M + mm] = (unsigned long long)std::ldexp(frac, 64);
+      u[(size_t)pos * M + mm] = (unsigned long long)std::ldexp(frac, 64);
     }
   }
   std::vector<float> W((size_t)M * L.nz);
@@ -388,8 +528,9 @@ int build_table_kspace(Plan& p, const pat_medium& m, bool force_complex, cudaStr
   }
   GEN_CUDA(cudaFuncSetAttribute((const void*)k_kspace, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)smem));
-  k_kspace<<<(unsigned)L.nkb, 256, smem, s>>>(L.px, L.py, m.mz, L.nz, L.nt, L.nzg, L.zg,
-                                              L.real ? 0 : 1, u_d, W_d, p.table, L.K);
+  k_kspace<<<(unsigned)((npos + 31) / 32), 256, smem, s>>>(L.px, L.py, m.mz, L.nz, L.nt, L.nzg,
+                                                            L.zg, L.real ? 0 : 1, u_d, W_d,
+                                                            p.table, npos);
   GEN_CUDA(cudaGetLastError());
   GEN_CUDA(cudaStreamSynchronize(s));
   cleanup();

@@ -364,9 +364,9 @@ size_t smem_for(int kchunks) {
 
 // Forward-direction tile of bin k, row tile mt (t rows), part, from the real
 // blocked FP32 table; adjoint tile of bin k, K chunk kc (t columns), part.
-__global__ void k_split_tables(const float* __restrict__ table, int nz, int nt, int nzg,
-                               int64_t K, unsigned char* __restrict__ fwd,
-                               unsigned char* __restrict__ adj) {
+__global__ void k_split_tables(const float* __restrict__ table, const int* __restrict__ rep,
+                               int nz, int nt, int nzg, int64_t K,
+                               unsigned char* __restrict__ fwd, unsigned char* __restrict__ adj) {
   const int64_t n = K * nt * nz;
   const int mtiles = nt / kTile;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -374,7 +374,8 @@ __global__ void k_split_tables(const float* __restrict__ table, int nz, int nt, 
     const int z = (int)(i % nz);
     const int t = (int)((i / nz) % nt);
     const int64_t k = i / ((int64_t)nz * nt);
-    const int64_t kb = k >> 5, l = k & 31;
+    const int64_t row = rep ? rep[k] : k;  // folded tables: the bin's representative row
+    const int64_t kb = row >> 5, l = row & 31;
     const float h = table[(((kb * nt + t) * nzg + z / 4) * 32 + l) * 4 + z % 4];
     const __nv_bfloat16 hi = __float2bfloat16_rn(h);
     const __nv_bfloat16 lo = __float2bfloat16_rn(h - __bfloat162float(hi));
@@ -410,8 +411,9 @@ cudaError_t tc_build_tables(const Plan& p, void* fwd, void* adj, cudaStream_t s)
   int64_t n = L.K * L.nt * L.nz;
   int64_t g = (n + 255) / 256;
   if (g > 152 * 64) g = 152 * 64;
-  tc::k_split_tables<<<(int)g, 256, 0, s>>>(static_cast<const float*>(p.table), L.nz, L.nt,
-                                            L.nzg, L.K, static_cast<unsigned char*>(fwd),
+  tc::k_split_tables<<<(int)g, 256, 0, s>>>(static_cast<const float*>(p.table),
+                                            L.fold ? p.fold_rep : nullptr, L.nz, L.nt, L.nzg,
+                                            L.K, static_cast<unsigned char*>(fwd),
                                             static_cast<unsigned char*>(adj));
   return cudaGetLastError();
 }

@@ -29,6 +29,7 @@ PAT_ERR_UNSUPPORTED = -5
 FLAG_FP64 = 1
 FLAG_FORCE_COMPLEX = 2
 FLAG_BF16_SPLIT = 4
+FLAG_NO_FOLD = 8
 
 TABLE_SPATIAL_F64 = 0
 TABLE_SPATIAL_F32 = 1
@@ -70,7 +71,8 @@ class PlanInfo(ctypes.Structure):
                 ("table_bytes", ctypes.c_int64),
                 ("workspace_bytes", ctypes.c_int64), ("table_max_abs", ctypes.c_double),
                 ("table_max_imag", ctypes.c_double), ("tensor_table_bytes", ctypes.c_int64),
-                ("tensor_min_batch", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("tensor_min_batch", ctypes.c_int32), ("folded", ctypes.c_int32),
+                ("table_rows", ctypes.c_int64)]
 
 
 class FistaParams(ctypes.Structure):
@@ -188,7 +190,7 @@ class Plan:
     def __init__(self, nx: int, ny: int, nz: int, nt: int, px: int | None = None,
                  py: int | None = None, max_batch: int = 1, fp64: bool = False,
                  force_complex: bool = False, table=None, medium: Medium | None = None,
-                 bf16_split: bool = False, stream=None):
+                 bf16_split: bool = False, fold: bool = True, stream=None):
         L = lib()
         self.nx, self.ny, self.nz, self.nt = nx, ny, nz, nt
         self.px = px if px is not None else _pow2_at_least(2 * nx)
@@ -196,7 +198,7 @@ class Plan:
         self.max_batch = max_batch
         self.fp64 = fp64
         flags = ((FLAG_FP64 if fp64 else 0) | (FLAG_FORCE_COMPLEX if force_complex else 0)
-                 | (FLAG_BF16_SPLIT if bf16_split else 0))
+                 | (FLAG_BF16_SPLIT if bf16_split else 0) | (0 if fold else FLAG_NO_FOLD))
         self._geom = Geometry(nx, ny, nz, nt, self.px, self.py, max_batch, flags)
         self._h = ctypes.c_void_p(0)
         s = _stream(stream)
@@ -386,11 +388,14 @@ class Plan:
 
 
 def plan_estimate(nx: int, ny: int, nz: int, nt: int, px: int | None = None, py: int | None = None,
-                  max_batch: int = 1, fp64: bool = False, real_table: bool = True):
-    """(table bytes, workspace bytes) a plan would take on the device."""
+                  max_batch: int = 1, fp64: bool = False, real_table: bool = True,
+                  bf16_split: bool = False):
+    """(table bytes including the split-BF16 tables, workspace bytes) a plan
+    would take on the device."""
     px = px if px is not None else _pow2_at_least(2 * nx)
     py = py if py is not None else _pow2_at_least(2 * ny)
-    g = Geometry(nx, ny, nz, nt, px, py, max_batch, FLAG_FP64 if fp64 else 0)
+    g = Geometry(nx, ny, nz, nt, px, py, max_batch,
+                 (FLAG_FP64 if fp64 else 0) | (FLAG_BF16_SPLIT if bf16_split else 0))
     tb, ws = ctypes.c_int64(0), ctypes.c_int64(0)
     _check(lib().pat_plan_estimate(ctypes.byref(g), 1 if real_table else 0, ctypes.byref(tb),
                                    ctypes.byref(ws)))

@@ -80,16 +80,23 @@ class CudaEngine:
         with torch.cuda.stream(self.stream):
             med = Medium(geom.c, geom.dx, geom.dx, geom.dx, geom.dt, geom.depth_period(), geom.z0)
             self.plan = Plan(geom.n, geom.n, geom.nz, geom.nt, geom.pad, geom.pad,
-                             max_batch=slots, medium=med, force_complex=force_complex)
+                             max_batch=slots, medium=med, force_complex=force_complex,
+                             bf16_split=self.tensor_ok(geom, slots) and not force_complex)
             v0 = torch.ones((geom.nz, geom.n, geom.n), dtype=torch.float32, device="cuda")
             self.L = 1.01 * self.plan.power_norm(v0, power_iters)
         self.ref = None
         self.kernels = 0
 
     @staticmethod
-    def estimate(geom: Geometry, slots: int) -> int:
+    def tensor_ok(geom: Geometry, slots: int) -> bool:
+        """Grids the split-BF16 tensor-core contraction takes (batched slots)."""
+        return slots >= 2 and geom.nz == 128 and geom.nt % 128 == 0 and geom.nt <= 512
+
+    @classmethod
+    def estimate(cls, geom: Geometry, slots: int) -> int:
         from .pat import plan_estimate
-        tb, ws = plan_estimate(geom.n, geom.n, geom.nz, geom.nt, geom.pad, geom.pad, slots)
+        tb, ws = plan_estimate(geom.n, geom.n, geom.nz, geom.nt, geom.pad, geom.pad, slots,
+                               bf16_split=cls.tensor_ok(geom, slots))
         return tb + ws
 
     def bytes(self) -> int:

@@ -101,15 +101,22 @@ def gaussian_field(shape, seed: int = 0) -> np.ndarray:
 
 
 def random_kernels(nz: int, nt: int, px: int, py: int, seed: int = 0,
-                   even: bool = False) -> np.ndarray:
+                   even: bool = False, d4: bool = False) -> np.ndarray:
     """A random spatial kernel library h[nz][nt][py][px] (wrapped origin),
     U[-1, 1]. With even=True every plane satisfies h(-u) = h(u) (index
-    negation modulo the padded size), i.e. its spectrum is real."""
+    negation modulo the padded size), i.e. its spectrum is real. With d4=True
+    (px == py) every plane is the average of its 8 images under the square's
+    symmetries (ux -> -ux, uy -> -uy, ux <-> uy), like a radially symmetric
+    kernel: its spectrum is real and depends on {|kx|, |ky|} only."""
     h = rng(seed).uniform(-1.0, 1.0, (nz, nt, py, px))
-    if even:
+    if even or d4:
         iy = (-np.arange(py)) % py
         ix = (-np.arange(px)) % px
         h = 0.5 * (h + h[:, :, iy][:, :, :, ix])
+    if d4:
+        assert px == py, "the square's symmetries need px == py"
+        h = 0.5 * (h + h[:, :, iy])            # uy -> -uy
+        h = 0.5 * (h + np.swapaxes(h, 2, 3))   # ux <-> uy
     return h
 
 

@@ -24,7 +24,13 @@ def _tables(g, kind, seed=0):
         return synth.random_kernels(g.nz, g.nt, g.px, g.py, seed=seed)
     if kind == "even":        # even kernels: real spectra
         return synth.random_kernels(g.nz, g.nt, g.px, g.py, seed=seed, even=True)
+    if kind == "d4":          # the square's symmetries: real spectra of {|kx|, |ky|}
+        return synth.random_kernels(g.nz, g.nt, g.px, g.py, seed=seed, d4=True)
     return kspace_table(g, MED_CFG1)[0]
+
+
+def _expect_fold(g, kind):
+    return kind in ("d4", "kspace") and g.px == g.py
 
 
 def _ref_ops(h, g):
@@ -33,13 +39,17 @@ def _ref_ops(h, g):
 
 
 @pytest.mark.parametrize("g", [CFG1, RAGGED, RECT, SMALLP], ids=["cfg1", "ragged", "rect", "p16"])
-@pytest.mark.parametrize("kind", ["random", "even", "kspace"])
+@pytest.mark.parametrize("kind", ["random", "even", "d4", "kspace"])
 @pytest.mark.parametrize("fp64", [False, True])
 def test_forward_and_adjoint_match_oracle(g, kind, fp64):
+    if kind == "d4" and g.px != g.py:
+        pytest.skip("the square's symmetries need a square padded grid")
     h = _tables(g, kind, seed=g.nx)
     A, AT = _ref_ops(h, g)
     plan = Plan(g.nx, g.ny, g.nz, g.nt, g.px, g.py, table=h, fp64=fp64)
-    assert plan.info()["real_table"] == (0 if kind == "random" else 1)
+    info = plan.info()
+    assert info["real_table"] == (0 if kind == "random" else 1)
+    assert info["folded"] == (1 if _expect_fold(g, kind) and not fp64 else 0)
     rho = synth.blobs(g.nx, g.ny, g.nz, count=8, seed=1) + 0.1 * synth.gaussian_object(g.nx, g.ny, g.nz, 2)
     y = synth.gaussian_field((g.nt, g.ny, g.nx), seed=3)
     tol = 1e-12 if fp64 else 1e-5
@@ -55,13 +65,45 @@ def test_forward_and_adjoint_match_oracle(g, kind, fp64):
 def test_forced_complex_equals_real_path(fp64):
     g = CFG1
     h = _tables(g, "kspace")
-    pr = Plan(g.nx, g.ny, g.nz, g.nt, g.px, g.py, table=h, fp64=fp64)
+    pr = Plan(g.nx, g.ny, g.nz, g.nt, g.px, g.py, table=h, fp64=fp64, fold=False)
     pc = Plan(g.nx, g.ny, g.nz, g.nt, g.px, g.py, table=h, fp64=fp64, force_complex=True)
     assert pr.info()["real_table"] == 1 and pc.info()["real_table"] == 0
     assert pc.info()["table_bytes"] == 2 * pr.info()["table_bytes"]
     rho = synth.blobs(g.nx, g.ny, g.nz, count=8, seed=4)
     dr, dc = host(pr.forward(cuda(rho, fp64))), host(pc.forward(cuda(rho, fp64)))
     assert oracle.rel_l2(dr, dc) < (1e-13 if fp64 else 1e-6)
+
+
+@pytest.mark.parametrize("g", [CFG1, oracle.Grid.square(48, 12, 40), SMALLP],
+                         ids=["cfg1", "n48", "p16"])
+@pytest.mark.parametrize("B", [1, 3])
+def test_folded_equals_unfolded(g, B):
+    """One table row per representative {|kx|, |ky|} gives what one row per bin gives."""
+    h = _tables(g, "d4", seed=31)
+    pf = Plan(g.nx, g.ny, g.nz, g.nt, g.px, g.py, table=h, max_batch=B)
+    pu = Plan(g.nx, g.ny, g.nz, g.nt, g.px, g.py, table=h, max_batch=B, fold=False)
+    fi, ui = pf.info(), pu.info()
+    assert fi["folded"] == 1 and ui["folded"] == 0
+    P = g.px
+    assert fi["table_rows"] == (P // 2 + 1) * (P // 2 + 2) // 2 and ui["table_rows"] == ui["bins"]
+    # rows are stored in blocks of 32
+    assert fi["table_bytes"] * ((ui["bins"] + 31) // 32) == ui["table_bytes"] * ((fi["table_rows"] + 31) // 32)
+    xs = np.stack([synth.blobs(g.nx, g.ny, g.nz, count=4, seed=40 + s) for s in range(B)])
+    ys = np.stack([synth.gaussian_field((g.nt, g.ny, g.nx), 50 + s) for s in range(B)])
+    for a, b in ((pf.forward(cuda(xs)), pu.forward(cuda(xs))),
+                 (pf.adjoint(cuda(ys)), pu.adjoint(cuda(ys)))):
+        a, b = host(a), host(b)
+        assert np.abs(a - b).max() <= 1e-6 * np.abs(b).max()
+
+
+def test_fold_rejected_when_not_symmetric():
+    g = CFG1
+    h = _tables(g, "d4", seed=32)
+    P = g.px
+    h[3, 10, 1, 2] += 0.5           # breaks ux <-> uy for one plane ...
+    h[3, 10, P - 1, P - 2] += 0.5   # ... but keeps h(-u) = h(u): still a real spectrum
+    plan = Plan(g.nx, g.ny, g.nz, g.nt, g.px, g.py, table=h)
+    assert plan.info()["folded"] == 0 and plan.info()["real_table"] == 1
 
 
 @pytest.mark.parametrize("fp64", [False, True])

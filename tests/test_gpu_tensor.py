@@ -24,8 +24,9 @@ def test_tensor_contraction_matches_cuda_core(n, nt, batch):
     plan = Plan(g.nx, g.ny, g.nz, g.nt, g.px, g.py, max_batch=batch,
                 medium=_medium(g, MED_50UM), bf16_split=True)
     info = plan.info()
-    assert info["real_table"] == 1 and info["tensor_min_batch"] == 2
-    assert info["tensor_table_bytes"] == 2 * info["table_bytes"]
+    assert info["real_table"] == 1 and info["tensor_min_batch"] == 2 and info["folded"] == 1
+    # hi + lo BF16 per (bin, t, z), one copy per direction
+    assert info["tensor_table_bytes"] == 2 * info["bins"] * g.nt * g.nz * 4
     Kp = info["bins_padded"]
     gen = torch.Generator(device="cuda").manual_seed(1)
     X = torch.randn((batch, g.nz, Kp), dtype=torch.complex64, device="cuda", generator=gen)
