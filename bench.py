@@ -241,6 +241,27 @@ def run_ours(args, world, rank, local):
         hbm, peak_src = 6800.0, "fallback"
     achieved = algo / (fwd_ms / 1e3) / 1e9
 
+    # every stage of one A + A^T pair on its own (CUDA events), with its
+    # algorithmic bytes (inputs + outputs, + the table for the contractions)
+    slab_z = torch.empty((NZ, N, N), dtype=torch.float32, device=dev).uniform_()
+    slab_t = torch.empty((NT, N, N), dtype=torch.float32, device=dev).uniform_()
+    Sz = torch.empty((NZ, P // 2 + 1, P), dtype=torch.complex64, device=dev)
+    St = torch.empty((NT, P // 2 + 1, P), dtype=torch.complex64, device=dev)
+    oz, ot = torch.empty_like(slab_z), torch.empty_like(slab_t)
+    plan.stage_spectrum(slab_z, out=Sz)
+    plan.stage_spectrum(slab_t, out=St)
+    stage = {}
+    for name, fn, nbytes in (
+            ("a2_spectrum_depths", lambda: plan.stage_spectrum(slab_z, out=Sz), NZ * (N * N * 4 + K * 8)),
+            ("a3_contract_fwd", lambda: plan.stage_contract(Xb, Yb), algo),
+            ("a4_image_times", lambda: plan.stage_image(St, out=ot), NT * (N * N * 4 + K * 8)),
+            ("a5_spectrum_times", lambda: plan.stage_spectrum(slab_t, out=St), NT * (N * N * 4 + K * 8)),
+            ("a6_contract_adj", lambda: plan.stage_contract(Yb, Xb, adjoint=True), algo),
+            ("a7_image_depths", lambda: plan.stage_image(Sz, out=oz), NZ * (N * N * 4 + K * 8))):
+        ms = events_ms(fn, 20)
+        stage[name] = {"us": ms * 1e3, "gbs": nbytes / (ms / 1e3) / 1e9,
+                       "frac_hbm": nbytes / (ms / 1e3) / 1e9 / hbm}
+
     # plain single-precision path: complex64 table, one volume at a time
     plan_c = Plan(N, N, NZ, NT, P, P, medium=med, force_complex=True)
     xc = torch.empty_like(x)
@@ -288,6 +309,7 @@ def run_ours(args, world, rank, local):
                 "h2d_bytes_per_step": int(y_h.numel() * 4),
                 "d2h_bytes_per_step": int(x_h.numel() * 4)},
         "gpu_launches": launches,
+        "stages": stage,
         "clocks": clk.summary(),
         "L": L,
         "resid2_last": rep["resid2_last"],
