@@ -18,7 +18,9 @@
  * ---------------------------------------------------------------------------
  * Conventions (every entry point)
  *   Arrays are dense, row-major, x fastest:
- *     object rho [batch][nz][ny][nx],  data d [batch][nt][ny][nx].
+ *     object rho [batch][nz][ny][nx],  data d [batch][nt][my][mx],
+ *   where (my, mx) = (ny, nx) unless pat_plan_set_sampling put the data on a
+ *   coarser scan grid. Below, "[ny][nx]" of data means [my][mx].
  *   Element type: float for single-precision plans, double for plans created
  *   with PAT_FLAG_FP64 ("real_t" below).
  *   Pointers may be device memory (the normal case; the call is asynchronous on
@@ -195,6 +197,21 @@ const char* pat_last_error(void);
 /* Sets the smallest batch that uses the tensor-core contraction of a plan
  * built with PAT_FLAG_BF16_SPLIT (default 2; 0 = always the CUDA-core path). */
 int pat_plan_set_tensor_batch(pat_plan* plan, int min_batch);
+
+/* Measurement operator (Sec. 2.3, Sec. 3.3): the object stays on the
+ * reconstruction grid while the data are recorded only at the scan positions
+ *   x = ox + sx i (0 <= i < mx),  y = oy + sy j (0 <= j < my),
+ *   mx = ceil((nx - ox) / sx),    my = ceil((ny - oy) / sy),
+ * of the nx x ny sensor grid (e.g. sx = sy = 2 for a reconstruction grid twice
+ * as fine as the scan grid). Afterwards pat_forward applies S H (H of Eq. 7-8,
+ * then keep the scan positions; data real_t[batch][nt][my][mx]), pat_adjoint
+ * applies H* S^T (zero-fill the other sensor positions, then Eq. 11), and
+ * pat_gradient, pat_power_norm, pat_fista_solve and the slots use that pair.
+ * sx = sy = 1, ox = oy = 0 restores the plain operator. Needs sx, sy >= 1,
+ * 0 <= ox < nx, 0 <= oy < ny. Synchronises the device; the plan's cached
+ * graphs are rebuilt on next use and data loaded into slots must be reloaded.
+ * The diagnostic stage entry points are not affected. */
+int pat_plan_set_sampling(pat_plan* plan, int sx, int sy, int ox, int oy);
 
 /* Synchronises the device and reports whether any bounded device-side wait of
  * the plan's kernels gave up since the last check (PAT_ERR_TIMEOUT; the flag

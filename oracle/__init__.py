@@ -200,6 +200,46 @@ def adjoint_fft(Hf, d, g: Grid) -> np.ndarray:
     return rho
 
 
+# ----------------------------------------------------------------------------- measurement
+def scan_positions(n: int, step: int, offset: int) -> list:
+    """Sensor-grid indices of one scan axis: offset, offset + step, ... < n
+    (Sec. 3.3: the scan grid is coarser than the reconstruction grid)."""
+    assert step >= 1 and 0 <= offset < n
+    out, c = [], offset
+    while c < n:
+        out.append(c)
+        c += step
+    return out
+
+
+def sample_scan(d, sx: int, sy: int, ox: int, oy: int) -> np.ndarray:
+    """S of the measurement operator composed with H (Sec. 2.3, Sec. 3.3):
+    keeps the samples at the scan positions x = ox + sx i, y = oy + sy j of
+    every [ny][nx] plane of d (leading axes untouched)."""
+    d = _f64(d)
+    xs = scan_positions(d.shape[-1], sx, ox)
+    ys = scan_positions(d.shape[-2], sy, oy)
+    out = np.empty(d.shape[:-2] + (len(ys), len(xs)))
+    for j, y in enumerate(ys):
+        for i, x in enumerate(xs):
+            out[..., j, i] = d[..., y, x]
+    return out
+
+
+def zero_fill(ds, ny: int, nx: int, sx: int, sy: int, ox: int, oy: int) -> np.ndarray:
+    """S^T: places scan-grid samples ds[..., my, mx] at their sensor positions
+    of an [ny][nx] plane and zeros everywhere else."""
+    ds = _f64(ds)
+    xs = scan_positions(nx, sx, ox)
+    ys = scan_positions(ny, sy, oy)
+    assert ds.shape[-2:] == (len(ys), len(xs))
+    out = np.zeros(ds.shape[:-2] + (ny, nx))
+    for j, y in enumerate(ys):
+        for i, x in enumerate(xs):
+            out[..., y, x] = ds[..., j, i]
+    return out
+
+
 # ----------------------------------------------------------------------------- physics
 @dataclass(frozen=True)
 class Medium:

@@ -14,9 +14,11 @@ import numpy as np
 
 class Operator:
     """H and H* of one geometry, from the oracle's FFT form (default) or the
-    direct spatial form of Eq. 7 / Eq. 11."""
+    direct spatial form of Eq. 7 / Eq. 11. With ``sampling = (sx, sy, ox, oy)``
+    the pair is S H and H* S^T, S the measurement operator that keeps the scan
+    positions (Sec. 2.3, Sec. 3.3)."""
 
-    def __init__(self, grid, Hf=None, h=None, form: str = "fft"):
+    def __init__(self, grid, Hf=None, h=None, form: str = "fft", sampling=None):
         from . import adjoint_fft, adjoint_spatial, forward_fft, forward_spatial, table_spectrum
         self.g = grid
         if form == "fft":
@@ -29,6 +31,7 @@ class Operator:
             self._AT = lambda y: adjoint_spatial(h, y, grid)
         else:
             raise ValueError(form)
+        self.sampling = tuple(sampling) if sampling is not None else None
 
     @property
     def obj_shape(self):
@@ -36,12 +39,24 @@ class Operator:
 
     @property
     def data_shape(self):
-        return (self.g.nt, self.g.ny, self.g.nx)
+        if self.sampling is None:
+            return (self.g.nt, self.g.ny, self.g.nx)
+        from . import scan_positions
+        sx, sy, ox, oy = self.sampling
+        return (self.g.nt, len(scan_positions(self.g.ny, sy, oy)),
+                len(scan_positions(self.g.nx, sx, ox)))
 
     def A(self, x):
-        return self._A(x)
+        d = self._A(x)
+        if self.sampling is None:
+            return d
+        from . import sample_scan
+        return sample_scan(d, *self.sampling)
 
     def AT(self, y):
+        if self.sampling is not None:
+            from . import zero_fill
+            y = zero_fill(y, self.g.ny, self.g.nx, *self.sampling)
         return self._AT(y)
 
 

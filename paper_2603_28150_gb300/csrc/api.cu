@@ -63,6 +63,8 @@ Layout make_layout(const pat_geometry* g) {
   L.nkb = L.Kpad / 32;
   L.tstride = g->ny + (g->ny & 1);
   L.tslice = (int64_t)(g->px / 2 + 1) * L.tstride;
+  L.mx = g->nx;
+  L.my = g->ny;
   set_representation(L, false);
   return L;
 }
@@ -212,8 +214,21 @@ int build_tensor_tables(pat_plan* pp, int flags, cudaStream_t s) {
   return PAT_OK;
 }
 
+// Destroys the cached CUDA graphs (they captured pointers and launch
+// parameters that are about to change).
+void drop_graphs(Plan& p) {
+  for (Graph* g = p.graphs; g;) {
+    Graph* n = g->next;
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    delete g;
+    g = n;
+  }
+  p.graphs = nullptr;
+}
+
 size_t obj_elems(const Layout& L, int batch) { return (size_t)batch * L.nz * L.ny * L.nx; }
-size_t dat_elems(const Layout& L, int batch) { return (size_t)batch * L.nt * L.ny * L.nx; }
+// data live on the scan grid (the whole sensor grid unless sampling is set)
+size_t dat_elems(const Layout& L, int batch) { return (size_t)batch * L.nt * L.my * L.mx; }
 
 }  // namespace
 
@@ -222,17 +237,19 @@ namespace pat {
 cudaError_t forward_dev(const Plan& p, const void* rho, void* d, int batch, cudaStream_t s,
                         const void* sub, double* sumsq, int groups, double* group_sums) {
   const Layout& L = p.L;
-  const int64_t plane = (int64_t)L.ny * L.nx;
+  const int64_t plane = (int64_t)L.ny * L.nx, scan = (int64_t)L.my * L.mx;
   cudaError_t e = launch_spectrum(p, rho, plane, L.nx, L.ny, p.X, L.Kpad, batch * L.nz, s);
   if (e != cudaSuccess) return e;
   if ((e = launch_contract_fwd(p, p.X, p.Y, batch, s)) != cudaSuccess) return e;
-  return launch_image(p, p.Y, L.Kpad, d, plane, batch * L.nt, sub, sumsq, s, groups, group_sums);
+  return launch_image(p, p.Y, L.Kpad, d, scan, batch * L.nt, sub, sumsq, s, groups, group_sums,
+                      sampling_of(L));
 }
 
 cudaError_t adjoint_dev(const Plan& p, const void* d, void* rho, int batch, cudaStream_t s) {
   const Layout& L = p.L;
-  const int64_t plane = (int64_t)L.ny * L.nx;
-  cudaError_t e = launch_spectrum(p, d, plane, L.nx, L.ny, p.Y, L.Kpad, batch * L.nt, s);
+  const int64_t plane = (int64_t)L.ny * L.nx, scan = (int64_t)L.my * L.mx;
+  cudaError_t e = launch_spectrum(p, d, scan, L.nx, L.ny, p.Y, L.Kpad, batch * L.nt, s,
+                                  sampling_of(L));
   if (e != cudaSuccess) return e;
   if ((e = launch_contract_adj(p, p.Y, p.X, batch, s)) != cudaSuccess) return e;
   return launch_image(p, p.X, L.Kpad, rho, plane, batch * L.nz, nullptr, nullptr, s);
@@ -488,6 +505,25 @@ int pat_plan_set_tensor_batch(pat_plan* plan, int min_batch) {
   return PAT_OK;
 }
 
+int pat_plan_set_sampling(pat_plan* plan, int sx, int sy, int ox, int oy) {
+  PAT_GUARD_BEGIN
+  if (!plan) return fail(PAT_ERR_ARG, "plan is NULL");
+  Layout& L = plan->p.L;
+  if (sx < 1 || sy < 1 || ox < 0 || oy < 0 || ox >= L.nx || oy >= L.ny)
+    return fail(PAT_ERR_ARG, "need sx, sy >= 1 and 0 <= ox < nx, 0 <= oy < ny");
+  // work queued on the plan's buffers must not see the layout change
+  PAT_CUDA(cudaDeviceSynchronize());
+  drop_graphs(plan->p);
+  L.sx = sx;
+  L.sy = sy;
+  L.ox = ox;
+  L.oy = oy;
+  L.mx = (L.nx - ox + sx - 1) / sx;
+  L.my = (L.ny - oy + sy - 1) / sy;
+  return PAT_OK;
+  PAT_GUARD_END
+}
+
 int pat_plan_check(pat_plan* plan) {
   PAT_GUARD_BEGIN
   if (!plan) return fail(PAT_ERR_ARG, "plan is NULL");
@@ -635,13 +671,7 @@ int pat_fista_solve(pat_plan* plan, const void* y, void* x, int batch,
     PAT_CUDA(cudaMalloc(&p.betas, sizeof(double) * cap));
     PAT_CUDA(cudaMalloc(&p.r2_dev, sizeof(double) * cap));
     p.betas_cap = p.r2_cap = cap;
-    for (Graph* g = p.graphs; g;) {  // graphs captured the old pointers
-      Graph* n = g->next;
-      cudaGraphExecDestroy(g->exec);
-      delete g;
-      g = n;
-    }
-    p.graphs = nullptr;
+    drop_graphs(p);  // graphs captured the old pointers
   }
   std::vector<double> betas(iters + 1, 0.0);
   double t = 1.0;

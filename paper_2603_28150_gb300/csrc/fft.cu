@@ -202,14 +202,25 @@ constexpr size_t smem_bytes() {
   return sizeof(cx<R>) * (size_t)(P + Shape<P>::VPB * Shape<P>::VSTR);
 }
 
+// Compact index of sensor coordinate c on a scan axis (offset o, stride st,
+// n samples), or -1 when c is not a scan position.
+__device__ __forceinline__ int scan_index(int c, int o, int st, int n) {
+  const int d = c - o;
+  if (d < 0 || d % st) return -1;
+  const int i = d / st;
+  return i < n ? i : -1;
+}
+
 // Stage i, row pass: rows y0 = 2 pair, y0 + 1 of slice s packed as a + i b,
 // zero-padded from nx_in to P, transformed; half spectra written to
-// T[s][kx][y] for kx in [0, P/2].
+// T[s][kx][y] for kx in [0, P/2]. With sampling on, the slice is the
+// zero-filled image of scan-grid data in[s][my][mx] (the adjoint of the
+// measurement operator, Sec. 3.3).
 template <typename R, int P>
 __global__ void __launch_bounds__(kThreads) k_row_r2c(const R* __restrict__ in, int64_t in_stride,
                                                       int nx_in, int ny_in, cx<R>* __restrict__ T,
                                                       int tstride, int64_t tslice,
-                                                      const cx<R>* __restrict__ tw_g) {
+                                                      const cx<R>* __restrict__ tw_g, Samp sm) {
   using SH = Shape<P>;
   cx<R>* tw;
   cx<R>* bufs = setup_smem<R, P>(tw_g, &tw);
@@ -217,14 +228,33 @@ __global__ void __launch_bounds__(kThreads) k_row_r2c(const R* __restrict__ in, 
   const int64_t s = blockIdx.y;
   const int pair0 = blockIdx.x * SH::VPB;
   const int y0 = 2 * (pair0 + v);
-  const R* row0 = in + s * in_stride + (int64_t)y0 * nx_in;
-  const bool ok0 = y0 < ny_in, ok1 = y0 + 1 < ny_in;
+  const R* base = in + s * in_stride;
+  const R* row0;
+  const R* row1;
+  bool ok0, ok1;
+  if (!sm.on) {
+    ok0 = y0 < ny_in;
+    ok1 = y0 + 1 < ny_in;
+    row0 = base + (int64_t)y0 * nx_in;
+    row1 = row0 + nx_in;
+  } else {
+    const int j0 = y0 < ny_in ? scan_index(y0, sm.oy, sm.sy, sm.my) : -1;
+    const int j1 = y0 + 1 < ny_in ? scan_index(y0 + 1, sm.oy, sm.sy, sm.my) : -1;
+    ok0 = j0 >= 0;
+    ok1 = j1 >= 0;
+    row0 = base + (int64_t)(ok0 ? j0 : 0) * sm.mx;
+    row1 = base + (int64_t)(ok1 ? j1 : 0) * sm.mx;
+  }
   __syncthreads();  // twiddles staged
   auto ld = [&](int x) -> cx<R> {
     R a = 0, b = 0;
     if (x < nx_in) {
-      if (ok0) a = row0[x];
-      if (ok1) b = row0[nx_in + x];
+      int xi = x;
+      if (sm.on) xi = scan_index(x, sm.ox, sm.sx, sm.mx);
+      if (xi >= 0) {
+        if (ok0) a = row0[xi];
+        if (ok1) b = row1[xi];
+      }
     }
     return mk<R>(a, b);
   };
@@ -302,13 +332,15 @@ __global__ void __launch_bounds__(kThreads) k_col_inv(const cx<R>* __restrict__ 
 // Z[P - kx] = conj(A) + i conj(B), inverse FFT over x; Re -> row y0,
 // Im -> row y0 + 1, columns [0, nx_out) kept. With `sub`, writes
 // image - sub and accumulates its squares (FP64) per block into partials.
+// With sampling on, only the scan positions are kept, written compactly to
+// out[s][my][mx] (the measurement operator of Sec. 3.3); `sub` has that layout.
 template <typename R, int P>
 __global__ void __launch_bounds__(kThreads) k_row_c2r(const cx<R>* __restrict__ T, int tstride,
                                                       int64_t tslice, int nx_out, int ny_out,
                                                       R* __restrict__ out, int64_t out_stride,
                                                       const R* __restrict__ sub,
                                                       double* __restrict__ partials,
-                                                      const cx<R>* __restrict__ tw_g) {
+                                                      const cx<R>* __restrict__ tw_g, Samp sm) {
   using SH = Shape<P>;
   cx<R>* tw;
   cx<R>* bufs = setup_smem<R, P>(tw_g, &tw);
@@ -353,24 +385,47 @@ __global__ void __launch_bounds__(kThreads) k_row_c2r(const cx<R>* __restrict__ 
   }
   __syncthreads();
   const int y0 = 2 * (pair0 + v);
-  const bool ok0 = y0 < ny_out, ok1 = y0 + 1 < ny_out;
-  R* d0 = out + s * out_stride + (int64_t)y0 * nx_out;
-  const R* s0 = sub ? sub + s * out_stride + (int64_t)y0 * nx_out : nullptr;
+  // destination rows (compact scan rows with sampling on)
+  bool ok0, ok1;
+  int64_t off0, off1;
+  if (!sm.on) {
+    ok0 = y0 < ny_out;
+    ok1 = y0 + 1 < ny_out;
+    off0 = (int64_t)y0 * nx_out;
+    off1 = off0 + nx_out;
+  } else {
+    const int j0 = y0 < ny_out ? scan_index(y0, sm.oy, sm.sy, sm.my) : -1;
+    const int j1 = y0 + 1 < ny_out ? scan_index(y0 + 1, sm.oy, sm.sy, sm.my) : -1;
+    ok0 = j0 >= 0;
+    ok1 = j1 >= 0;
+    off0 = (int64_t)(ok0 ? j0 : 0) * sm.mx;
+    off1 = (int64_t)(ok1 ? j1 : 0) * sm.mx;
+  }
+  R* dslice = out + s * out_stride;
+  const R* sslice = sub ? sub + s * out_stride : nullptr;
   double acc = 0.0;
   auto st = [&](int x, cx<R> z) {
-    if (x >= nx_out || !ok0) return;
-    R r0 = z.x, r1 = z.y;
-    if (s0) {
-      r0 -= s0[x];
-      acc += (double)r0 * (double)r0;
+    if (x >= nx_out) return;
+    int xi = x;
+    if (sm.on) {
+      xi = scan_index(x, sm.ox, sm.sx, sm.mx);
+      if (xi < 0) return;
     }
-    d0[x] = r0;
+    if (ok0) {
+      R r0 = z.x;
+      if (sslice) {
+        r0 -= sslice[off0 + xi];
+        acc += (double)r0 * (double)r0;
+      }
+      dslice[off0 + xi] = r0;
+    }
     if (ok1) {
-      if (s0) {
-        r1 -= s0[nx_out + x];
+      R r1 = z.y;
+      if (sslice) {
+        r1 -= sslice[off1 + xi];
         acc += (double)r1 * (double)r1;
       }
-      d0[nx_out + x] = r1;
+      dslice[off1 + xi] = r1;
     }
   };
   SmemLoad<R> ld;
@@ -398,14 +453,14 @@ cudaError_t set_smem_attr(const void* fn) {
 // ---- dispatch on the transform length ---------------------------------------
 template <typename R, int P>
 cudaError_t row_r2c(const R* in, int64_t in_stride, int nx_in, int ny_in, cx<R>* T, int tstride,
-                    int64_t tslice, int S, const cx<R>* tw, cudaStream_t st) {
+                    int64_t tslice, int S, const cx<R>* tw, cudaStream_t st, Samp sm) {
   using SH = Shape<P>;
   cudaError_t e = set_smem_attr<R, P>((const void*)k_row_r2c<R, P>);
   if (e != cudaSuccess) return e;
   const int pairs = (ny_in + 1) / 2;
   dim3 grid((pairs + SH::VPB - 1) / SH::VPB, S);
   k_row_r2c<R, P><<<grid, kThreads, smem_bytes<R, P>(), st>>>(in, in_stride, nx_in, ny_in, T,
-                                                                tstride, tslice, tw);
+                                                                tstride, tslice, tw, sm);
   return cudaGetLastError();
 }
 
@@ -438,7 +493,7 @@ cudaError_t col_inv(const cx<R>* in, int64_t in_stride, int ncols, int S, cx<R>*
 template <typename R, int P>
 cudaError_t row_c2r(const cx<R>* T, int tstride, int64_t tslice, int nx_out, int ny_out, R* out,
                     int64_t out_stride, int S, const R* sub, double* partials, const cx<R>* tw,
-                    cudaStream_t st, int* nblocks) {
+                    cudaStream_t st, int* nblocks, Samp sm) {
   using SH = Shape<P>;
   cudaError_t e = set_smem_attr<R, P>((const void*)k_row_c2r<R, P>);
   if (e != cudaSuccess) return e;
@@ -446,7 +501,7 @@ cudaError_t row_c2r(const cx<R>* T, int tstride, int64_t tslice, int nx_out, int
   dim3 grid((pairs + SH::VPB - 1) / SH::VPB, S);
   *nblocks = (int)(grid.x * grid.y);
   k_row_c2r<R, P><<<grid, kThreads, smem_bytes<R, P>(), st>>>(
-      T, tstride, tslice, nx_out, ny_out, out, out_stride, sub, partials, tw);
+      T, tstride, tslice, nx_out, ny_out, out, out_stride, sub, partials, tw, sm);
   return cudaGetLastError();
 }
 
@@ -464,7 +519,7 @@ cudaError_t row_c2r(const cx<R>* T, int tstride, int64_t tslice, int nx_out, int
 
 template <typename R>
 cudaError_t spectrum_t(const Plan& p, const R* in, int64_t in_stride, int nx_in, int ny_in,
-                       cx<R>* out, int64_t out_stride, int S, cudaStream_t st) {
+                       cx<R>* out, int64_t out_stride, int S, cudaStream_t st, Samp sm) {
   const Layout& L = p.L;
   const int tstride = ny_in + (ny_in & 1);
   const int64_t tslice = (int64_t)(L.px / 2 + 1) * tstride;
@@ -473,7 +528,8 @@ cudaError_t spectrum_t(const Plan& p, const R* in, int64_t in_stride, int nx_in,
   const cx<R>* twy = static_cast<const cx<R>*>(p.twy);
   cudaError_t e;
   auto row = [&]() -> cudaError_t {
-    PAT_P_SWITCH(L.px, (row_r2c<R, P_>(in, in_stride, nx_in, ny_in, T, tstride, tslice, S, twx, st)))
+    PAT_P_SWITCH(L.px, (row_r2c<R, P_>(in, in_stride, nx_in, ny_in, T, tstride, tslice, S, twx, st,
+                                        sm)))
   };
   if ((e = row()) != cudaSuccess) return e;
   auto col = [&]() -> cudaError_t {
@@ -486,7 +542,7 @@ cudaError_t spectrum_t(const Plan& p, const R* in, int64_t in_stride, int nx_in,
 template <typename R>
 cudaError_t image_t(const Plan& p, const cx<R>* in, int64_t in_stride, R* out, int64_t out_stride,
                     int S, const R* sub, double* sumsq, cudaStream_t st, int groups,
-                    double* group_sums) {
+                    double* group_sums, Samp sm) {
   const Layout& L = p.L;
   cx<R>* T = static_cast<cx<R>*>(p.T);
   const cx<R>* twx = static_cast<const cx<R>*>(p.twx);
@@ -502,7 +558,7 @@ cudaError_t image_t(const Plan& p, const cx<R>* in, int64_t in_stride, R* out, i
   double* partials = (sumsq || grouped) ? p.red : nullptr;
   auto row = [&]() -> cudaError_t {
     PAT_P_SWITCH(L.px, (row_c2r<R, P_>(T, L.tstride, L.tslice, L.nx, L.ny, out, out_stride, S, sub,
-                                        partials, twx, st, &nblocks)))
+                                        partials, twx, st, &nblocks, sm)))
   };
   if ((e = row()) != cudaSuccess) return e;
   // partials are slice-major, so each group of S / groups slices owns a
@@ -515,26 +571,26 @@ cudaError_t image_t(const Plan& p, const cx<R>* in, int64_t in_stride, R* out, i
 }  // namespace
 
 cudaError_t launch_spectrum(const Plan& p, const void* in, int64_t in_stride, int nx_in, int ny_in,
-                            void* out, int64_t out_stride, int S, cudaStream_t s) {
+                            void* out, int64_t out_stride, int S, cudaStream_t s, Samp sm) {
   if (S <= 0) return cudaSuccess;
   if (p.L.fp64)
     return spectrum_t<double>(p, static_cast<const double*>(in), in_stride, nx_in, ny_in,
-                              static_cast<cx<double>*>(out), out_stride, S, s);
+                              static_cast<cx<double>*>(out), out_stride, S, s, sm);
   return spectrum_t<float>(p, static_cast<const float*>(in), in_stride, nx_in, ny_in,
-                           static_cast<cx<float>*>(out), out_stride, S, s);
+                           static_cast<cx<float>*>(out), out_stride, S, s, sm);
 }
 
 cudaError_t launch_image(const Plan& p, const void* in, int64_t in_stride, void* out,
                          int64_t out_stride, int S, const void* sub, double* sumsq,
-                         cudaStream_t s, int groups, double* group_sums) {
+                         cudaStream_t s, int groups, double* group_sums, Samp sm) {
   if (S <= 0) return cudaSuccess;
   if (p.L.fp64)
     return image_t<double>(p, static_cast<const cx<double>*>(in), in_stride,
                            static_cast<double*>(out), out_stride, S,
-                           static_cast<const double*>(sub), sumsq, s, groups, group_sums);
+                           static_cast<const double*>(sub), sumsq, s, groups, group_sums, sm);
   return image_t<float>(p, static_cast<const cx<float>*>(in), in_stride, static_cast<float*>(out),
                         out_stride, S, static_cast<const float*>(sub), sumsq, s, groups,
-                        group_sums);
+                        group_sums, sm);
 }
 
 }  // namespace pat

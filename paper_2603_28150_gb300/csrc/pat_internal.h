@@ -83,7 +83,28 @@ struct Layout {
   // representative (a, b), 0 <= a <= b <= P/2, shared by up to 4 bins.
   bool fold = false;
   int64_t U = 0, Upad = 0, nub = 0;  // representatives, padded to 32, blocks of 32
+  // Measurement operator: data live on the scan grid x = ox + sx i, y = oy + sy j
+  // (i < mx, j < my) of the sensor grid; sx = sy = 1 is the plain operator.
+  int sx = 1, sy = 1, ox = 0, oy = 0, mx = 0, my = 0;
 };
+
+// Sampling pattern handed to the row kernels (identity when s.on == false).
+struct Samp {
+  bool on;
+  int sx, sy, ox, oy, mx, my;
+};
+inline Samp sampling_of(const Layout& L) {
+  Samp s;
+  s.on = L.sx != 1 || L.sy != 1 || L.ox != 0 || L.oy != 0;
+  s.sx = L.sx;
+  s.sy = L.sy;
+  s.ox = L.ox;
+  s.oy = L.oy;
+  s.mx = L.mx;
+  s.my = L.my;
+  return s;
+}
+inline Samp no_sampling() { return Samp{false, 1, 1, 0, 0, 0, 0}; }
 
 struct Graph;  // CUDA-graph cache (api.cu)
 
@@ -196,13 +217,15 @@ int cuda_fail(cudaError_t e, const char* what);
 // length nx_in valid of px, ny_in valid rows of py) -> spectra [S][px/2+1][py]
 // with slice stride out_stride complex elements.
 cudaError_t launch_spectrum(const Plan& p, const void* in, int64_t in_stride, int nx_in, int ny_in,
-                            void* out, int64_t out_stride, int S, cudaStream_t s);
+                            void* out, int64_t out_stride, int S, cudaStream_t s,
+                            Samp samp = no_sampling());
 // Stage iii: spectra [S][px/2+1][py] -> real [S][ny][nx] (crop), optionally
 // out = image - sub (sub has out's layout) with sum of squares added to
 // *sumsq (FP64, via the plan's reduction scratch when sumsq != nullptr).
 cudaError_t launch_image(const Plan& p, const void* in, int64_t in_stride, void* out,
                          int64_t out_stride, int S, const void* sub, double* sumsq,
-                         cudaStream_t s, int groups = 0, double* group_sums = nullptr);
+                         cudaStream_t s, int groups = 0, double* group_sums = nullptr,
+                         Samp samp = no_sampling());
 // Contractions over the resident table (tensor cores when the plan has the
 // split tables and batch >= tc_min_batch).
 cudaError_t launch_contract_fwd(const Plan& p, const void* X, void* Y, int batch, cudaStream_t s);

@@ -67,7 +67,7 @@ __global__ void k_slot_copy(Slots sl, int dst, int src) {
 }
 
 size_t vol_bytes(const Layout& L) { return (size_t)L.nz * L.ny * L.nx * L.rsize; }
-size_t dat_bytes(const Layout& L) { return (size_t)L.nt * L.ny * L.nx * L.rsize; }
+size_t dat_bytes(const Layout& L) { return (size_t)L.nt * L.my * L.mx * L.rsize; }
 
 cudaError_t slot_step(pat_plan* pp, int n, cudaStream_t s) {
   Plan& p = pp->p;

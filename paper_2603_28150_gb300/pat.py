@@ -43,7 +43,7 @@ EXPORTS = (
     "pat_fista_solve", "pat_dot_f64", "pat_stage_spectrum", "pat_stage_image",
     "pat_stage_contract", "pat_spectrum_noalloc", "pat_plan_estimate", "pat_slot_load",
     "pat_slot_move", "pat_slots_step", "pat_slot_read", "pat_plan_set_tensor_batch",
-    "pat_plan_check",
+    "pat_plan_check", "pat_plan_set_sampling",
 )
 
 
@@ -128,6 +128,7 @@ def lib(build_if_missing: bool = True):
         "pat_slot_read": ([P, I, V, D, P], I),
         "pat_plan_set_tensor_batch": ([P, I], I),
         "pat_plan_check": ([P], I),
+        "pat_plan_set_sampling": ([P, I, I, I, I], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -193,6 +194,8 @@ class Plan:
                  bf16_split: bool = False, fold: bool = True, stream=None):
         L = lib()
         self.nx, self.ny, self.nz, self.nt = nx, ny, nz, nt
+        self.mx, self.my = nx, ny          # scan grid of the data (see set_sampling)
+        self.sampling = (1, 1, 0, 0)
         self.px = px if px is not None else _pow2_at_least(2 * nx)
         self.py = py if py is not None else _pow2_at_least(2 * ny)
         self.max_batch = max_batch
@@ -227,6 +230,16 @@ class Plan:
         """Batches >= min_batch use the tensor-core contraction (0 = never)."""
         _check(lib().pat_plan_set_tensor_batch(self._h, min_batch))
 
+    def set_sampling(self, sx: int = 1, sy: int = 1, ox: int = 0, oy: int = 0) -> None:
+        """Measurement operator (Sec. 2.3, 3.3): data are kept only at the scan
+        positions x = ox + sx i, y = oy + sy j of the sensor grid, so forward is
+        S H (data [nt][my][mx]) and adjoint H* S^T (zero-filled). (1, 1, 0, 0)
+        is the plain operator. Data loaded into slots must be reloaded."""
+        _check(lib().pat_plan_set_sampling(self._h, sx, sy, ox, oy))
+        self.sampling = (sx, sy, ox, oy)
+        self.mx = -(-(self.nx - ox) // sx)
+        self.my = -(-(self.ny - oy) // sy)
+
     def check(self) -> None:
         """Raises PatError(PAT_ERR_TIMEOUT) if a bounded device wait gave up."""
         _check(lib().pat_plan_check(self._h))
@@ -250,7 +263,7 @@ class Plan:
         return (batch, self.nz, self.ny, self.nx)
 
     def data_shape(self, batch: int = 1):
-        return (batch, self.nt, self.ny, self.nx)
+        return (batch, self.nt, self.my, self.mx)
 
     def _batch_of(self, a, per) -> int:
         n = int(np.prod(a.shape))
@@ -284,7 +297,7 @@ class Plan:
     def adjoint(self, d, out=None, stream=None):
         """rho = H* d (Eq. 11)."""
         self._check_dtype(d)
-        b = self._batch_of(d, self.nt * self.ny * self.nx)
+        b = self._batch_of(d, self.nt * self.my * self.mx)
         if out is None:
             out = self._empty_like_device(self.obj_shape(b) if d.ndim == 4 else
                                           self.obj_shape(1)[1:], d)
@@ -313,7 +326,7 @@ class Plan:
               power_iters: int = 50, warm_start: bool = False, stream=None):
         """FISTA for Eq. 12-14; returns (x, report dict)."""
         self._check_dtype(y)
-        b = self._batch_of(y, self.nt * self.ny * self.nx)
+        b = self._batch_of(y, self.nt * self.my * self.mx)
         if x is None:
             x = self._empty_like_device(self.obj_shape(b) if y.ndim == 4 else
                                         self.obj_shape(1)[1:], y)
@@ -336,7 +349,7 @@ class Plan:
 
     # ------------------------------------------------------------------ slots
     def slot_load(self, slot: int, y, lam: float, L: float, stream=None) -> None:
-        """Loads one FISTA request (data y [nt][ny][nx]) into `slot`."""
+        """Loads one FISTA request (data y [nt][my][mx]) into `slot`."""
         self._check_dtype(y)
         _check(lib().pat_slot_load(self._h, slot, _ptr(y), lam, L, _stream(stream)))
 
