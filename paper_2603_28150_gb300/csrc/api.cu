@@ -153,7 +153,8 @@ int alloc_workspace(pat_plan* pp) {
   PAT_CUDA(cudaMalloc(&p.red, sizeof(double) * x.c2r_partials));
   PAT_CUDA(cudaMalloc(&x.res, sizeof(double) * 8));
   PAT_CUDA(cudaMalloc(&x.scal, sizeof(double) * 2));
-  PAT_CUDA(cudaMalloc(&p.iter_dev, sizeof(int)));
+  PAT_CUDA(cudaMalloc(&p.iter_dev, 2 * sizeof(int)));
+  PAT_CUDA(cudaMemset(p.iter_dev, 0, 2 * sizeof(int)));
   const size_t sb = sizeof(double) * L.max_batch;
   PAT_CUDA(cudaMalloc(&x.slots.t, sb));
   PAT_CUDA(cudaMalloc(&x.slots.beta, sb));
@@ -316,12 +317,6 @@ __global__ void k_fill_hash(R* v, int64_t n, unsigned long long seed) {
   }
 }
 
-__global__ void k_record_tick(int* iter, const double* r2_cur, double* r2_hist, int cap) {
-  const int k = *iter;
-  if (k < cap) r2_hist[k] = *r2_cur;
-  *iter = k + 1;
-}
-
 // Power iteration on the plan's buffers: v in vol_a (normalised here first).
 int power_dev(pat_plan* pp, int iters, double* L_out, cudaStream_t s) {
   Plan& p = pp->p;
@@ -352,11 +347,9 @@ cudaError_t fista_iter(pat_plan* pp, int batch, cudaStream_t s) {
   cudaError_t e = forward_dev(p, p.vol_a, p.dat_a, batch, s, p.dat_b, x.res + 1);
   if (e != cudaSuccess) return e;
   if ((e = adjoint_dev(p, p.dat_a, p.vol_c, batch, s)) != cudaSuccess) return e;
-  if ((e = launch_fista_update(p, p.vol_a, p.vol_b, p.vol_c, (int64_t)obj_elems(L, batch),
-                                   x.scal, p.betas, p.iter_dev, s)) != cudaSuccess)
-    return e;
-  k_record_tick<<<1, 1, 0, s>>>(p.iter_dev, x.res + 1, p.r2_dev, p.r2_cap);
-  return cudaGetLastError();
+  return launch_fista_update(p, p.vol_a, p.vol_b, p.vol_c, (int64_t)obj_elems(L, batch), x.scal,
+                             p.betas, p.iter_dev, x.res + 1, p.r2_dev, p.r2_cap,
+                             reinterpret_cast<unsigned*>(p.iter_dev + 1), s);
 }
 
 Graph* graph_for(pat_plan* pp, int batch, int* rc) {

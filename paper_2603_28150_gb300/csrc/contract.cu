@@ -99,6 +99,7 @@ __global__ void __launch_bounds__(kWarps * 32)
   const int64_t k = kb * 32 + lane;
   const int b0 = blockIdx.y * VB;
   const int nzp = nzg * ZG;
+  pdl_wait();
   for (int i = threadIdx.x; i < VB * nzp * 32; i += blockDim.x) {
     const int l = i & 31, z = (i >> 5) % nzp, v = (i >> 5) / nzp;
     const int64_t kk = kb * 32 + l;
@@ -157,6 +158,7 @@ __global__ void __launch_bounds__(kWarps * 32, (sizeof(R) == 4 && !CPLX && VB ==
       for (int v = 0; v < VB; ++v) acc[j][q][v] = mk<R>(0, 0);
   const bool kok = k < K;
   const V* tb = table + (kb * nt) * (int64_t)nzg * 32 + lane;
+  pdl_wait();
 #pragma unroll 1
   for (int t = 0; t < nt; ++t) {
     cx<R> d[VB];
@@ -216,6 +218,7 @@ __global__ void __launch_bounds__(kWarps * 32, 2)
   const int4 mem = u < U ? members[u] : make_int4(-1, -1, -1, -1);
   const int bins[4] = {mem.x, mem.y, mem.z, mem.w};
   const cx<float>* Xb = X + (int64_t)b * nz * Kpad;
+  pdl_wait();
   for (int z = warp; z < nzp; z += kWarps) {
 #pragma unroll
     for (int m = 0; m < 4; ++m)
@@ -287,6 +290,7 @@ __global__ void __launch_bounds__(kWarps * 32, 2)
     for (int q = 0; q < 4; ++q)
 #pragma unroll
       for (int m = 0; m < 4; ++m) acc[j][q][m] = mk<float>(0.f, 0.f);
+  pdl_wait();
   for (int t0 = 0; t0 < nt; t0 += kTC) {
     __syncthreads();
     for (int tt = warp; tt < kTC; tt += kWarps) {
@@ -350,11 +354,10 @@ cudaError_t fold_fwd(const Plan& p, const void* X, void* Y, int batch, cudaStrea
     if (e != cudaSuccess) return e;
   }
   dim3 grid((unsigned)L.nub, (unsigned)batch);
-  k_fold_fwd<<<grid, kWarps * 32, smem, s>>>(
-      static_cast<const float4*>(p.table), reinterpret_cast<const int4*>(p.fold_members),
-      static_cast<const cx<float>*>(X), static_cast<cx<float>*>(Y), L.nz, L.nt, L.nzg, L.U,
-      L.Kpad);
-  return cudaGetLastError();
+  return launch_pdl(k_fold_fwd, grid, dim3(kWarps * 32), smem, s,
+                    static_cast<const float4*>(p.table),
+                    reinterpret_cast<const int4*>(p.fold_members), static_cast<const cx<float>*>(X),
+                    static_cast<cx<float>*>(Y), L.nz, L.nt, L.nzg, L.U, L.Kpad);
 }
 
 cudaError_t fold_adj(const Plan& p, const void* D, void* Z, int batch, cudaStream_t s) {
@@ -362,11 +365,10 @@ cudaError_t fold_adj(const Plan& p, const void* D, void* Z, int batch, cudaStrea
   constexpr int GPW = 2;
   dim3 grid((unsigned)L.nub, (unsigned)batch,
             (unsigned)((L.nzg + kWarps * GPW - 1) / (kWarps * GPW)));
-  k_fold_adj<GPW><<<grid, kWarps * 32, 0, s>>>(
-      static_cast<const float4*>(p.table), reinterpret_cast<const int4*>(p.fold_members),
-      static_cast<const cx<float>*>(D), static_cast<cx<float>*>(Z), L.nz, L.nt, L.nzg, L.U,
-      L.Kpad);
-  return cudaGetLastError();
+  return launch_pdl(k_fold_adj<GPW>, grid, dim3(kWarps * 32), 0, s,
+                    static_cast<const float4*>(p.table),
+                    reinterpret_cast<const int4*>(p.fold_members), static_cast<const cx<float>*>(D),
+                    static_cast<cx<float>*>(Z), L.nz, L.nt, L.nzg, L.U, L.Kpad);
 }
 
 template <typename R, bool CPLX, int VB>
@@ -381,10 +383,10 @@ cudaError_t fwd_t(const Plan& p, const void* X, void* Y, int batch, cudaStream_t
     if (e != cudaSuccess) return e;
   }
   dim3 grid((unsigned)L.nkb, (unsigned)((batch + VB - 1) / VB));
-  fn<<<grid, kWarps * 32, smem, s>>>(static_cast<const typename vec16<R>::type*>(p.table),
-                                     static_cast<const cx<R>*>(X), static_cast<cx<R>*>(Y), L.nz,
-                                     L.nt, L.nzg, L.K, L.Kpad, batch);
-  return cudaGetLastError();
+  return launch_pdl(fn, grid, dim3(kWarps * 32), smem, s,
+                    static_cast<const typename vec16<R>::type*>(p.table),
+                    static_cast<const cx<R>*>(X), static_cast<cx<R>*>(Y), L.nz, L.nt, L.nzg, L.K,
+                    L.Kpad, batch);
 }
 
 template <typename R, bool CPLX, int VB, int GPW>
@@ -393,10 +395,10 @@ cudaError_t adj_launch(const Plan& p, const void* D, void* Z, int batch, cudaStr
   const int per_chunk = kWarps * GPW;
   dim3 grid((unsigned)L.nkb, (unsigned)((batch + VB - 1) / VB),
             (unsigned)((L.nzg + per_chunk - 1) / per_chunk));
-  k_contract_adj<R, CPLX, VB, GPW><<<grid, kWarps * 32, 0, s>>>(
-      static_cast<const typename vec16<R>::type*>(p.table), static_cast<const cx<R>*>(D),
-      static_cast<cx<R>*>(Z), L.nz, L.nt, L.nzg, L.K, L.Kpad, batch);
-  return cudaGetLastError();
+  return launch_pdl(k_contract_adj<R, CPLX, VB, GPW>, grid, dim3(kWarps * 32), 0, s,
+                    static_cast<const typename vec16<R>::type*>(p.table),
+                    static_cast<const cx<R>*>(D), static_cast<cx<R>*>(Z), L.nz, L.nt, L.nzg, L.K,
+                    L.Kpad, batch);
 }
 
 template <typename R, bool CPLX, int VB>

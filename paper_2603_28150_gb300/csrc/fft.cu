@@ -216,7 +216,7 @@ __device__ __forceinline__ int scan_index(int c, int o, int st, int n) {
 // T[s][kx][y] for kx in [0, P/2]. With sampling on, the slice is the
 // zero-filled image of scan-grid data in[s][my][mx] (the adjoint of the
 // measurement operator, Sec. 3.3).
-template <typename R, int P>
+template <typename R, int P, bool SAMP>
 __global__ void __launch_bounds__(kThreads) k_row_r2c(const R* __restrict__ in, int64_t in_stride,
                                                       int nx_in, int ny_in, cx<R>* __restrict__ T,
                                                       int tstride, int64_t tslice,
@@ -232,7 +232,7 @@ __global__ void __launch_bounds__(kThreads) k_row_r2c(const R* __restrict__ in, 
   const R* row0;
   const R* row1;
   bool ok0, ok1;
-  if (!sm.on) {
+  if (!SAMP) {
     ok0 = y0 < ny_in;
     ok1 = y0 + 1 < ny_in;
     row0 = base + (int64_t)y0 * nx_in;
@@ -245,12 +245,13 @@ __global__ void __launch_bounds__(kThreads) k_row_r2c(const R* __restrict__ in, 
     row0 = base + (int64_t)(ok0 ? j0 : 0) * sm.mx;
     row1 = base + (int64_t)(ok1 ? j1 : 0) * sm.mx;
   }
+  pdl_wait();
   __syncthreads();  // twiddles staged
   auto ld = [&](int x) -> cx<R> {
     R a = 0, b = 0;
     if (x < nx_in) {
       int xi = x;
-      if (sm.on) xi = scan_index(x, sm.ox, sm.sx, sm.mx);
+      if (SAMP) xi = scan_index(x, sm.ox, sm.sx, sm.mx);
       if (xi >= 0) {
         if (ok0) a = row0[xi];
         if (ok1) b = row1[xi];
@@ -294,6 +295,7 @@ __global__ void __launch_bounds__(kThreads) k_col_fwd(const cx<R>* __restrict__ 
   const int64_t s = ok ? g / ncols : 0, kx = ok ? g % ncols : 0;
   const cx<R>* src = T + s * tslice + kx * tstride;
   cx<R>* dst = out + s * out_stride + kx * P;
+  pdl_wait();
   __syncthreads();
   auto ld = [&](int y) -> cx<R> { return (ok && y < n_in) ? src[y] : mk<R>(0, 0); };
   auto st = [&](int y, cx<R> val) {
@@ -319,6 +321,7 @@ __global__ void __launch_bounds__(kThreads) k_col_inv(const cx<R>* __restrict__ 
   const int64_t s = ok ? g / ncols : 0, kx = ok ? g % ncols : 0;
   const cx<R>* src = in + s * in_stride + kx * P;
   cx<R>* dst = T + s * tslice + kx * tstride;
+  pdl_wait();
   __syncthreads();
   auto ld = [&](int y) -> cx<R> { return ok ? src[y] : mk<R>(0, 0); };
   auto st = [&](int y, cx<R> val) {
@@ -334,7 +337,7 @@ __global__ void __launch_bounds__(kThreads) k_col_inv(const cx<R>* __restrict__ 
 // image - sub and accumulates its squares (FP64) per block into partials.
 // With sampling on, only the scan positions are kept, written compactly to
 // out[s][my][mx] (the measurement operator of Sec. 3.3); `sub` has that layout.
-template <typename R, int P>
+template <typename R, int P, bool SAMP>
 __global__ void __launch_bounds__(kThreads) k_row_c2r(const cx<R>* __restrict__ T, int tstride,
                                                       int64_t tslice, int nx_out, int ny_out,
                                                       R* __restrict__ out, int64_t out_stride,
@@ -348,6 +351,7 @@ __global__ void __launch_bounds__(kThreads) k_row_c2r(const cx<R>* __restrict__ 
   const int64_t s = blockIdx.y;
   const int pair0 = blockIdx.x * SH::VPB;
   const cx<R>* src = T + s * tslice;
+  pdl_wait();
   // all global loads first (independent, in flight together), then the
   // Hermitian packing into shared memory
   constexpr int NH = SH::VPB * (P / 2 + 1);
@@ -388,7 +392,7 @@ __global__ void __launch_bounds__(kThreads) k_row_c2r(const cx<R>* __restrict__ 
   // destination rows (compact scan rows with sampling on)
   bool ok0, ok1;
   int64_t off0, off1;
-  if (!sm.on) {
+  if (!SAMP) {
     ok0 = y0 < ny_out;
     ok1 = y0 + 1 < ny_out;
     off0 = (int64_t)y0 * nx_out;
@@ -407,7 +411,7 @@ __global__ void __launch_bounds__(kThreads) k_row_c2r(const cx<R>* __restrict__ 
   auto st = [&](int x, cx<R> z) {
     if (x >= nx_out) return;
     int xi = x;
-    if (sm.on) {
+    if (SAMP) {
       xi = scan_index(x, sm.ox, sm.sx, sm.mx);
       if (xi < 0) return;
     }
@@ -455,13 +459,13 @@ template <typename R, int P>
 cudaError_t row_r2c(const R* in, int64_t in_stride, int nx_in, int ny_in, cx<R>* T, int tstride,
                     int64_t tslice, int S, const cx<R>* tw, cudaStream_t st, Samp sm) {
   using SH = Shape<P>;
-  cudaError_t e = set_smem_attr<R, P>((const void*)k_row_r2c<R, P>);
+  auto fn = sm.on ? k_row_r2c<R, P, true> : k_row_r2c<R, P, false>;
+  cudaError_t e = set_smem_attr<R, P>((const void*)fn);
   if (e != cudaSuccess) return e;
   const int pairs = (ny_in + 1) / 2;
   dim3 grid((pairs + SH::VPB - 1) / SH::VPB, S);
-  k_row_r2c<R, P><<<grid, kThreads, smem_bytes<R, P>(), st>>>(in, in_stride, nx_in, ny_in, T,
-                                                                tstride, tslice, tw, sm);
-  return cudaGetLastError();
+  return launch_pdl(fn, grid, dim3(kThreads), smem_bytes<R, P>(), st, in, in_stride, nx_in, ny_in,
+                    T, tstride, tslice, tw, sm);
 }
 
 template <typename R, int P>
@@ -472,9 +476,8 @@ cudaError_t col_fwd(const cx<R>* T, int tstride, int64_t tslice, int n_in, int n
   if (e != cudaSuccess) return e;
   const int64_t nvec = (int64_t)S * ncols;
   const int64_t blocks = (nvec + SH::VPB - 1) / SH::VPB;
-  k_col_fwd<R, P><<<(unsigned)blocks, kThreads, smem_bytes<R, P>(), st>>>(
-      T, tstride, tslice, n_in, ncols, nvec, out, out_stride, tw);
-  return cudaGetLastError();
+  return launch_pdl(k_col_fwd<R, P>, dim3((unsigned)blocks), dim3(kThreads), smem_bytes<R, P>(), st,
+                    T, tstride, tslice, n_in, ncols, nvec, out, out_stride, tw);
 }
 
 template <typename R, int P>
@@ -485,9 +488,8 @@ cudaError_t col_inv(const cx<R>* in, int64_t in_stride, int ncols, int S, cx<R>*
   if (e != cudaSuccess) return e;
   const int64_t nvec = (int64_t)S * ncols;
   const int64_t blocks = (nvec + SH::VPB - 1) / SH::VPB;
-  k_col_inv<R, P><<<(unsigned)blocks, kThreads, smem_bytes<R, P>(), st>>>(
-      in, in_stride, ncols, nvec, T, tstride, tslice, n_out, tw);
-  return cudaGetLastError();
+  return launch_pdl(k_col_inv<R, P>, dim3((unsigned)blocks), dim3(kThreads), smem_bytes<R, P>(), st,
+                    in, in_stride, ncols, nvec, T, tstride, tslice, n_out, tw);
 }
 
 template <typename R, int P>
@@ -495,14 +497,14 @@ cudaError_t row_c2r(const cx<R>* T, int tstride, int64_t tslice, int nx_out, int
                     int64_t out_stride, int S, const R* sub, double* partials, const cx<R>* tw,
                     cudaStream_t st, int* nblocks, Samp sm) {
   using SH = Shape<P>;
-  cudaError_t e = set_smem_attr<R, P>((const void*)k_row_c2r<R, P>);
+  auto fn = sm.on ? k_row_c2r<R, P, true> : k_row_c2r<R, P, false>;
+  cudaError_t e = set_smem_attr<R, P>((const void*)fn);
   if (e != cudaSuccess) return e;
   const int pairs = (ny_out + 1) / 2;
   dim3 grid((pairs + SH::VPB - 1) / SH::VPB, S);
   *nblocks = (int)(grid.x * grid.y);
-  k_row_c2r<R, P><<<grid, kThreads, smem_bytes<R, P>(), st>>>(
-      T, tstride, tslice, nx_out, ny_out, out, out_stride, sub, partials, tw, sm);
-  return cudaGetLastError();
+  return launch_pdl(fn, grid, dim3(kThreads), smem_bytes<R, P>(), st, T, tstride, tslice, nx_out,
+                    ny_out, out, out_stride, sub, partials, tw, sm);
 }
 
 #define PAT_P_SWITCH(PV, CALL)                           \

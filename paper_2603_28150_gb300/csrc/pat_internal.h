@@ -106,6 +106,36 @@ inline Samp sampling_of(const Layout& L) {
 }
 inline Samp no_sampling() { return Samp{false, 1, 1, 0, 0, 0, 0}; }
 
+// ---- programmatic dependent launch ------------------------------------------
+// The kernels of the operator and FISTA path are launched with launch_pdl: a
+// kernel's blocks may be scheduled as the blocks of the previous kernel in its
+// stream exit, do their prologue (index arithmetic, reads of plan constants
+// such as twiddles and fold maps), then wait in pdl_wait() until the previous
+// grid has completed and its writes are visible. Every kernel launched this
+// way calls pdl_wait() before it touches any buffer that another kernel reads
+// or writes. (Blocks do not signal their dependents early: measured on the
+// bench geometry, an early signal let waiting blocks crowd the running
+// contraction and cost more than the launch latency it hid.)
+__device__ __forceinline__ void pdl_wait() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                       cudaStream_t s, Args... args) {
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 struct Graph;  // CUDA-graph cache (api.cu)
 
 struct Plan {
@@ -127,7 +157,7 @@ struct Plan {
   unsigned int* red_counter = nullptr;
   double* betas = nullptr;  // FISTA momentum coefficients per iteration
   int betas_cap = 0;
-  int* iter_dev = nullptr;  // FISTA iteration counter (graph replay)
+  int* iter_dev = nullptr;  // [0] FISTA iteration counter (graph replay), [1] block counter
   double* r2_dev = nullptr; // FISTA residual norms per iteration
   int r2_cap = 0;
   Graph* graphs = nullptr;
@@ -272,9 +302,12 @@ cudaError_t launch_partials_sum(const double* partials, int n, double* out, cuda
 // out[g] = sum of partials[g * per, (g + 1) * per) for g < groups (in order, FP64).
 cudaError_t launch_group_sums(const double* partials, int per, int groups, double* out,
                               cudaStream_t s);
-// FISTA step; scal = {1/L, lambda/L}, beta_k = betas[*iter] (device memory).
+// FISTA step; scal = {1/L, lambda/L}, beta_k = betas[*iter] (device memory);
+// then r2_hist[*iter] = *r2_cur (if *iter < cap) and ++*iter, by the last
+// block to finish (`done`: a zero-initialised counter the kernel resets).
 cudaError_t launch_fista_update(const Plan& p, void* y, void* xprev, const void* grad, int64_t n,
-                                const double* scal, const double* betas, const int* iter,
+                                const double* scal, const double* betas, int* iter,
+                                const double* r2_cur, double* r2_hist, int cap, unsigned* done,
                                 cudaStream_t s);
 cudaError_t launch_scale_by_inv_norm(const Plan& p, const void* in, void* out, int64_t n,
                                      const double* sumsq_dev, cudaStream_t s);

@@ -26,6 +26,7 @@ __global__ void __launch_bounds__(256) k_slot_update(R* __restrict__ y, R* __res
                                                      int64_t n, const double* __restrict__ invL,
                                                      const double* __restrict__ lamL,
                                                      const double* __restrict__ beta) {
+  pdl_wait();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t s = i / vol;
@@ -80,16 +81,14 @@ cudaError_t slot_step(pat_plan* pp, int n, cudaStream_t s) {
   int64_t g = (tot + 255) / 256;
   if (g > 152 * 16) g = 152 * 16;
   if (L.fp64)
-    k_slot_update<double><<<(int)g, 256, 0, s>>>(static_cast<double*>(p.vol_a),
-                                                 static_cast<double*>(p.vol_b),
-                                                 static_cast<const double*>(p.vol_c), vol, tot,
-                                                 sl.invL, sl.lamL, sl.beta);
+    e = launch_pdl(k_slot_update<double>, dim3((unsigned)g), dim3(256), 0, s,
+                   static_cast<double*>(p.vol_a), static_cast<double*>(p.vol_b),
+                   static_cast<const double*>(p.vol_c), vol, tot, sl.invL, sl.lamL, sl.beta);
   else
-    k_slot_update<float><<<(int)g, 256, 0, s>>>(static_cast<float*>(p.vol_a),
-                                                static_cast<float*>(p.vol_b),
-                                                static_cast<const float*>(p.vol_c), vol, tot,
-                                                sl.invL, sl.lamL, sl.beta);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    e = launch_pdl(k_slot_update<float>, dim3((unsigned)g), dim3(256), 0, s,
+                   static_cast<float*>(p.vol_a), static_cast<float*>(p.vol_b),
+                   static_cast<const float*>(p.vol_c), vol, tot, sl.invL, sl.lamL, sl.beta);
+  if (e != cudaSuccess) return e;
   k_slot_tick<<<(n + 127) / 128, 128, 0, s>>>(sl.t, sl.beta, sl.k, n);
   return cudaGetLastError();
 }

@@ -28,6 +28,7 @@ __device__ __forceinline__ double block_sum(double v) {
 template <typename R>
 __global__ void __launch_bounds__(kBlock) k_dot(const R* __restrict__ a, const R* __restrict__ b,
                                                 int64_t n, double* __restrict__ partials) {
+  pdl_wait();
   double acc = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)kBlock + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * kBlock)
@@ -38,6 +39,7 @@ __global__ void __launch_bounds__(kBlock) k_dot(const R* __restrict__ a, const R
 
 __global__ void __launch_bounds__(1024) k_sum_partials(const double* __restrict__ partials, int n,
                                                        double* __restrict__ out) {
+  pdl_wait();
   double acc = 0.0;
   for (int i = threadIdx.x; i < n; i += 1024) acc += partials[i];
   const double s = block_sum(acc);
@@ -48,6 +50,7 @@ __global__ void __launch_bounds__(1024) k_sum_partials(const double* __restrict_
 __global__ void __launch_bounds__(256) k_group_sums(const double* __restrict__ partials, int per,
                                                     double* __restrict__ out) {
   const double* p = partials + (int64_t)blockIdx.x * per;
+  pdl_wait();
   double acc = 0.0;
   for (int i = threadIdx.x; i < per; i += 256) acc += p[i];
   const double s = block_sum(acc);
@@ -57,15 +60,22 @@ __global__ void __launch_bounds__(256) k_group_sums(const double* __restrict__ p
 // x_k = max(y - g/L - lambda/L, 0) (prox of Eq. 14 after the gradient step of
 // Eq. 15); y <- x_k + beta_k (x_k - x_{k-1}); xprev <- x_k. The scalars 1/L,
 // lambda/L (scal) and beta_k = betas[*iter] are read from device memory so one
-// captured graph serves every iteration.
+// captured graph serves every iteration. The last block to finish records
+// this iteration's ||H y_k - d||^2 (*r2_cur) in r2_hist[*iter] and advances
+// *iter (every block has read *iter before it counts itself done).
 template <typename R>
 __global__ void __launch_bounds__(kBlock) k_fista_update(R* __restrict__ y, R* __restrict__ xprev,
                                                          const R* __restrict__ grad, int64_t n,
                                                          const double* __restrict__ scal,
                                                          const double* __restrict__ betas,
-                                                         const int* __restrict__ iter) {
+                                                         int* __restrict__ iter,
+                                                         const double* __restrict__ r2_cur,
+                                                         double* __restrict__ r2_hist, int cap,
+                                                         unsigned* __restrict__ done) {
+  pdl_wait();
   const R invL = (R)scal[0], lamL = (R)scal[1];
-  const R beta = (R)betas[*iter];
+  const int k = *iter;
+  const R beta = (R)betas[k];
   for (int64_t i = blockIdx.x * (int64_t)kBlock + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * kBlock) {
     const R yv = y[i], g = grad[i], xp = xprev[i];
@@ -73,6 +83,18 @@ __global__ void __launch_bounds__(kBlock) k_fista_update(R* __restrict__ y, R* _
     x = x > (R)0 ? x : (R)0;
     y[i] = x + beta * (x - xp);
     xprev[i] = x;
+  }
+  __shared__ bool last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(done, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    if (k < cap) r2_hist[k] = *r2_cur;
+    *iter = k + 1;
+    *done = 0;
   }
 }
 
@@ -96,43 +118,39 @@ int grid_for(int64_t n, int cap) {
 }  // namespace
 
 cudaError_t launch_partials_sum(const double* partials, int n, double* out, cudaStream_t s) {
-  k_sum_partials<<<1, 1024, 0, s>>>(partials, n, out);
-  return cudaGetLastError();
+  return launch_pdl(k_sum_partials, dim3(1), dim3(1024), 0, s, partials, n, out);
 }
 
 cudaError_t launch_group_sums(const double* partials, int per, int groups, double* out,
                               cudaStream_t s) {
-  k_group_sums<<<groups, 256, 0, s>>>(partials, per, out);
-  return cudaGetLastError();
+  return launch_pdl(k_group_sums, dim3(groups), dim3(256), 0, s, partials, per, out);
 }
 
 cudaError_t launch_dot(const Plan& p, const void* a, const void* b, int64_t n, double* out_dev,
                        cudaStream_t s) {
   const int g = grid_for(n, kReduceBlocks);
-  if (p.L.fp64)
-    k_dot<double><<<g, kBlock, 0, s>>>(static_cast<const double*>(a), static_cast<const double*>(b),
-                                        n, p.red);
-  else
-    k_dot<float><<<g, kBlock, 0, s>>>(static_cast<const float*>(a), static_cast<const float*>(b), n,
-                                       p.red);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e =
+      p.L.fp64 ? launch_pdl(k_dot<double>, dim3(g), dim3(kBlock), 0, s,
+                            static_cast<const double*>(a), static_cast<const double*>(b), n, p.red)
+               : launch_pdl(k_dot<float>, dim3(g), dim3(kBlock), 0, s,
+                            static_cast<const float*>(a), static_cast<const float*>(b), n, p.red);
   if (e != cudaSuccess) return e;
   return launch_partials_sum(p.red, g, out_dev, s);
 }
 
 cudaError_t launch_fista_update(const Plan& p, void* y, void* xprev, const void* grad, int64_t n,
-                                const double* scal, const double* betas, const int* iter,
+                                const double* scal, const double* betas, int* iter,
+                                const double* r2_cur, double* r2_hist, int cap, unsigned* done,
                                 cudaStream_t s) {
   const int g = grid_for(n, 152 * 16);
   if (p.L.fp64)
-    k_fista_update<double><<<g, kBlock, 0, s>>>(static_cast<double*>(y), static_cast<double*>(xprev),
-                                                 static_cast<const double*>(grad), n, scal, betas,
-                                                 iter);
-  else
-    k_fista_update<float><<<g, kBlock, 0, s>>>(static_cast<float*>(y), static_cast<float*>(xprev),
-                                                static_cast<const float*>(grad), n, scal, betas,
-                                                iter);
-  return cudaGetLastError();
+    return launch_pdl(k_fista_update<double>, dim3(g), dim3(kBlock), 0, s,
+                      static_cast<double*>(y), static_cast<double*>(xprev),
+                      static_cast<const double*>(grad), n, scal, betas, iter, r2_cur, r2_hist, cap,
+                      done);
+  return launch_pdl(k_fista_update<float>, dim3(g), dim3(kBlock), 0, s, static_cast<float*>(y),
+                    static_cast<float*>(xprev), static_cast<const float*>(grad), n, scal, betas,
+                    iter, r2_cur, r2_hist, cap, done);
 }
 
 cudaError_t launch_scale_by_inv_norm(const Plan& p, const void* in, void* out, int64_t n,
