@@ -211,6 +211,135 @@ __device__ __forceinline__ int scan_index(int c, int o, int st, int n) {
   return i < n ? i : -1;
 }
 
+// Input of one packed row pair (rows y0, y0 + 1 of a slice, a + i b),
+// zero-padded from nx_in: the plain [ny][nx] slice, or with SAMP the
+// zero-filled image of scan-grid data [my][mx] (the adjoint of the measurement
+// operator, Sec. 3.3). Rows at or past ny_in read as zero.
+template <typename R, bool SAMP>
+struct RowPairLoad {
+  const R* row0;
+  const R* row1;
+  bool ok0, ok1;
+  int nx_in;
+  Samp sm;
+  __device__ __forceinline__ RowPairLoad(const R* base, int y0, int nx, int ny_in, Samp s)
+      : nx_in(nx), sm(s) {
+    if (!SAMP) {
+      ok0 = y0 < ny_in;
+      ok1 = y0 + 1 < ny_in;
+      row0 = base + (int64_t)y0 * nx_in;
+      row1 = row0 + nx_in;
+    } else {
+      const int j0 = y0 < ny_in ? scan_index(y0, sm.oy, sm.sy, sm.my) : -1;
+      const int j1 = y0 + 1 < ny_in ? scan_index(y0 + 1, sm.oy, sm.sy, sm.my) : -1;
+      ok0 = j0 >= 0;
+      ok1 = j1 >= 0;
+      row0 = base + (int64_t)(ok0 ? j0 : 0) * sm.mx;
+      row1 = base + (int64_t)(ok1 ? j1 : 0) * sm.mx;
+    }
+  }
+  __device__ __forceinline__ cx<R> operator()(int x) const {
+    R a = 0, b = 0;
+    if (x < nx_in) {
+      int xi = x;
+      if (SAMP) xi = scan_index(x, sm.ox, sm.sx, sm.mx);
+      if (xi >= 0) {
+        if (ok0) a = row0[xi];
+        if (ok1) b = row1[xi];
+      }
+    }
+    return mk<R>(a, b);
+  }
+};
+
+// Output of one row pair of an image slice from the packed inverse transform
+// (Re -> row y0, Im -> row y0 + 1), columns [0, nx_out) kept; with `sub`,
+// writes image - sub and accumulates its squares (FP64) in acc. With SAMP
+// only the scan positions are kept, written compactly to [my][mx] (the
+// measurement operator of Sec. 3.3); `sub` has that layout. Rows at or past
+// ny_out are not written.
+template <typename R, bool SAMP>
+struct RowPairStore {
+  R* dslice;
+  const R* sslice;
+  int64_t off0, off1;
+  bool ok0, ok1;
+  int nx_out;
+  Samp sm;
+  double acc = 0.0;
+  __device__ __forceinline__ RowPairStore(R* out_slice, const R* sub_slice, int y0, int nx,
+                                          int ny_out, Samp s)
+      : dslice(out_slice), sslice(sub_slice), nx_out(nx), sm(s) {
+    if (!SAMP) {
+      ok0 = y0 < ny_out;
+      ok1 = y0 + 1 < ny_out;
+      off0 = (int64_t)y0 * nx_out;
+      off1 = off0 + nx_out;
+    } else {
+      const int j0 = y0 < ny_out ? scan_index(y0, sm.oy, sm.sy, sm.my) : -1;
+      const int j1 = y0 + 1 < ny_out ? scan_index(y0 + 1, sm.oy, sm.sy, sm.my) : -1;
+      ok0 = j0 >= 0;
+      ok1 = j1 >= 0;
+      off0 = (int64_t)(ok0 ? j0 : 0) * sm.mx;
+      off1 = (int64_t)(ok1 ? j1 : 0) * sm.mx;
+    }
+  }
+  __device__ __forceinline__ void operator()(int x, cx<R> z) {
+    if (x >= nx_out) return;
+    int xi = x;
+    if (SAMP) {
+      xi = scan_index(x, sm.ox, sm.sx, sm.mx);
+      if (xi < 0) return;
+    }
+    if (ok0) {
+      R r0 = z.x;
+      if (sslice) {
+        r0 -= sslice[off0 + xi];
+        acc += (double)r0 * (double)r0;
+      }
+      dslice[off0 + xi] = r0;
+    }
+    if (ok1) {
+      R r1 = z.y;
+      if (sslice) {
+        r1 -= sslice[off1 + xi];
+        acc += (double)r1 * (double)r1;
+      }
+      dslice[off1 + xi] = r1;
+    }
+  }
+};
+
+// Deterministic block sum of acc (warp shuffle tree, then warp 0 over the
+// warps) written by thread 0 to *dst. Every thread of the block calls it.
+__device__ __forceinline__ void block_sum_to(double acc, double* dst) {
+  __shared__ double wsum[kThreads / 32];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double w = threadIdx.x < kThreads / 32 ? wsum[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+    if (threadIdx.x == 0) *dst = w;
+  }
+}
+
+// Row pair (A, B) of half spectra at kx from the transform Z of the packed
+// pair a + i b: A = (Z + conj Zm) / 2, B = (Z - conj Zm) / (2i), Zm = Z[P - kx].
+template <typename R>
+__device__ __forceinline__ void untangle(cx<R> Z, cx<R> Zm, cx<R>* A, cx<R>* B) {
+  *A = mk<R>((R)0.5 * (Z.x + Zm.x), (R)0.5 * (Z.y - Zm.y));
+  *B = mk<R>((R)0.5 * (Z.y + Zm.y), (R)-0.5 * (Z.x - Zm.x));
+}
+
+// Inverse of untangle, written into a packed vector: Z[kx] = A + i B and
+// Z[P - kx] = conj(A) + i conj(B) (A, B the half spectra of two real rows).
+template <typename R, int P>
+__device__ __forceinline__ void pack_pair(cx<R>* b, int kx, cx<R> A, cx<R> B) {
+  b[pidx(kx)] = mk<R>(A.x - B.y, A.y + B.x);
+  if (kx > 0 && kx < P / 2) b[pidx(P - kx)] = mk<R>(A.x + B.y, B.x - A.y);
+}
+
 // Stage i, row pass: rows y0 = 2 pair, y0 + 1 of slice s packed as a + i b,
 // zero-padded from nx_in to P, transformed; half spectra written to
 // T[s][kx][y] for kx in [0, P/2]. With sampling on, the slice is the
@@ -227,38 +356,9 @@ __global__ void __launch_bounds__(kThreads) k_row_r2c(const R* __restrict__ in, 
   const int v = threadIdx.x / SH::TPV, tid = threadIdx.x % SH::TPV;
   const int64_t s = blockIdx.y;
   const int pair0 = blockIdx.x * SH::VPB;
-  const int y0 = 2 * (pair0 + v);
-  const R* base = in + s * in_stride;
-  const R* row0;
-  const R* row1;
-  bool ok0, ok1;
-  if (!SAMP) {
-    ok0 = y0 < ny_in;
-    ok1 = y0 + 1 < ny_in;
-    row0 = base + (int64_t)y0 * nx_in;
-    row1 = row0 + nx_in;
-  } else {
-    const int j0 = y0 < ny_in ? scan_index(y0, sm.oy, sm.sy, sm.my) : -1;
-    const int j1 = y0 + 1 < ny_in ? scan_index(y0 + 1, sm.oy, sm.sy, sm.my) : -1;
-    ok0 = j0 >= 0;
-    ok1 = j1 >= 0;
-    row0 = base + (int64_t)(ok0 ? j0 : 0) * sm.mx;
-    row1 = base + (int64_t)(ok1 ? j1 : 0) * sm.mx;
-  }
+  RowPairLoad<R, SAMP> ld(in + s * in_stride, 2 * (pair0 + v), nx_in, ny_in, sm);
   pdl_wait();
   __syncthreads();  // twiddles staged
-  auto ld = [&](int x) -> cx<R> {
-    R a = 0, b = 0;
-    if (x < nx_in) {
-      int xi = x;
-      if (SAMP) xi = scan_index(x, sm.ox, sm.sx, sm.mx);
-      if (xi >= 0) {
-        if (ok0) a = row0[xi];
-        if (ok1) b = row1[xi];
-      }
-    }
-    return mk<R>(a, b);
-  };
   NoStore<R> st;
   run_passes<R, P, 0, false, true, false>(bufs + v * SH::VSTR, tw, tid, ld, st);
   cx<R>* dst = T + s * tslice;
@@ -267,11 +367,9 @@ __global__ void __launch_bounds__(kThreads) k_row_r2c(const R* __restrict__ in, 
     const int vv = i % SH::VPB, kx = i / SH::VPB;
     const int yy = 2 * (pair0 + vv);
     if (yy >= ny_in) continue;
-    const cx<R> Z = bufs[vv * SH::VSTR + pidx(kx)];
-    const cx<R> Zm = bufs[vv * SH::VSTR + pidx((P - kx) & (P - 1))];
-    // A = (Z + conj Zm) / 2 (row yy), B = (Z - conj Zm) / (2i) (row yy + 1)
-    const cx<R> A = mk<R>((R)0.5 * (Z.x + Zm.x), (R)0.5 * (Z.y - Zm.y));
-    const cx<R> B = mk<R>((R)0.5 * (Z.y + Zm.y), (R)-0.5 * (Z.x - Zm.x));
+    cx<R> A, B;
+    untangle(bufs[vv * SH::VSTR + pidx(kx)], bufs[vv * SH::VSTR + pidx((P - kx) & (P - 1))], &A,
+             &B);
     cx<R>* o = dst + (int64_t)kx * tstride + yy;
     o[0] = A;
     o[1] = B;  // tstride is even, so yy + 1 < tstride
@@ -382,70 +480,15 @@ __global__ void __launch_bounds__(kThreads) k_row_c2r(const cx<R>* __restrict__ 
         A.y = 0;
         B.y = 0;
       }
-      cx<R>* b = bufs + vv * SH::VSTR;
-      b[pidx(kx)] = mk<R>(A.x - B.y, A.y + B.x);
-      if (kx > 0 && kx < P / 2) b[pidx(P - kx)] = mk<R>(A.x + B.y, B.x - A.y);
+      pack_pair<R, P>(bufs + vv * SH::VSTR, kx, A, B);
     }
   }
   __syncthreads();
-  const int y0 = 2 * (pair0 + v);
-  // destination rows (compact scan rows with sampling on)
-  bool ok0, ok1;
-  int64_t off0, off1;
-  if (!SAMP) {
-    ok0 = y0 < ny_out;
-    ok1 = y0 + 1 < ny_out;
-    off0 = (int64_t)y0 * nx_out;
-    off1 = off0 + nx_out;
-  } else {
-    const int j0 = y0 < ny_out ? scan_index(y0, sm.oy, sm.sy, sm.my) : -1;
-    const int j1 = y0 + 1 < ny_out ? scan_index(y0 + 1, sm.oy, sm.sy, sm.my) : -1;
-    ok0 = j0 >= 0;
-    ok1 = j1 >= 0;
-    off0 = (int64_t)(ok0 ? j0 : 0) * sm.mx;
-    off1 = (int64_t)(ok1 ? j1 : 0) * sm.mx;
-  }
-  R* dslice = out + s * out_stride;
-  const R* sslice = sub ? sub + s * out_stride : nullptr;
-  double acc = 0.0;
-  auto st = [&](int x, cx<R> z) {
-    if (x >= nx_out) return;
-    int xi = x;
-    if (SAMP) {
-      xi = scan_index(x, sm.ox, sm.sx, sm.mx);
-      if (xi < 0) return;
-    }
-    if (ok0) {
-      R r0 = z.x;
-      if (sslice) {
-        r0 -= sslice[off0 + xi];
-        acc += (double)r0 * (double)r0;
-      }
-      dslice[off0 + xi] = r0;
-    }
-    if (ok1) {
-      R r1 = z.y;
-      if (sslice) {
-        r1 -= sslice[off1 + xi];
-        acc += (double)r1 * (double)r1;
-      }
-      dslice[off1 + xi] = r1;
-    }
-  };
+  RowPairStore<R, SAMP> st(out + s * out_stride, sub ? sub + s * out_stride : nullptr,
+                           2 * (pair0 + v), nx_out, ny_out, sm);
   SmemLoad<R> ld;
   run_passes<R, P, 0, true, false, true>(bufs + v * SH::VSTR, tw, tid, ld, st);
-  if (partials) {
-    // deterministic block sum: warp shuffle tree, then warp 0 over the warps
-    __shared__ double wsum[kThreads / 32];
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = acc;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-      double w = threadIdx.x < kThreads / 32 ? wsum[threadIdx.x] : 0.0;
-      for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
-      if (threadIdx.x == 0) partials[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = w;
-    }
-  }
+  if (partials) block_sum_to(st.acc, partials + (int64_t)blockIdx.y * gridDim.x + blockIdx.x);
 }
 
 template <typename R, int P>
@@ -550,14 +593,14 @@ cudaError_t image_t(const Plan& p, const cx<R>* in, int64_t in_stride, R* out, i
   const cx<R>* twx = static_cast<const cx<R>*>(p.twx);
   const cx<R>* twy = static_cast<const cx<R>*>(p.twy);
   cudaError_t e;
+  int nblocks = 0;
+  const bool grouped = groups > 0 && group_sums != nullptr;
+  double* partials = (sumsq || grouped) ? p.red : nullptr;
   auto col = [&]() -> cudaError_t {
     PAT_P_SWITCH(L.py, (col_inv<R, P_>(in, in_stride, L.px / 2 + 1, S, T, L.tstride, L.tslice, L.ny,
                                         twy, st)))
   };
   if ((e = col()) != cudaSuccess) return e;
-  int nblocks = 0;
-  const bool grouped = groups > 0 && group_sums != nullptr;
-  double* partials = (sumsq || grouped) ? p.red : nullptr;
   auto row = [&]() -> cudaError_t {
     PAT_P_SWITCH(L.px, (row_c2r<R, P_>(T, L.tstride, L.tslice, L.nx, L.ny, out, out_stride, S, sub,
                                         partials, twx, st, &nblocks, sm)))

@@ -9,10 +9,12 @@ from tests.helpers import cuda, host
 
 pytestmark = pytest.mark.gpu
 
-# (nx, ny, px, py): every supported transform length, odd/ragged sizes, non-square
+# (nx, ny, px, py): every supported transform length, odd/ragged sizes (odd
+# row counts, a single row), non-square.
 GRIDS = [(5, 7, 16, 16), (16, 16, 32, 32), (32, 32, 64, 64), (64, 50, 128, 128),
          (128, 128, 256, 256), (100, 60, 256, 128), (256, 256, 512, 512), (17, 3, 1024, 16),
-         (512, 400, 1024, 1024)]
+         (512, 400, 1024, 1024), (29, 31, 64, 64), (45, 13, 128, 128), (101, 77, 256, 256),
+         (3, 1, 256, 256), (200, 133, 512, 512)]
 
 
 def _plan(nx, ny, px, py, nslices, fp64=False):
