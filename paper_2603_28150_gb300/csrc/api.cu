@@ -82,7 +82,7 @@ void free_plan(pat_plan* pp) {
   void* bufs[] = {p.table, p.twx,    p.twy,     p.X,         p.Y,      p.T,       p.vol_a,
                   p.vol_b, p.vol_c,  p.dat_a,   p.dat_b,     p.red,    p.betas,   p.iter_dev,
                   p.r2_dev, x.io_obj[0], x.io_obj[1], x.io_dat, x.res, x.scal,
-                  p.tc_fwd, p.tc_adj, p.tc_err, p.fold_members, p.fold_rep,
+                  p.tc_fwd, p.tc_adj, p.tc_err, p.fold_members, p.fold_rep, p.fold_slot,
                   x.slots.t, x.slots.beta, x.slots.invL, x.slots.lamL, x.slots.r2, x.slots.k};
   for (void* b : bufs) cudaFree(b);
   if (x.cap) cudaStreamDestroy(x.cap);
@@ -117,12 +117,21 @@ int c2r_partials_bound(const Layout& L) {
   return (int)(smax * ((L.ny + 1) / 2 + 1));
 }
 
+// Complex elements per row of the X / Y spectra buffers: the bins (Kpad), or
+// the representative slots 4 * Upad of a folded single-precision plan's
+// batched tensor-core path, whichever is longer.
+int64_t spectrum_row_cap(const Layout& L) {
+  if (L.fp64 || L.px != L.py) return L.Kpad;
+  const int64_t h = L.px / 2, U = (h + 1) * (h + 2) / 2;
+  return std::max<int64_t>(L.Kpad, 4 * ((U + 31) / 32 * 32));
+}
+
 // Device bytes of a plan's workspace, including the host-staging buffers
 // allocated on the first call with host pointers.
 int64_t workspace_bytes(const Layout& L) {
   const size_t cs = 2 * L.rsize;
   const int64_t smax = (int64_t)L.max_batch * std::max(L.nz, L.nt);
-  const int64_t xy = smax * L.Kpad * (int64_t)cs;
+  const int64_t xy = smax * spectrum_row_cap(L) * (int64_t)cs;
   const int64_t tb = smax * L.tslice * (int64_t)cs;
   const int64_t vol = (int64_t)L.max_batch * L.nz * L.ny * L.nx * (int64_t)L.rsize;
   const int64_t dat = (int64_t)L.max_batch * L.nt * L.ny * L.nx * (int64_t)L.rsize;
@@ -137,7 +146,7 @@ int alloc_workspace(pat_plan* pp) {
   const Layout& L = p.L;
   const size_t cs = 2 * L.rsize;
   const int64_t smax = (int64_t)L.max_batch * std::max(L.nz, L.nt);
-  const size_t xy = (size_t)smax * L.Kpad * cs;
+  const size_t xy = (size_t)smax * spectrum_row_cap(L) * cs;
   const size_t tb = (size_t)smax * L.tslice * cs;
   const size_t vol = (size_t)L.max_batch * L.nz * L.ny * L.nx * L.rsize;
   const size_t dat = (size_t)L.max_batch * L.nt * L.ny * L.nx * L.rsize;
@@ -239,21 +248,29 @@ cudaError_t forward_dev(const Plan& p, const void* rho, void* d, int batch, cuda
                         const void* sub, double* sumsq, int groups, double* group_sums) {
   const Layout& L = p.L;
   const int64_t plane = (int64_t)L.ny * L.nx, scan = (int64_t)L.my * L.mx;
-  cudaError_t e = launch_spectrum(p, rho, plane, L.nx, L.ny, p.X, L.Kpad, batch * L.nz, s);
+  const bool sl = tc_slots(p, batch);
+  const int64_t row = sl ? slot_row(L) : L.Kpad;
+  const int* slot = sl ? p.fold_slot : nullptr;
+  cudaError_t e = launch_spectrum(p, rho, plane, L.nx, L.ny, p.X, row, batch * L.nz, s,
+                                  no_sampling(), slot);
   if (e != cudaSuccess) return e;
   if ((e = launch_contract_fwd(p, p.X, p.Y, batch, s)) != cudaSuccess) return e;
-  return launch_image(p, p.Y, L.Kpad, d, scan, batch * L.nt, sub, sumsq, s, groups, group_sums,
-                      sampling_of(L));
+  return launch_image(p, p.Y, row, d, scan, batch * L.nt, sub, sumsq, s, groups, group_sums,
+                      sampling_of(L), slot);
 }
 
 cudaError_t adjoint_dev(const Plan& p, const void* d, void* rho, int batch, cudaStream_t s) {
   const Layout& L = p.L;
   const int64_t plane = (int64_t)L.ny * L.nx, scan = (int64_t)L.my * L.mx;
-  cudaError_t e = launch_spectrum(p, d, scan, L.nx, L.ny, p.Y, L.Kpad, batch * L.nt, s,
-                                  sampling_of(L));
+  const bool sl = tc_slots(p, batch);
+  const int64_t row = sl ? slot_row(L) : L.Kpad;
+  const int* slot = sl ? p.fold_slot : nullptr;
+  cudaError_t e = launch_spectrum(p, d, scan, L.nx, L.ny, p.Y, row, batch * L.nt, s,
+                                  sampling_of(L), slot);
   if (e != cudaSuccess) return e;
   if ((e = launch_contract_adj(p, p.Y, p.X, batch, s)) != cudaSuccess) return e;
-  return launch_image(p, p.X, L.Kpad, rho, plane, batch * L.nz, nullptr, nullptr, s);
+  return launch_image(p, p.X, row, rho, plane, batch * L.nz, nullptr, nullptr, s, 0, nullptr,
+                      no_sampling(), slot);
 }
 
 cudaError_t instantiate_counted(cudaGraph_t graph, cudaGraphExec_t* exec, int* kernels) {
@@ -761,10 +778,22 @@ int pat_stage_contract(pat_plan* plan, const void* in, void* out, int batch, int
   if (batch == 0) return PAT_OK;
   if (!in || !out) return fail(PAT_ERR_ARG, "in or out is NULL");
   cudaStream_t s = (cudaStream_t)stream;
+  const Plan& p = plan->p;
+  const int64_t rin = (int64_t)batch * (adjoint ? p.L.nt : p.L.nz);
+  const int64_t rout = (int64_t)batch * (adjoint ? p.L.nz : p.L.nt);
+  if (tc_slots(p, batch)) {  // the tensor path's slot layout, converted in and out
+    PAT_CUDA(launch_to_slots(p, in, p.X, rin, s));
+    if (adjoint)
+      PAT_CUDA(launch_contract_adj(p, p.X, p.Y, batch, s));
+    else
+      PAT_CUDA(launch_contract_fwd(p, p.X, p.Y, batch, s));
+    PAT_CUDA(launch_from_slots(p, p.Y, out, rout, s));
+    return PAT_OK;
+  }
   if (adjoint)
-    PAT_CUDA(launch_contract_adj(plan->p, in, out, batch, s));
+    PAT_CUDA(launch_contract_adj(p, in, out, batch, s));
   else
-    PAT_CUDA(launch_contract_fwd(plan->p, in, out, batch, s));
+    PAT_CUDA(launch_contract_fwd(p, in, out, batch, s));
   return PAT_OK;
   PAT_GUARD_END
 }

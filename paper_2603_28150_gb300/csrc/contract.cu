@@ -13,6 +13,8 @@
 //     in registers while walking t; D comes through the read-only cache.
 // Real tables (even kernels) store one float per (k, t, z): the real and
 // imaginary parts of X are contracted by the same real coefficient.
+#include <algorithm>
+
 #include "pat_internal.h"
 
 namespace pat {
@@ -426,6 +428,43 @@ cudaError_t adj_vb(const Plan& p, const void* D, void* Z, int batch, cudaStream_
 }
 
 }  // namespace
+
+__global__ void k_to_slots(const float2* __restrict__ in, float2* __restrict__ out,
+                           const int* __restrict__ slot, int64_t K, int64_t Kpad, int64_t srow,
+                           int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i / K, k = i % K;
+    out[r * srow + __ldg(slot + k)] = in[r * Kpad + k];
+  }
+}
+
+__global__ void k_from_slots(const float2* __restrict__ in, float2* __restrict__ out,
+                             const int* __restrict__ slot, int64_t K, int64_t Kpad, int64_t srow,
+                             int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i / K, k = i % K;
+    out[r * Kpad + k] = in[r * srow + __ldg(slot + k)];
+  }
+}
+
+cudaError_t launch_to_slots(const Plan& p, const void* in, void* out, int64_t S, cudaStream_t s) {
+  const int64_t n = S * p.L.K;
+  const int g = (int)std::min<int64_t>((n + 255) / 256, 152 * 32);
+  k_to_slots<<<g, 256, 0, s>>>(static_cast<const float2*>(in), static_cast<float2*>(out),
+                               p.fold_slot, p.L.K, p.L.Kpad, slot_row(p.L), n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_from_slots(const Plan& p, const void* in, void* out, int64_t S,
+                              cudaStream_t s) {
+  const int64_t n = S * p.L.K;
+  const int g = (int)std::min<int64_t>((n + 255) / 256, 152 * 32);
+  k_from_slots<<<g, 256, 0, s>>>(static_cast<const float2*>(in), static_cast<float2*>(out),
+                                 p.fold_slot, p.L.K, p.L.Kpad, slot_row(p.L), n);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_contract_fwd(const Plan& p, const void* X, void* Y, int batch, cudaStream_t s) {
   if (p.tc_fwd && p.tc_min_batch > 0 && batch >= p.tc_min_batch)

@@ -377,13 +377,15 @@ __global__ void __launch_bounds__(kThreads) k_row_r2c(const R* __restrict__ in, 
 }
 
 // Stage i, column pass: T[s][kx][0..n_in) zero-padded to P, FFT over y,
-// written to out[s][kx][0..P) (slice stride out_stride).
+// written to out[s][kx][0..P) (slice stride out_stride), or with `slot` to
+// out[s][slot[kx * P + ky]] (the representative-slot layout).
 template <typename R, int P>
 __global__ void __launch_bounds__(kThreads) k_col_fwd(const cx<R>* __restrict__ T, int tstride,
                                                       int64_t tslice, int n_in, int ncols,
                                                       int64_t nvec, cx<R>* __restrict__ out,
                                                       int64_t out_stride,
-                                                      const cx<R>* __restrict__ tw_g) {
+                                                      const cx<R>* __restrict__ tw_g,
+                                                      const int* __restrict__ slot) {
   using SH = Shape<P>;
   cx<R>* tw;
   cx<R>* bufs = setup_smem<R, P>(tw_g, &tw);
@@ -392,24 +394,26 @@ __global__ void __launch_bounds__(kThreads) k_col_fwd(const cx<R>* __restrict__ 
   const bool ok = g < nvec;
   const int64_t s = ok ? g / ncols : 0, kx = ok ? g % ncols : 0;
   const cx<R>* src = T + s * tslice + kx * tstride;
-  cx<R>* dst = out + s * out_stride + kx * P;
+  cx<R>* dst = out + s * out_stride;
+  const int* sl = slot ? slot + kx * P : nullptr;
   pdl_wait();
   __syncthreads();
   auto ld = [&](int y) -> cx<R> { return (ok && y < n_in) ? src[y] : mk<R>(0, 0); };
   auto st = [&](int y, cx<R> val) {
-    if (ok) dst[y] = val;
+    if (ok) dst[sl ? __ldg(sl + y) : kx * P + y] = val;
   };
   run_passes<R, P, 0, false, true, true>(bufs + v * SH::VSTR, tw, tid, ld, st);
 }
 
-// Stage iii, column pass: in[s][kx][0..P) inverse FFT over ky, rows
-// [0, n_out) kept (crop) into T[s][kx][y].
+// Stage iii, column pass: in[s][kx][0..P) (or with `slot`, in[s][slot[kx * P +
+// ky]]) inverse FFT over ky, rows [0, n_out) kept (crop) into T[s][kx][y].
 template <typename R, int P>
 __global__ void __launch_bounds__(kThreads) k_col_inv(const cx<R>* __restrict__ in,
                                                       int64_t in_stride, int ncols, int64_t nvec,
                                                       cx<R>* __restrict__ T, int tstride,
                                                       int64_t tslice, int n_out,
-                                                      const cx<R>* __restrict__ tw_g) {
+                                                      const cx<R>* __restrict__ tw_g,
+                                                      const int* __restrict__ slot) {
   using SH = Shape<P>;
   cx<R>* tw;
   cx<R>* bufs = setup_smem<R, P>(tw_g, &tw);
@@ -417,11 +421,14 @@ __global__ void __launch_bounds__(kThreads) k_col_inv(const cx<R>* __restrict__ 
   const int64_t g = (int64_t)blockIdx.x * SH::VPB + v;
   const bool ok = g < nvec;
   const int64_t s = ok ? g / ncols : 0, kx = ok ? g % ncols : 0;
-  const cx<R>* src = in + s * in_stride + kx * P;
+  const cx<R>* src = in + s * in_stride;
+  const int* sl = slot ? slot + kx * P : nullptr;
   cx<R>* dst = T + s * tslice + kx * tstride;
   pdl_wait();
   __syncthreads();
-  auto ld = [&](int y) -> cx<R> { return ok ? src[y] : mk<R>(0, 0); };
+  auto ld = [&](int y) -> cx<R> {
+    return ok ? src[sl ? __ldg(sl + y) : kx * P + y] : mk<R>(0, 0);
+  };
   auto st = [&](int y, cx<R> val) {
     if (ok && y < n_out) dst[y] = val;
   };
@@ -513,26 +520,27 @@ cudaError_t row_r2c(const R* in, int64_t in_stride, int nx_in, int ny_in, cx<R>*
 
 template <typename R, int P>
 cudaError_t col_fwd(const cx<R>* T, int tstride, int64_t tslice, int n_in, int ncols, int S,
-                    cx<R>* out, int64_t out_stride, const cx<R>* tw, cudaStream_t st) {
+                    cx<R>* out, int64_t out_stride, const cx<R>* tw, cudaStream_t st,
+                    const int* slot) {
   using SH = Shape<P>;
   cudaError_t e = set_smem_attr<R, P>((const void*)k_col_fwd<R, P>);
   if (e != cudaSuccess) return e;
   const int64_t nvec = (int64_t)S * ncols;
   const int64_t blocks = (nvec + SH::VPB - 1) / SH::VPB;
   return launch_pdl(k_col_fwd<R, P>, dim3((unsigned)blocks), dim3(kThreads), smem_bytes<R, P>(), st,
-                    T, tstride, tslice, n_in, ncols, nvec, out, out_stride, tw);
+                    T, tstride, tslice, n_in, ncols, nvec, out, out_stride, tw, slot);
 }
 
 template <typename R, int P>
 cudaError_t col_inv(const cx<R>* in, int64_t in_stride, int ncols, int S, cx<R>* T, int tstride,
-                    int64_t tslice, int n_out, const cx<R>* tw, cudaStream_t st) {
+                    int64_t tslice, int n_out, const cx<R>* tw, cudaStream_t st, const int* slot) {
   using SH = Shape<P>;
   cudaError_t e = set_smem_attr<R, P>((const void*)k_col_inv<R, P>);
   if (e != cudaSuccess) return e;
   const int64_t nvec = (int64_t)S * ncols;
   const int64_t blocks = (nvec + SH::VPB - 1) / SH::VPB;
   return launch_pdl(k_col_inv<R, P>, dim3((unsigned)blocks), dim3(kThreads), smem_bytes<R, P>(), st,
-                    in, in_stride, ncols, nvec, T, tstride, tslice, n_out, tw);
+                    in, in_stride, ncols, nvec, T, tstride, tslice, n_out, tw, slot);
 }
 
 template <typename R, int P>
@@ -564,7 +572,8 @@ cudaError_t row_c2r(const cx<R>* T, int tstride, int64_t tslice, int nx_out, int
 
 template <typename R>
 cudaError_t spectrum_t(const Plan& p, const R* in, int64_t in_stride, int nx_in, int ny_in,
-                       cx<R>* out, int64_t out_stride, int S, cudaStream_t st, Samp sm) {
+                       cx<R>* out, int64_t out_stride, int S, cudaStream_t st, Samp sm,
+                       const int* slot) {
   const Layout& L = p.L;
   const int tstride = ny_in + (ny_in & 1);
   const int64_t tslice = (int64_t)(L.px / 2 + 1) * tstride;
@@ -579,7 +588,7 @@ cudaError_t spectrum_t(const Plan& p, const R* in, int64_t in_stride, int nx_in,
   if ((e = row()) != cudaSuccess) return e;
   auto col = [&]() -> cudaError_t {
     PAT_P_SWITCH(L.py, (col_fwd<R, P_>(T, tstride, tslice, ny_in, L.px / 2 + 1, S, out, out_stride,
-                                        twy, st)))
+                                        twy, st, slot)))
   };
   return col();
 }
@@ -587,7 +596,7 @@ cudaError_t spectrum_t(const Plan& p, const R* in, int64_t in_stride, int nx_in,
 template <typename R>
 cudaError_t image_t(const Plan& p, const cx<R>* in, int64_t in_stride, R* out, int64_t out_stride,
                     int S, const R* sub, double* sumsq, cudaStream_t st, int groups,
-                    double* group_sums, Samp sm) {
+                    double* group_sums, Samp sm, const int* slot) {
   const Layout& L = p.L;
   cx<R>* T = static_cast<cx<R>*>(p.T);
   const cx<R>* twx = static_cast<const cx<R>*>(p.twx);
@@ -598,7 +607,7 @@ cudaError_t image_t(const Plan& p, const cx<R>* in, int64_t in_stride, R* out, i
   double* partials = (sumsq || grouped) ? p.red : nullptr;
   auto col = [&]() -> cudaError_t {
     PAT_P_SWITCH(L.py, (col_inv<R, P_>(in, in_stride, L.px / 2 + 1, S, T, L.tstride, L.tslice, L.ny,
-                                        twy, st)))
+                                        twy, st, slot)))
   };
   if ((e = col()) != cudaSuccess) return e;
   auto row = [&]() -> cudaError_t {
@@ -616,26 +625,29 @@ cudaError_t image_t(const Plan& p, const cx<R>* in, int64_t in_stride, R* out, i
 }  // namespace
 
 cudaError_t launch_spectrum(const Plan& p, const void* in, int64_t in_stride, int nx_in, int ny_in,
-                            void* out, int64_t out_stride, int S, cudaStream_t s, Samp sm) {
+                            void* out, int64_t out_stride, int S, cudaStream_t s, Samp sm,
+                            const int* slot) {
   if (S <= 0) return cudaSuccess;
   if (p.L.fp64)
     return spectrum_t<double>(p, static_cast<const double*>(in), in_stride, nx_in, ny_in,
-                              static_cast<cx<double>*>(out), out_stride, S, s, sm);
+                              static_cast<cx<double>*>(out), out_stride, S, s, sm, slot);
   return spectrum_t<float>(p, static_cast<const float*>(in), in_stride, nx_in, ny_in,
-                           static_cast<cx<float>*>(out), out_stride, S, s, sm);
+                           static_cast<cx<float>*>(out), out_stride, S, s, sm, slot);
 }
 
 cudaError_t launch_image(const Plan& p, const void* in, int64_t in_stride, void* out,
                          int64_t out_stride, int S, const void* sub, double* sumsq,
-                         cudaStream_t s, int groups, double* group_sums, Samp sm) {
+                         cudaStream_t s, int groups, double* group_sums, Samp sm,
+                         const int* slot) {
   if (S <= 0) return cudaSuccess;
   if (p.L.fp64)
     return image_t<double>(p, static_cast<const cx<double>*>(in), in_stride,
                            static_cast<double*>(out), out_stride, S,
-                           static_cast<const double*>(sub), sumsq, s, groups, group_sums, sm);
+                           static_cast<const double*>(sub), sumsq, s, groups, group_sums, sm,
+                           slot);
   return image_t<float>(p, static_cast<const cx<float>*>(in), in_stride, static_cast<float*>(out),
                         out_stride, S, static_cast<const float*>(sub), sumsq, s, groups,
-                        group_sums, sm);
+                        group_sums, sm, slot);
 }
 
 }  // namespace pat

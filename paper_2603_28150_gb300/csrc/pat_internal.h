@@ -166,6 +166,10 @@ struct Plan {
   // the representative of each bin
   int* fold_members = nullptr;  // [Upad][4]
   int* fold_rep = nullptr;      // [K]
+  // Slot layout of the spectra on the batched tensor-core path: row [Upad][4]
+  // complex, bin k at fold_slot[k] = 4 u + i (the i-th member of its
+  // representative u), so a representative's bins share one 32-byte sector.
+  int* fold_slot = nullptr;     // [K]
   double fold_deviation = 0;    // max |Hh(bin) - Hh(representative)| seen (stored scale)
   // split-BF16 tensor-core tables (tc_contract.cu)
   void* tc_fwd = nullptr;
@@ -248,19 +252,30 @@ int cuda_fail(cudaError_t e, const char* what);
 // with slice stride out_stride complex elements.
 cudaError_t launch_spectrum(const Plan& p, const void* in, int64_t in_stride, int nx_in, int ny_in,
                             void* out, int64_t out_stride, int S, cudaStream_t s,
-                            Samp samp = no_sampling());
+                            Samp samp = no_sampling(), const int* slot = nullptr);
 // Stage iii: spectra [S][px/2+1][py] -> real [S][ny][nx] (crop), optionally
 // out = image - sub (sub has out's layout) with sum of squares added to
 // *sumsq (FP64, via the plan's reduction scratch when sumsq != nullptr).
 cudaError_t launch_image(const Plan& p, const void* in, int64_t in_stride, void* out,
                          int64_t out_stride, int S, const void* sub, double* sumsq,
                          cudaStream_t s, int groups = 0, double* group_sums = nullptr,
-                         Samp samp = no_sampling());
+                         Samp samp = no_sampling(), const int* slot = nullptr);
 // Contractions over the resident table (tensor cores when the plan has the
 // split tables and batch >= tc_min_batch).
 cudaError_t launch_contract_fwd(const Plan& p, const void* X, void* Y, int batch, cudaStream_t s);
 cudaError_t launch_contract_adj(const Plan& p, const void* D, void* Z, int batch, cudaStream_t s);
 
+// The batched tensor-core contraction of a folded plan reads and writes
+// spectra in the representative-slot layout (rows of 4 * Upad complex
+// values, bin k at fold_slot[k]); every other path uses rows of Kpad bins.
+inline bool tc_slots(const Plan& p, int batch) {
+  return p.tc_fwd && p.L.fold && p.tc_min_batch > 0 && batch >= p.tc_min_batch;
+}
+inline int64_t slot_row(const Layout& L) { return 4 * L.Upad; }
+// [S][Kpad] bins -> [S][4 Upad] slots and back (single precision).
+cudaError_t launch_to_slots(const Plan& p, const void* in, void* out, int64_t S, cudaStream_t s);
+cudaError_t launch_from_slots(const Plan& p, const void* in, void* out, int64_t S,
+                              cudaStream_t s);
 // Split-BF16 tensor-core contraction (tc_contract.cu).
 bool tc_supported(const Layout& L);
 size_t tc_table_bytes(const Layout& L);  // one direction

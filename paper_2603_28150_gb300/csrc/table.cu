@@ -233,7 +233,7 @@ std::vector<double> twiddles(int n) {
 int build_fold_maps(Plan& p, std::vector<int>* rep_bins) {
   Layout& L = p.L;
   const int P = L.px, half = P / 2;
-  std::vector<int> members, rep((size_t)L.K, -1);
+  std::vector<int> members, rep((size_t)L.K, -1), slot((size_t)L.K, -1);
   for (int a = 0; a <= half; ++a)
     for (int b = a; b <= half; ++b) {
       // bins (kx, ky) of the half spectrum with {kx, |ky|} = {a, b}
@@ -248,7 +248,10 @@ int build_fold_maps(Plan& p, std::vector<int>* rep_bins) {
       const int u = (int)(members.size() / 4);
       for (int i = 0; i < 4; ++i) {
         members.push_back(out[i]);
-        if (out[i] >= 0) rep[out[i]] = u;
+        if (out[i] >= 0) {
+          rep[out[i]] = u;
+          slot[out[i]] = 4 * u + i;
+        }
       }
     }
   L.U = (int64_t)members.size() / 4;
@@ -261,6 +264,9 @@ int build_fold_maps(Plan& p, std::vector<int>* rep_bins) {
     rep_bins->resize((size_t)L.U);
     for (int64_t u = 0; u < L.U; ++u) (*rep_bins)[u] = members[4 * u];
   }
+  PAT_CUDA(cudaMalloc(&p.fold_slot, slot.size() * sizeof(int)));
+  PAT_CUDA(cudaMemcpy(p.fold_slot, slot.data(), slot.size() * sizeof(int),
+                      cudaMemcpyHostToDevice));
   PAT_CUDA(cudaMalloc(&p.fold_members, members.size() * sizeof(int)));
   PAT_CUDA(cudaMalloc(&p.fold_rep, rep.size() * sizeof(int)));
   PAT_CUDA(cudaMemcpy(p.fold_members, members.data(), members.size() * sizeof(int),

@@ -21,6 +21,12 @@
 // accumulators with tcgen05.ld and write Y / Z (G consecutive bins per row).
 // Every wait is bounded: on timeout the kernel records an error, drains its
 // own copies, frees tensor memory and returns.
+//
+// D4-folded plans (k_tc_fold) keep one tile set per representative {|kx|,
+// |ky|} (a quarter of the bytes) and put its up to 4 bins side by side in the
+// MMA's N dimension (N = 4 x 32); their spectra use the representative-slot
+// layout (a representative's 4 bins in one 32-byte sector of every row), so
+// the gathers and stores of the batched operands stay whole sectors.
 #include <cuda_bf16.h>
 #include <stdint.h>
 
@@ -357,6 +363,292 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_contract(Params p) {
                  : "memory");
 }
 
+// ---- D4-folded tables: one tile set per representative, N = 4 bins x 32 -----
+// Per representative u the MMA's B operand holds its (up to) 4 member bins:
+// row n = m * 32 + h * 16 + b is the real (h = 0) or imaginary (h = 1) part of
+// volume b at bin members[u][m], so one pass over u's tiles serves all 4 bins
+// (the table is read once per representative instead of once per bin).
+// Warp roles (192 threads): warp 0 streams the table tiles (cp.async.bulk,
+// kFS-slot ring), warp 1 issues the MMAs, warps 2-5 gather and split the B
+// operand into two alternating buffers and drain the accumulators (two
+// alternating TMEM buffers of 256 columns) to Y / Z, so gathering, MMAs and
+// the epilogue of consecutive representatives overlap.
+//   forward: M = 128 time samples of tile mt, K = nz = 128, accumulator units
+//            of two time tiles; one B chunk per representative;
+//   adjoint: M = nz = 128 depths, K = 128-sample chunks kc of nt, one
+//            accumulator per representative; one B chunk per kc.
+constexpr int kFS = 3;                    // table slots
+constexpr int kFThreads = 192;
+constexpr int kFN = 128;                  // MMA N: 4 members x (re, im) x 16 volumes
+constexpr int kFBBytes = kFN * kTile * 2;  // one part (hi or lo) of a B chunk: 32 KB
+
+struct FoldParams {
+  const unsigned char* table;  // split tiles of this direction, per representative
+  const int4* members;         // [U] bins of each representative (-1 = none)
+  const float2* in;            // X [b][nz][srow] (fwd) or D [b][nt][srow] (adj), slot layout
+  float2* out;                 // Y [b][nt][srow] (fwd) or Z [b][nz][srow] (adj), slot layout
+  int64_t U, srow;
+  int batch;
+  int rows_in, rows_out;  // nz, nt (fwd) or nt, nz (adj)
+  int R;                  // tile rows per representative: mtiles (fwd) or kchunks (adj)
+  int* err;
+};
+
+// Bounded wait that also gives up once another role has aborted.
+// (try_wait itself suspends the thread for a bounded time, so the loop polls
+// without sleeping; 2^22 polls bound the wait to a few seconds.)
+__device__ __forceinline__ bool fwait(uint64_t* bar, uint32_t parity, volatile int* abort_s) {
+  for (uint32_t i = 0; i < (1u << 22); ++i) {
+    if (mbar_test(bar, parity)) return true;
+    if (*abort_s) return false;
+  }
+  *abort_s = 1;
+  return false;
+}
+// Warp-uniform form: every lane polls, all lanes get the same answer.
+__device__ __forceinline__ bool fwait_warp(uint64_t* bar, uint32_t parity, volatile int* abort_s) {
+  return __all_sync(0xffffffffu, fwait(bar, parity, abort_s));
+}
+__device__ __forceinline__ int member(int4 v, int m) {
+  return m == 0 ? v.x : (m == 1 ? v.y : (m == 2 ? v.z : v.w));
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+template <bool ADJ>
+__global__ void __launch_bounds__(kFThreads, 1) k_tc_fold(FoldParams p) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  unsigned char* slots = smem;                               // [kFS][32 KB]
+  unsigned char* bbuf = smem + (size_t)kFS * kTileBytes;     // [2][hi 32 KB | lo 32 KB]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(bbuf + 2 * 2 * (size_t)kFBBytes);
+  uint64_t* full = bars;             // [kFS] tile landed
+  uint64_t* empty = bars + kFS;      // [kFS] tile consumed by the MMAs
+  uint64_t* bready = bars + 2 * kFS;  // [2] B chunk written (128 arrivals)
+  uint64_t* bfree = bready + 2;       // [2] B chunk consumed by the MMAs
+  uint64_t* afull = bfree + 2;        // [2] accumulator buffer complete
+  uint64_t* aempty = afull + 2;       // [2] accumulator buffer drained (128 arrivals)
+  uint64_t* drainb = aempty + 2;      // [1] all MMAs done (teardown)
+  uint32_t* tmem_base_s = reinterpret_cast<uint32_t*>(drainb + 1);
+  volatile int* abort_s = reinterpret_cast<volatile int*>(tmem_base_s + 1);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t nmine = blockIdx.x < p.U ? (p.U - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int R = p.R;
+  // forward: accumulator units of two time tiles; adjoint: one per representative
+  const int NA = ADJ ? 1 : (R + 1) / 2;
+  const int NB = ADJ ? R : 1;  // B chunks per representative
+  constexpr int kCols = 512;
+
+  if (tid == 0) {
+    for (int s = 0; s < kFS; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&bready[i], 128);
+      mbar_init(&bfree[i], 1);
+      mbar_init(&afull[i], 1);
+      mbar_init(&aempty[i], 128);
+    }
+    mbar_init(drainb, 1);
+    *abort_s = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_base_s)),
+                 "r"(kCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_base_s;
+  int64_t issued = 0;  // table tiles copied (warp 0)
+
+  if (warp == 0) {
+    // ---- producer: the tiles of this CTA's representatives, in MMA order
+    const int64_t total = nmine * 2 * R;
+    for (int64_t j = 0; j < total && !*abort_s; ++j) {
+      const int s = (int)(j % kFS);
+      if (j >= kFS && !fwait_warp(&empty[s], (uint32_t)(((j / kFS) - 1) & 1), abort_s)) break;
+      if (lane == 0) {
+        const int64_t u = blockIdx.x + (j / (2 * R)) * gridDim.x;
+        const int64_t tile = u * 2 * R + j % (2 * R);
+        mbar_arrive_expect_tx(&full[s], kTileBytes);
+        bulk_g2s(slots + (size_t)s * kTileBytes, p.table + tile * (int64_t)kTileBytes, kTileBytes,
+                 &full[s]);
+      }
+      issued = j + 1;
+      __syncwarp();
+    }
+  } else if (warp == 1) {
+    // ---- MMA issuer (lane 0); tile j of representative i is (r, part) = (j / 2, j % 2)
+    constexpr uint32_t idesc = idesc_bf16(kTile, kFN);
+    int64_t j = 0;
+    for (int64_t i = 0; i < nmine && !*abort_s; ++i) {
+      bool ok = true;
+      for (int r = 0; r < R && ok; ++r) {
+        const int64_t c = ADJ ? i * NB + r : i;  // B chunk
+        if (ADJ || r == 0) ok = fwait_warp(&bready[c & 1], (uint32_t)((c >> 1) & 1), abort_s);
+        const int64_t q = ADJ ? i : i * NA + r / 2;  // accumulator unit
+        const bool unit_start = ADJ ? r == 0 : (r % 2 == 0);
+        if (ok && unit_start && q >= 2)
+          ok = fwait_warp(&aempty[q & 1], (uint32_t)(((q >> 1) - 1) & 1), abort_s);
+        if (!ok) break;
+        tc_fence_after();
+        const unsigned char* bh = bbuf + (size_t)(c & 1) * 2 * kFBBytes;
+        const unsigned char* bl = bh + kFBBytes;
+        const uint32_t d = tmem + (uint32_t)((q & 1) * 256 + (ADJ ? 0 : (r % 2) * 128));
+        for (int part = 0; part < 2 && ok; ++part, ++j) {
+          const int s = (int)(j % kFS);
+          ok = fwait_warp(&full[s], (uint32_t)((j / kFS) & 1), abort_s);
+          if (!ok) break;
+          tc_fence_after();
+          if (lane == 0) {
+            const unsigned char* a = slots + (size_t)s * kTileBytes;
+#pragma unroll
+            for (int ks = 0; ks < kTile / 16; ++ks) {
+              const uint32_t off = ks * 2 * kLBO;
+              const uint64_t ad = smem_desc(a + off);
+              // hi tile: hi.hi and hi.lo; lo tile: lo.hi
+              const bool first = part == 0 && ks == 0 && (ADJ ? r == 0 : true);
+              mma_bf16(d, ad, smem_desc(bh + off), idesc, first ? 0u : 1u);
+              if (part == 0) mma_bf16(d, ad, smem_desc(bl + off), idesc, 1u);
+            }
+            mma_commit(&empty[s]);
+          }
+          __syncwarp();
+        }
+        if (!ok) break;
+        const bool unit_end = ADJ ? r == R - 1 : (r % 2 == 1 || r == R - 1);
+        if (lane == 0) {
+          if (ADJ || r == R - 1) mma_commit(&bfree[c & 1]);
+          if (unit_end) mma_commit(&afull[q & 1]);
+        }
+        __syncwarp();
+      }
+    }
+  } else {
+    // ---- gather + split (B operand) and epilogue (accumulators -> Y / Z)
+    const int ct = tid - 64;     // 0..127
+    const int quarter = warp & 3;  // TMEM lanes 32 * quarter ... of this warp
+    // Operands in the slot layout: row (b, r) of X / D holds the 4 members of
+    // representative u at [4u, 4u + 4) of its srow complex values (32 bytes).
+    auto gather = [&](int64_t i, int kc, int64_t c) -> bool {
+      if (c >= 2 && !fwait_warp(&bfree[c & 1], (uint32_t)(((c >> 1) - 1) & 1), abort_s))
+        return false;
+      tc_fence_after();
+      const int64_t u = blockIdx.x + i * gridDim.x;
+      const int4 mem = p.members[u];
+      unsigned char* bh = bbuf + (size_t)(c & 1) * 2 * kFBBytes;
+      // items (b, octet of rows): 16 x 16, two per thread, all loads in flight
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const int it = ct + k * 128;
+        const int b = it & 15, oct = it >> 4;
+        const bool live = b < p.batch;
+        float4 lo4[8], hi4[8];  // members (0, 1) and (2, 3) of 8 rows
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int row = kc * kTile + oct * 8 + q;
+          const float4* src = reinterpret_cast<const float4*>(
+              p.in + ((int64_t)b * p.rows_in + row) * p.srow + 4 * u);
+          lo4[q] = live ? __ldg(src) : make_float4(0.f, 0.f, 0.f, 0.f);
+          hi4[q] = live ? __ldg(src + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          const bool present = member(mem, m) >= 0;
+          float re[8], im[8];
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const float4 w = m < 2 ? lo4[q] : hi4[q];
+            re[q] = present ? ((m & 1) ? w.z : w.x) : 0.f;
+            im[q] = present ? ((m & 1) ? w.w : w.y) : 0.f;
+          }
+          uint4 h, l;
+          split8(re, &h, &l);
+          *reinterpret_cast<uint4*>(bh + core_off(m * 32 + b, oct * 8)) = h;
+          *reinterpret_cast<uint4*>(bh + kFBBytes + core_off(m * 32 + b, oct * 8)) = l;
+          split8(im, &h, &l);
+          *reinterpret_cast<uint4*>(bh + core_off(m * 32 + 16 + b, oct * 8)) = h;
+          *reinterpret_cast<uint4*>(bh + kFBBytes + core_off(m * 32 + 16 + b, oct * 8)) = l;
+        }
+      }
+      fence_proxy_async();
+      mbar_arrive(&bready[c & 1]);
+      return true;
+    };
+    // Accumulator columns m * 32 + b (real) and m * 32 + 16 + b (imaginary) of
+    // row r go to out row (b, r) at [4u, 4u + 4) as two 16-byte stores.
+    auto epilogue = [&](int64_t i, int a, int64_t q) -> bool {
+      if (!fwait_warp(&afull[q & 1], (uint32_t)((q >> 1) & 1), abort_s)) return false;
+      tc_fence_after();
+      const int64_t u = blockIdx.x + i * gridDim.x;
+      const int nmt = ADJ ? 1 : min(2, R - 2 * a);
+      for (int h = 0; h < nmt; ++h) {
+        const int row = (ADJ ? 0 : (2 * a + h) * kTile) + quarter * 32 + lane;
+        float v[4][32];
+        const uint32_t col = (uint32_t)((q & 1) * 256 + h * 128);
+#pragma unroll
+        for (int m = 0; m < 4; ++m)
+          tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + col + (uint32_t)(m * 32), v[m]);
+#pragma unroll
+        for (int bb = 0; bb < kVB; ++bb) {
+          if (bb >= p.batch) break;
+          float4* o =
+              reinterpret_cast<float4*>(p.out + ((int64_t)bb * p.rows_out + row) * p.srow + 4 * u);
+          o[0] = make_float4(v[0][bb], v[0][16 + bb], v[1][bb], v[1][16 + bb]);
+          o[1] = make_float4(v[2][bb], v[2][16 + bb], v[3][bb], v[3][16 + bb]);
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(&aempty[q & 1]);
+      return true;
+    };
+    bool ok = true;
+    if (!ADJ) {
+      if (nmine > 0) ok = gather(0, 0, 0);
+      for (int64_t i = 0; i < nmine && ok; ++i) {
+        if (i + 1 < nmine) ok = gather(i + 1, 0, i + 1);
+        for (int a = 0; a < NA && ok; ++a) ok = epilogue(i, a, i * NA + a);
+      }
+    } else {
+      for (int64_t i = 0; i < nmine && ok; ++i) {
+        for (int kc = 0; kc < NB && ok; ++kc) ok = gather(i, kc, i * NB + kc);
+        if (ok && i >= 1) ok = epilogue(i - 1, 0, i - 1);
+      }
+      if (ok && nmine > 0) ok = epilogue(nmine - 1, 0, nmine - 1);
+    }
+  }
+
+  // ---- teardown (also after a timeout): drain our copies, free tensor memory
+  __syncthreads();
+  if (warp == 0 && lane == 0 && *abort_s) {
+    atomicExch(p.err, 1);
+    // every copy issued lands before the shared memory is released
+    for (int64_t j = issued - kFS < 0 ? 0 : issued - kFS; j < issued; ++j)
+      mbar_wait(&full[j % kFS], (uint32_t)((j / kFS) & 1));
+  }
+  if (warp == 1 && lane == 0 && *abort_s) {
+    mma_commit(drainb);  // arrives once every MMA issued so far has completed
+    mbar_wait(drainb, 0);
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols)
+                 : "memory");
+}
+
+size_t fold_smem() {
+  return (size_t)kFS * kTileBytes + 4 * (size_t)kFBBytes + 8 * (2 * kFS + 9) + 16;
+}
+
 template <int G, int S>
 size_t smem_for(int kchunks) {
   return (size_t)S * kTileBytes + (size_t)G * kchunks * 2 * kBBytes + 8 * (2 * S + 2) + 16;
@@ -402,18 +694,21 @@ bool tc_supported(const Layout& L) {
   return !L.fp64 && L.real && L.nz == tc::kTile && L.nt % tc::kTile == 0 && L.nt <= 4 * tc::kTile;
 }
 
+// Folded plans keep one tile set per representative, the others one per bin.
 size_t tc_table_bytes(const Layout& L) {
-  return (size_t)L.K * (L.nt / tc::kTile) * 2 * tc::kTileBytes;  // one direction
+  const int64_t rows = L.fold ? L.U : L.K;
+  return (size_t)rows * (L.nt / tc::kTile) * 2 * tc::kTileBytes;  // one direction
 }
 
 cudaError_t tc_build_tables(const Plan& p, void* fwd, void* adj, cudaStream_t s) {
   const Layout& L = p.L;
-  int64_t n = L.K * L.nt * L.nz;
+  // folded: tile set u is table row u (the representative's row)
+  const int64_t rows = L.fold ? L.U : L.K;
+  int64_t n = rows * L.nt * L.nz;
   int64_t g = (n + 255) / 256;
   if (g > 152 * 64) g = 152 * 64;
-  tc::k_split_tables<<<(int)g, 256, 0, s>>>(static_cast<const float*>(p.table),
-                                            L.fold ? p.fold_rep : nullptr, L.nz, L.nt, L.nzg,
-                                            L.K, static_cast<unsigned char*>(fwd),
+  tc::k_split_tables<<<(int)g, 256, 0, s>>>(static_cast<const float*>(p.table), nullptr, L.nz,
+                                            L.nt, L.nzg, rows, static_cast<unsigned char*>(fwd),
                                             static_cast<unsigned char*>(adj));
   return cudaGetLastError();
 }
@@ -428,6 +723,32 @@ cudaError_t tc_contract(const Plan& p, const void* tables_fwd, const void* table
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
+  if (L.fold) {
+    const size_t smem = tc::fold_smem();
+    auto fn = adjoint ? tc::k_tc_fold<true> : tc::k_tc_fold<false>;
+    e = cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    if (e != cudaSuccess) return e;
+    const int rows_in = adjoint ? L.nt : L.nz, rows_out = adjoint ? L.nz : L.nt;
+    for (int b0 = 0; b0 < batch; b0 += tc::kVB) {
+      tc::FoldParams q;
+      q.table = static_cast<const unsigned char*>(adjoint ? tables_adj : tables_fwd);
+      q.members = reinterpret_cast<const int4*>(p.fold_members);
+      q.in = static_cast<const float2*>(in) + (int64_t)b0 * rows_in * 4 * L.Upad;
+      q.out = static_cast<float2*>(out) + (int64_t)b0 * rows_out * 4 * L.Upad;
+      q.U = L.U;
+      q.srow = 4 * L.Upad;
+      q.batch = std::min(tc::kVB, batch - b0);
+      q.rows_in = rows_in;
+      q.rows_out = rows_out;
+      q.R = L.nt / tc::kTile;
+      q.err = err;
+      const int grid = (int)std::min<int64_t>(L.U, sms);
+      fn<<<grid, tc::kFThreads, smem, s>>>(q);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }
   for (int b0 = 0; b0 < batch; b0 += tc::kVB) {
     tc::Params q;
     q.K = L.K;

@@ -16,17 +16,21 @@ def _medium(g, med):
     return Medium(med.c, med.dx, med.dy, med.dz, med.dt, oracle.mz_for(g.nz, g.nt, med), 1)
 
 
-@pytest.mark.parametrize("n,nt", [(16, 128), (24, 256), (32, 512)])
+@pytest.mark.parametrize("n,nt,fold", [(16, 128, True), (24, 256, True), (32, 512, True),
+                                        (24, 256, False)])
 @pytest.mark.parametrize("batch", [16, 5, 20])
-def test_tensor_contraction_matches_cuda_core(n, nt, batch):
+def test_tensor_contraction_matches_cuda_core(n, nt, fold, batch):
+    """Folded plans run one tile set per representative (N = 4 bins x 32
+    columns per MMA); unfolded plans one per bin."""
     import torch
     g = oracle.Grid.square(n, 128, nt)
     plan = Plan(g.nx, g.ny, g.nz, g.nt, g.px, g.py, max_batch=batch,
-                medium=_medium(g, MED_50UM), bf16_split=True)
+                medium=_medium(g, MED_50UM), bf16_split=True, fold=fold)
     info = plan.info()
-    assert info["real_table"] == 1 and info["tensor_min_batch"] == 2 and info["folded"] == 1
-    # hi + lo BF16 per (bin, t, z), one copy per direction
-    assert info["tensor_table_bytes"] == 2 * info["bins"] * g.nt * g.nz * 4
+    assert info["real_table"] == 1 and info["tensor_min_batch"] == 2
+    assert info["folded"] == (1 if fold else 0)
+    # hi + lo BF16 per (table row, t, z), one copy per direction
+    assert info["tensor_table_bytes"] == 2 * info["table_rows"] * g.nt * g.nz * 4
     Kp = info["bins_padded"]
     gen = torch.Generator(device="cuda").manual_seed(1)
     X = torch.randn((batch, g.nz, Kp), dtype=torch.complex64, device="cuda", generator=gen)
