@@ -379,7 +379,7 @@ __global__ void __launch_bounds__(kThreads) k_row_r2c(const R* __restrict__ in, 
 // Stage i, column pass: T[s][kx][0..n_in) zero-padded to P, FFT over y,
 // written to out[s][kx][0..P) (slice stride out_stride), or with `slot` to
 // out[s][slot[kx * P + ky]] (the representative-slot layout).
-template <typename R, int P>
+template <typename R, int P, bool SLOT>
 __global__ void __launch_bounds__(kThreads) k_col_fwd(const cx<R>* __restrict__ T, int tstride,
                                                       int64_t tslice, int n_in, int ncols,
                                                       int64_t nvec, cx<R>* __restrict__ out,
@@ -395,19 +395,19 @@ __global__ void __launch_bounds__(kThreads) k_col_fwd(const cx<R>* __restrict__ 
   const int64_t s = ok ? g / ncols : 0, kx = ok ? g % ncols : 0;
   const cx<R>* src = T + s * tslice + kx * tstride;
   cx<R>* dst = out + s * out_stride;
-  const int* sl = slot ? slot + kx * P : nullptr;
+  const int* sl = SLOT ? slot + kx * P : nullptr;
   pdl_wait();
   __syncthreads();
   auto ld = [&](int y) -> cx<R> { return (ok && y < n_in) ? src[y] : mk<R>(0, 0); };
   auto st = [&](int y, cx<R> val) {
-    if (ok) dst[sl ? __ldg(sl + y) : kx * P + y] = val;
+    if (ok) dst[SLOT ? __ldg(sl + y) : kx * P + y] = val;
   };
   run_passes<R, P, 0, false, true, true>(bufs + v * SH::VSTR, tw, tid, ld, st);
 }
 
 // Stage iii, column pass: in[s][kx][0..P) (or with `slot`, in[s][slot[kx * P +
 // ky]]) inverse FFT over ky, rows [0, n_out) kept (crop) into T[s][kx][y].
-template <typename R, int P>
+template <typename R, int P, bool SLOT>
 __global__ void __launch_bounds__(kThreads) k_col_inv(const cx<R>* __restrict__ in,
                                                       int64_t in_stride, int ncols, int64_t nvec,
                                                       cx<R>* __restrict__ T, int tstride,
@@ -422,12 +422,12 @@ __global__ void __launch_bounds__(kThreads) k_col_inv(const cx<R>* __restrict__ 
   const bool ok = g < nvec;
   const int64_t s = ok ? g / ncols : 0, kx = ok ? g % ncols : 0;
   const cx<R>* src = in + s * in_stride;
-  const int* sl = slot ? slot + kx * P : nullptr;
+  const int* sl = SLOT ? slot + kx * P : nullptr;
   cx<R>* dst = T + s * tslice + kx * tstride;
   pdl_wait();
   __syncthreads();
   auto ld = [&](int y) -> cx<R> {
-    return ok ? src[sl ? __ldg(sl + y) : kx * P + y] : mk<R>(0, 0);
+    return ok ? src[SLOT ? __ldg(sl + y) : kx * P + y] : mk<R>(0, 0);
   };
   auto st = [&](int y, cx<R> val) {
     if (ok && y < n_out) dst[y] = val;
@@ -523,11 +523,12 @@ cudaError_t col_fwd(const cx<R>* T, int tstride, int64_t tslice, int n_in, int n
                     cx<R>* out, int64_t out_stride, const cx<R>* tw, cudaStream_t st,
                     const int* slot) {
   using SH = Shape<P>;
-  cudaError_t e = set_smem_attr<R, P>((const void*)k_col_fwd<R, P>);
+  auto fn = slot ? k_col_fwd<R, P, true> : k_col_fwd<R, P, false>;
+  cudaError_t e = set_smem_attr<R, P>((const void*)fn);
   if (e != cudaSuccess) return e;
   const int64_t nvec = (int64_t)S * ncols;
   const int64_t blocks = (nvec + SH::VPB - 1) / SH::VPB;
-  return launch_pdl(k_col_fwd<R, P>, dim3((unsigned)blocks), dim3(kThreads), smem_bytes<R, P>(), st,
+  return launch_pdl(fn, dim3((unsigned)blocks), dim3(kThreads), smem_bytes<R, P>(), st,
                     T, tstride, tslice, n_in, ncols, nvec, out, out_stride, tw, slot);
 }
 
@@ -535,11 +536,12 @@ template <typename R, int P>
 cudaError_t col_inv(const cx<R>* in, int64_t in_stride, int ncols, int S, cx<R>* T, int tstride,
                     int64_t tslice, int n_out, const cx<R>* tw, cudaStream_t st, const int* slot) {
   using SH = Shape<P>;
-  cudaError_t e = set_smem_attr<R, P>((const void*)k_col_inv<R, P>);
+  auto fn = slot ? k_col_inv<R, P, true> : k_col_inv<R, P, false>;
+  cudaError_t e = set_smem_attr<R, P>((const void*)fn);
   if (e != cudaSuccess) return e;
   const int64_t nvec = (int64_t)S * ncols;
   const int64_t blocks = (nvec + SH::VPB - 1) / SH::VPB;
-  return launch_pdl(k_col_inv<R, P>, dim3((unsigned)blocks), dim3(kThreads), smem_bytes<R, P>(), st,
+  return launch_pdl(fn, dim3((unsigned)blocks), dim3(kThreads), smem_bytes<R, P>(), st,
                     in, in_stride, ncols, nvec, T, tstride, tslice, n_out, tw, slot);
 }
 
