@@ -235,7 +235,7 @@ __global__ void __launch_bounds__(kWarps * 32, 2)
     for (int r = 0; r < kRT; ++r)
 #pragma unroll
       for (int m = 0; m < 4; ++m) acc[r][m] = mk<float>(0.f, 0.f);
-#pragma unroll 2
+#pragma unroll 4
     for (int g = 0; g < nzg; ++g) {
       float hv[kRT][4];
 #pragma unroll
@@ -304,11 +304,11 @@ __global__ void __launch_bounds__(kWarps * 32, 2)
     }
     __syncthreads();
     const int tn = min(kTC, nt - t0);
-    // 4 samples per step: their GPW x 4 table loads are issued together
-    for (int tt = 0; tt < tn; tt += 4) {
-      float4 h[4][GPW];
+    // 8 samples per step: their GPW x 8 table loads are issued together
+    for (int tt = 0; tt < tn; tt += 8) {
+      float4 h[8][GPW];
 #pragma unroll
-      for (int r = 0; r < 4; ++r)
+      for (int r = 0; r < 8; ++r)
 #pragma unroll
         for (int j = 0; j < GPW; ++j) {
           const int g = gbase + j * kWarps;
@@ -317,7 +317,7 @@ __global__ void __launch_bounds__(kWarps * 32, 2)
                         : make_float4(0.f, 0.f, 0.f, 0.f);
         }
 #pragma unroll
-      for (int r = 0; r < 4; ++r) {
+      for (int r = 0; r < 8; ++r) {
         cx<float> d[4];
 #pragma unroll
         for (int m = 0; m < 4; ++m) d[m] = ds[(tt + r) & (kTC - 1)][m][lane];
