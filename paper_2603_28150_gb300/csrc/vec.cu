@@ -76,13 +76,35 @@ __global__ void __launch_bounds__(kBlock) k_fista_update(R* __restrict__ y, R* _
   const R invL = (R)scal[0], lamL = (R)scal[1];
   const int k = *iter;
   const R beta = (R)betas[k];
-  for (int64_t i = blockIdx.x * (int64_t)kBlock + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * kBlock) {
-    const R yv = y[i], g = grad[i], xp = xprev[i];
+  auto step = [&](R yv, R g, R xp, R* yo, R* xo) {
     R x = yv - g * invL - lamL;
     x = x > (R)0 ? x : (R)0;
-    y[i] = x + beta * (x - xp);
-    xprev[i] = x;
+    *yo = x + beta * (x - xp);
+    *xo = x;
+  };
+  const int64_t t0 = blockIdx.x * (int64_t)kBlock + threadIdx.x, nth = (int64_t)gridDim.x * kBlock;
+  int64_t head = 0;
+  if constexpr (sizeof(R) == 4) {  // 16-byte accesses (the plan's buffers are 256-byte aligned)
+    head = n & ~(int64_t)3;
+    float4* y4 = reinterpret_cast<float4*>(y);
+    float4* x4 = reinterpret_cast<float4*>(xprev);
+    const float4* g4 = reinterpret_cast<const float4*>(grad);
+    for (int64_t i = t0; i < head / 4; i += nth) {
+      const float4 yv = y4[i], g = __ldg(g4 + i), xp = x4[i];
+      float4 yo, xo;
+      step(yv.x, g.x, xp.x, &yo.x, &xo.x);
+      step(yv.y, g.y, xp.y, &yo.y, &xo.y);
+      step(yv.z, g.z, xp.z, &yo.z, &xo.z);
+      step(yv.w, g.w, xp.w, &yo.w, &xo.w);
+      y4[i] = yo;
+      x4[i] = xo;
+    }
+  }
+  for (int64_t i = head + t0; i < n; i += nth) {
+    R yo, xo;
+    step(y[i], grad[i], xprev[i], &yo, &xo);
+    y[i] = yo;
+    xprev[i] = xo;
   }
   __shared__ bool last;
   __syncthreads();
@@ -142,7 +164,7 @@ cudaError_t launch_fista_update(const Plan& p, void* y, void* xprev, const void*
                                 const double* scal, const double* betas, int* iter,
                                 const double* r2_cur, double* r2_hist, int cap, unsigned* done,
                                 cudaStream_t s) {
-  const int g = grid_for(n, 152 * 16);
+  const int g = grid_for(p.L.fp64 ? n : (n + 3) / 4, 152 * 16);
   if (p.L.fp64)
     return launch_pdl(k_fista_update<double>, dim3(g), dim3(kBlock), 0, s,
                       static_cast<double*>(y), static_cast<double*>(xprev),
