@@ -259,6 +259,25 @@ cudaError_t forward_dev(const Plan& p, const void* rho, void* d, int batch, cuda
                       sampling_of(L), slot);
 }
 
+cudaError_t gradient_dev(const Plan& p, const void* x, const void* y, void* grad, int batch,
+                         cudaStream_t s, double* sumsq, int groups, double* group_sums) {
+  const Layout& L = p.L;
+  const int64_t plane = (int64_t)L.ny * L.nx, scan = (int64_t)L.my * L.mx;
+  const bool sl = tc_slots(p, batch);
+  const int64_t row = sl ? slot_row(L) : L.Kpad;
+  const int* slot = sl ? p.fold_slot : nullptr;
+  cudaError_t e = launch_spectrum(p, x, plane, L.nx, L.ny, p.X, row, batch * L.nz, s,
+                                  no_sampling(), slot);
+  if (e != cudaSuccess) return e;
+  if ((e = launch_contract_fwd(p, p.X, p.Y, batch, s)) != cudaSuccess) return e;
+  if ((e = launch_residual(p, p.Y, row, y, scan, batch * L.nt, sumsq, s, groups, group_sums,
+                           sampling_of(L), slot, p.Y, row)) != cudaSuccess)
+    return e;
+  if ((e = launch_contract_adj(p, p.Y, p.X, batch, s)) != cudaSuccess) return e;
+  return launch_image(p, p.X, row, grad, plane, batch * L.nz, nullptr, nullptr, s, 0, nullptr,
+                      no_sampling(), slot);
+}
+
 cudaError_t adjoint_dev(const Plan& p, const void* d, void* rho, int batch, cudaStream_t s) {
   const Layout& L = p.L;
   const int64_t plane = (int64_t)L.ny * L.nx, scan = (int64_t)L.my * L.mx;
@@ -361,9 +380,8 @@ cudaError_t fista_iter(pat_plan* pp, int batch, cudaStream_t s) {
   Plan& p = pp->p;
   PlanExt& x = pp->x;
   const Layout& L = p.L;
-  cudaError_t e = forward_dev(p, p.vol_a, p.dat_a, batch, s, p.dat_b, x.res + 1);
+  cudaError_t e = gradient_dev(p, p.vol_a, p.dat_b, p.vol_c, batch, s, x.res + 1);
   if (e != cudaSuccess) return e;
-  if ((e = adjoint_dev(p, p.dat_a, p.vol_c, batch, s)) != cudaSuccess) return e;
   return launch_fista_update(p, p.vol_a, p.vol_b, p.vol_c, (int64_t)obj_elems(L, batch), x.scal,
                              p.betas, p.iter_dev, x.res + 1, p.r2_dev, p.r2_cap,
                              reinterpret_cast<unsigned*>(p.iter_dev + 1), s);
@@ -619,8 +637,7 @@ int pat_gradient(pat_plan* plan, const void* xin, const void* y, void* grad, int
   if ((rc = stage_in(ay, px.io_dat, db, s)) != PAT_OK) return rc;
   const bool hout = !is_device_ptr(grad);
   void* dst = hout ? px.io_obj[1] : grad;
-  PAT_CUDA(forward_dev(p, ax.dev, p.dat_a, batch, s, ay.dev, px.res + 1));
-  PAT_CUDA(adjoint_dev(p, p.dat_a, dst, batch, s));
+  PAT_CUDA(gradient_dev(p, ax.dev, ay.dev, dst, batch, s, px.res + 1));
   if (hout) PAT_CUDA(cudaMemcpyAsync(grad, dst, ob, cudaMemcpyDeviceToHost, s));
   if (resid2) PAT_CUDA(cudaMemcpyAsync(resid2, px.res + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
   if (hout || resid2 || ax.host || ay.host) PAT_CUDA(cudaStreamSynchronize(s));

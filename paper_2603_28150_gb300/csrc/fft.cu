@@ -435,30 +435,14 @@ __global__ void __launch_bounds__(kThreads) k_col_inv(const cx<R>* __restrict__ 
   run_passes<R, P, 0, true, true, true>(bufs + v * SH::VSTR, tw, tid, ld, st);
 }
 
-// Stage iii, row pass: half spectra A = T[s][kx][y0], B = T[s][kx][y0 + 1]
-// of two real rows, packed as Z = A + iB with the Hermitian extension
-// Z[P - kx] = conj(A) + i conj(B), inverse FFT over x; Re -> row y0,
-// Im -> row y0 + 1, columns [0, nx_out) kept. With `sub`, writes
-// image - sub and accumulates its squares (FP64) per block into partials.
-// With sampling on, only the scan positions are kept, written compactly to
-// out[s][my][mx] (the measurement operator of Sec. 3.3); `sub` has that layout.
-template <typename R, int P, bool SAMP>
-__global__ void __launch_bounds__(kThreads) k_row_c2r(const cx<R>* __restrict__ T, int tstride,
-                                                      int64_t tslice, int nx_out, int ny_out,
-                                                      R* __restrict__ out, int64_t out_stride,
-                                                      const R* __restrict__ sub,
-                                                      double* __restrict__ partials,
-                                                      const cx<R>* __restrict__ tw_g, Samp sm) {
+// Stage iii row pass, first half: the half spectra A = T[kx][y0], B =
+// T[kx][y0 + 1] of the block's VPB row pairs, packed Hermitian-extended into
+// the work vectors. All global loads first (independent, in flight
+// together), then the packing into shared memory.
+template <typename R, int P>
+__device__ __forceinline__ void load_packed_pairs(const cx<R>* __restrict__ src, int tstride,
+                                                  int pair0, int ny_out, cx<R>* bufs) {
   using SH = Shape<P>;
-  cx<R>* tw;
-  cx<R>* bufs = setup_smem<R, P>(tw_g, &tw);
-  const int v = threadIdx.x / SH::TPV, tid = threadIdx.x % SH::TPV;
-  const int64_t s = blockIdx.y;
-  const int pair0 = blockIdx.x * SH::VPB;
-  const cx<R>* src = T + s * tslice;
-  pdl_wait();
-  // all global loads first (independent, in flight together), then the
-  // Hermitian packing into shared memory
   constexpr int NH = SH::VPB * (P / 2 + 1);
   constexpr int NIT = (NH + kThreads - 1) / kThreads;
   constexpr int CH = 4;  // loads in flight per thread (bounded to keep occupancy)
@@ -490,12 +474,103 @@ __global__ void __launch_bounds__(kThreads) k_row_c2r(const cx<R>* __restrict__ 
       pack_pair<R, P>(bufs + vv * SH::VSTR, kx, A, B);
     }
   }
+}
+
+// Stage iii, row pass: half spectra A = T[s][kx][y0], B = T[s][kx][y0 + 1]
+// of two real rows, packed as Z = A + iB with the Hermitian extension
+// Z[P - kx] = conj(A) + i conj(B), inverse FFT over x; Re -> row y0,
+// Im -> row y0 + 1, columns [0, nx_out) kept. With `sub`, writes
+// image - sub and accumulates its squares (FP64) per block into partials.
+// With sampling on, only the scan positions are kept, written compactly to
+// out[s][my][mx] (the measurement operator of Sec. 3.3); `sub` has that layout.
+template <typename R, int P, bool SAMP>
+__global__ void __launch_bounds__(kThreads) k_row_c2r(const cx<R>* __restrict__ T, int tstride,
+                                                      int64_t tslice, int nx_out, int ny_out,
+                                                      R* __restrict__ out, int64_t out_stride,
+                                                      const R* __restrict__ sub,
+                                                      double* __restrict__ partials,
+                                                      const cx<R>* __restrict__ tw_g, Samp sm) {
+  using SH = Shape<P>;
+  cx<R>* tw;
+  cx<R>* bufs = setup_smem<R, P>(tw_g, &tw);
+  const int v = threadIdx.x / SH::TPV, tid = threadIdx.x % SH::TPV;
+  const int64_t s = blockIdx.y;
+  const int pair0 = blockIdx.x * SH::VPB;
+  const cx<R>* src = T + s * tslice;
+  pdl_wait();
+  load_packed_pairs<R, P>(src, tstride, pair0, ny_out, bufs);
   __syncthreads();
   RowPairStore<R, SAMP> st(out + s * out_stride, sub ? sub + s * out_stride : nullptr,
                            2 * (pair0 + v), nx_out, ny_out, sm);
   SmemLoad<R> ld;
   run_passes<R, P, 0, true, false, true>(bufs + v * SH::VSTR, tw, tid, ld, st);
   if (partials) block_sum_to(st.acc, partials + (int64_t)blockIdx.y * gridDim.x + blockIdx.x);
+}
+
+// Residual row pass between H and H* (the gradient of Eq. 15): for the
+// block's row pairs of slice s, the inverse row transform as k_row_c2r does
+// it, then r = image - y at the kept (scan) positions and zero elsewhere, its
+// squares summed in FP64 into partials, then the forward row transform of r as
+// k_row_r2c does it, its half spectra written back over the same rows of T
+// (each block reads its rows entirely before writing them). The residual
+// itself never leaves the chip.
+template <typename R, int P, bool SAMP>
+__global__ void __launch_bounds__(kThreads) k_row_resid(cx<R>* __restrict__ T, int tstride,
+                                                        int64_t tslice, int nx, int ny,
+                                                        const R* __restrict__ y,
+                                                        int64_t y_stride,
+                                                        double* __restrict__ partials,
+                                                        const cx<R>* __restrict__ tw_g, Samp sm) {
+  using SH = Shape<P>;
+  cx<R>* tw;
+  cx<R>* bufs = setup_smem<R, P>(tw_g, &tw);
+  const int v = threadIdx.x / SH::TPV, tid = threadIdx.x % SH::TPV;
+  const int64_t s = blockIdx.y;
+  const int pair0 = blockIdx.x * SH::VPB;
+  cx<R>* Ts = T + s * tslice;
+  pdl_wait();
+  load_packed_pairs<R, P>(Ts, tstride, pair0, ny, bufs);
+  __syncthreads();
+  cx<R>* b = bufs + v * SH::VSTR;
+  SmemLoad<R> sl;
+  NoStore<R> ns;
+  run_passes<R, P, 0, true, false, false>(b, tw, tid, sl, ns);  // image rows, natural order
+  // the layout of y: the row pair's offsets (scan rows with sampling on)
+  const int y0 = 2 * (pair0 + v);
+  RowPairStore<R, SAMP> rows(nullptr, y + s * y_stride, y0, nx, ny, sm);
+  double acc = 0.0;
+  for (int x = tid; x < P; x += SH::TPV) {
+    const cx<R> z = b[pidx(x)];
+    R r0 = 0, r1 = 0;
+    int xi = x < nx ? x : -1;
+    if (SAMP && xi >= 0) xi = scan_index(x, sm.ox, sm.sx, sm.mx);
+    if (xi >= 0) {
+      if (rows.ok0) {
+        r0 = z.x - rows.sslice[rows.off0 + xi];
+        acc += (double)r0 * (double)r0;
+      }
+      if (rows.ok1) {
+        r1 = z.y - rows.sslice[rows.off1 + xi];
+        acc += (double)r1 * (double)r1;
+      }
+    }
+    b[pidx(x)] = mk<R>(r0, r1);
+  }
+  __syncthreads();
+  run_passes<R, P, 0, false, false, false>(b, tw, tid, sl, ns);  // spectrum of r0 + i r1
+#pragma unroll 4
+  for (int i = threadIdx.x; i < SH::VPB * (P / 2 + 1); i += kThreads) {
+    const int vv = i % SH::VPB, kx = i / SH::VPB;
+    const int yy = 2 * (pair0 + vv);
+    if (yy >= ny) continue;
+    cx<R> A, B;
+    untangle(bufs[vv * SH::VSTR + pidx(kx)], bufs[vv * SH::VSTR + pidx((P - kx) & (P - 1))], &A,
+             &B);
+    cx<R>* o = Ts + (int64_t)kx * tstride + yy;
+    o[0] = A;
+    o[1] = B;  // tstride is even, so yy + 1 < tstride
+  }
+  if (partials) block_sum_to(acc, partials + (int64_t)blockIdx.y * gridDim.x + blockIdx.x);
 }
 
 template <typename R, int P>
@@ -558,6 +633,21 @@ cudaError_t row_c2r(const cx<R>* T, int tstride, int64_t tslice, int nx_out, int
   *nblocks = (int)(grid.x * grid.y);
   return launch_pdl(fn, grid, dim3(kThreads), smem_bytes<R, P>(), st, T, tstride, tslice, nx_out,
                     ny_out, out, out_stride, sub, partials, tw, sm);
+}
+
+template <typename R, int P>
+cudaError_t row_resid(cx<R>* T, int tstride, int64_t tslice, int nx, int ny, const R* y,
+                      int64_t y_stride, int S, double* partials, const cx<R>* tw, cudaStream_t st,
+                      int* nblocks, Samp sm) {
+  using SH = Shape<P>;
+  auto fn = sm.on ? k_row_resid<R, P, true> : k_row_resid<R, P, false>;
+  cudaError_t e = set_smem_attr<R, P>((const void*)fn);
+  if (e != cudaSuccess) return e;
+  const int pairs = (ny + 1) / 2;
+  dim3 grid((pairs + SH::VPB - 1) / SH::VPB, S);
+  *nblocks = (int)(grid.x * grid.y);
+  return launch_pdl(fn, grid, dim3(kThreads), smem_bytes<R, P>(), st, T, tstride, tslice, nx, ny, y,
+                    y_stride, partials, tw, sm);
 }
 
 #define PAT_P_SWITCH(PV, CALL)                           \
@@ -624,7 +714,58 @@ cudaError_t image_t(const Plan& p, const cx<R>* in, int64_t in_stride, R* out, i
   return cudaSuccess;
 }
 
+// Spectra of H x -> spectra of the residual r = S H x - y (S the measurement
+// operator, identity without sampling): column inverse pass into T, the fused
+// residual row pass in place, column forward pass into out; ||r||^2 summed as
+// image_t does.
+template <typename R>
+cudaError_t residual_t(const Plan& p, const cx<R>* in, int64_t in_stride, const R* y,
+                       int64_t y_stride, int S, double* sumsq, cudaStream_t st, int groups,
+                       double* group_sums, Samp sm, const int* slot, cx<R>* out,
+                       int64_t out_stride) {
+  const Layout& L = p.L;
+  cx<R>* T = static_cast<cx<R>*>(p.T);
+  const cx<R>* twx = static_cast<const cx<R>*>(p.twx);
+  const cx<R>* twy = static_cast<const cx<R>*>(p.twy);
+  cudaError_t e;
+  int nblocks = 0;
+  const bool grouped = groups > 0 && group_sums != nullptr;
+  double* partials = (sumsq || grouped) ? p.red : nullptr;
+  auto col = [&]() -> cudaError_t {
+    PAT_P_SWITCH(L.py, (col_inv<R, P_>(in, in_stride, L.px / 2 + 1, S, T, L.tstride, L.tslice, L.ny,
+                                        twy, st, slot)))
+  };
+  if ((e = col()) != cudaSuccess) return e;
+  auto row = [&]() -> cudaError_t {
+    PAT_P_SWITCH(L.px, (row_resid<R, P_>(T, L.tstride, L.tslice, L.nx, L.ny, y, y_stride, S,
+                                          partials, twx, st, &nblocks, sm)))
+  };
+  if ((e = row()) != cudaSuccess) return e;
+  if (grouped) e = launch_group_sums(p.red, nblocks / groups, groups, group_sums, st);
+  else if (sumsq) e = launch_partials_sum(p.red, nblocks, sumsq, st);
+  if (e != cudaSuccess) return e;
+  auto colf = [&]() -> cudaError_t {
+    PAT_P_SWITCH(L.py, (col_fwd<R, P_>(T, L.tstride, L.tslice, L.ny, L.px / 2 + 1, S, out,
+                                        out_stride, twy, st, slot)))
+  };
+  return colf();
+}
+
 }  // namespace
+
+cudaError_t launch_residual(const Plan& p, const void* in, int64_t in_stride, const void* y,
+                            int64_t y_stride, int S, double* sumsq, cudaStream_t s, int groups,
+                            double* group_sums, Samp sm, const int* slot, void* out,
+                            int64_t out_stride) {
+  if (S <= 0) return cudaSuccess;
+  if (p.L.fp64)
+    return residual_t<double>(p, static_cast<const cx<double>*>(in), in_stride,
+                              static_cast<const double*>(y), y_stride, S, sumsq, s, groups,
+                              group_sums, sm, slot, static_cast<cx<double>*>(out), out_stride);
+  return residual_t<float>(p, static_cast<const cx<float>*>(in), in_stride,
+                           static_cast<const float*>(y), y_stride, S, sumsq, s, groups, group_sums,
+                           sm, slot, static_cast<cx<float>*>(out), out_stride);
+}
 
 cudaError_t launch_spectrum(const Plan& p, const void* in, int64_t in_stride, int nx_in, int ny_in,
                             void* out, int64_t out_stride, int S, cudaStream_t s, Samp sm,

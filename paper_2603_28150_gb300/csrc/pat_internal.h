@@ -218,6 +218,11 @@ cudaError_t forward_dev(const Plan& p, const void* rho, void* d, int batch, cuda
                         const void* sub = nullptr, double* sumsq = nullptr, int groups = 0,
                         double* group_sums = nullptr);
 cudaError_t adjoint_dev(const Plan& p, const void* d, void* rho, int batch, cudaStream_t s);
+// grad = H*(S H x - y) (Eq. 15) with ||S H x - y||^2 summed into *sumsq, or per
+// group of nt slices into group_sums[groups]; the residual stays on the chip.
+cudaError_t gradient_dev(const Plan& p, const void* x, const void* y, void* grad, int batch,
+                         cudaStream_t s, double* sumsq, int groups = 0,
+                         double* group_sums = nullptr);
 // Records the kernel nodes of `graph`; instantiates it.
 cudaError_t instantiate_counted(cudaGraph_t graph, cudaGraphExec_t* exec, int* kernels);
 
@@ -260,6 +265,14 @@ cudaError_t launch_image(const Plan& p, const void* in, int64_t in_stride, void*
                          int64_t out_stride, int S, const void* sub, double* sumsq,
                          cudaStream_t s, int groups = 0, double* group_sums = nullptr,
                          Samp samp = no_sampling(), const int* slot = nullptr);
+// Stage iii then stage i on the data side of the gradient (Eq. 15): spectra
+// of H x (rows of in_stride) -> spectra of r = S H x - y (rows of out_stride;
+// out may be in), y [S][my][mx] with slice stride y_stride; ||r||^2 as in
+// launch_image. The residual image is never stored.
+cudaError_t launch_residual(const Plan& p, const void* in, int64_t in_stride, const void* y,
+                            int64_t y_stride, int S, double* sumsq, cudaStream_t s, int groups,
+                            double* group_sums, Samp samp, const int* slot, void* out,
+                            int64_t out_stride);
 // Contractions over the resident table (tensor cores when the plan has the
 // split tables and batch >= tc_min_batch).
 cudaError_t launch_contract_fwd(const Plan& p, const void* X, void* Y, int batch, cudaStream_t s);

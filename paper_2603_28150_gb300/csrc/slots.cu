@@ -74,9 +74,8 @@ cudaError_t slot_step(pat_plan* pp, int n, cudaStream_t s) {
   Plan& p = pp->p;
   Slots& sl = pp->x.slots;
   const Layout& L = p.L;
-  cudaError_t e = forward_dev(p, p.vol_a, p.dat_a, n, s, p.dat_b, nullptr, n, sl.r2);
+  cudaError_t e = gradient_dev(p, p.vol_a, p.dat_b, p.vol_c, n, s, nullptr, n, sl.r2);
   if (e != cudaSuccess) return e;
-  if ((e = adjoint_dev(p, p.dat_a, p.vol_c, n, s)) != cudaSuccess) return e;
   const int64_t vol = (int64_t)L.nz * L.ny * L.nx, tot = vol * n;
   int64_t g = (tot + 255) / 256;
   if (g > 152 * 16) g = 152 * 16;
