@@ -260,7 +260,8 @@ cudaError_t forward_dev(const Plan& p, const void* rho, void* d, int batch, cuda
 }
 
 cudaError_t gradient_dev(const Plan& p, const void* x, const void* y, void* grad, int batch,
-                         cudaStream_t s, double* sumsq, int groups, double* group_sums) {
+                         cudaStream_t s, double* sumsq, int groups, double* group_sums,
+                         const FistaStep* step) {
   const Layout& L = p.L;
   const int64_t plane = (int64_t)L.ny * L.nx, scan = (int64_t)L.my * L.mx;
   const bool sl = tc_slots(p, batch);
@@ -274,6 +275,7 @@ cudaError_t gradient_dev(const Plan& p, const void* x, const void* y, void* grad
                            sampling_of(L), slot, p.Y, row)) != cudaSuccess)
     return e;
   if ((e = launch_contract_adj(p, p.Y, p.X, batch, s)) != cudaSuccess) return e;
+  if (step) return launch_image_step(p, p.X, row, batch * L.nz, *step, s, slot);
   return launch_image(p, p.X, row, grad, plane, batch * L.nz, nullptr, nullptr, s, 0, nullptr,
                       no_sampling(), slot);
 }
@@ -379,12 +381,10 @@ int power_dev(pat_plan* pp, int iters, double* L_out, cudaStream_t s) {
 cudaError_t fista_iter(pat_plan* pp, int batch, cudaStream_t s) {
   Plan& p = pp->p;
   PlanExt& x = pp->x;
-  const Layout& L = p.L;
-  cudaError_t e = gradient_dev(p, p.vol_a, p.dat_b, p.vol_c, batch, s, x.res + 1);
-  if (e != cudaSuccess) return e;
-  return launch_fista_update(p, p.vol_a, p.vol_b, p.vol_c, (int64_t)obj_elems(L, batch), x.scal,
-                             p.betas, p.iter_dev, x.res + 1, p.r2_dev, p.r2_cap,
-                             reinterpret_cast<unsigned*>(p.iter_dev + 1), s);
+  // the gradient's last stage applies the step in place (no gradient array)
+  const FistaStep step{p.vol_a, p.vol_b, x.scal, p.betas, p.iter_dev, x.res + 1, p.r2_dev,
+                       p.r2_cap, reinterpret_cast<unsigned*>(p.iter_dev + 1)};
+  return gradient_dev(p, p.vol_a, p.dat_b, nullptr, batch, s, x.res + 1, 0, nullptr, &step);
 }
 
 Graph* graph_for(pat_plan* pp, int batch, int* rc) {

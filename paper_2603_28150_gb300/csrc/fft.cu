@@ -573,6 +573,61 @@ __global__ void __launch_bounds__(kThreads) k_row_resid(cx<R>* __restrict__ T, i
   if (partials) block_sum_to(acc, partials + (int64_t)blockIdx.y * gridDim.x + blockIdx.x);
 }
 
+// Stage iii row pass over the depth slices with the FISTA step (Eq. 14-15)
+// in place of the gradient store: each gradient value g of the kept columns
+// updates y (momentum point) and xprev (x_{k-1}) of its voxel in place; the
+// last block to finish advances the iteration (see FistaStep).
+template <typename R, int P>
+__global__ void __launch_bounds__(kThreads) k_row_c2r_step(
+    const cx<R>* __restrict__ T, int tstride, int64_t tslice, int nx, int ny, int64_t plane,
+    R* __restrict__ yv, R* __restrict__ xprev, const double* __restrict__ scal,
+    const double* __restrict__ betas, int* __restrict__ iter, const double* __restrict__ r2_cur,
+    double* __restrict__ r2_hist, int cap, unsigned* __restrict__ done,
+    const cx<R>* __restrict__ tw_g) {
+  using SH = Shape<P>;
+  cx<R>* tw;
+  cx<R>* bufs = setup_smem<R, P>(tw_g, &tw);
+  const int v = threadIdx.x / SH::TPV, tid = threadIdx.x % SH::TPV;
+  const int64_t s = blockIdx.y;
+  const int pair0 = blockIdx.x * SH::VPB;
+  pdl_wait();
+  const R invL = (R)scal[0], lamL = (R)scal[1];
+  const int k = *iter;
+  const R beta = (R)betas[k];
+  load_packed_pairs<R, P>(T + s * tslice, tstride, pair0, ny, bufs);
+  __syncthreads();
+  const int y0 = 2 * (pair0 + v);
+  const bool ok0 = y0 < ny, ok1 = y0 + 1 < ny;
+  R* ys = yv + s * plane + (int64_t)y0 * nx;
+  R* xs = xprev + s * plane + (int64_t)y0 * nx;
+  auto upd = [&](int64_t i, R g) {
+    const R ya = ys[i], xp = xs[i];
+    R x = ya - g * invL - lamL;
+    x = x > (R)0 ? x : (R)0;
+    ys[i] = x + beta * (x - xp);
+    xs[i] = x;
+  };
+  auto st = [&](int x, cx<R> z) {
+    if (x >= nx) return;
+    if (ok0) upd(x, z.x);
+    if (ok1) upd((int64_t)nx + x, z.y);
+  };
+  SmemLoad<R> ld;
+  run_passes<R, P, 0, true, false, true>(bufs + v * SH::VSTR, tw, tid, ld, st);
+  __shared__ bool last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(done, 1u) == gridDim.x * gridDim.y - 1;
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    if (k < cap) r2_hist[k] = *r2_cur;
+    *iter = k + 1;
+    *done = 0;
+  }
+}
+
 template <typename R, int P>
 cudaError_t set_smem_attr(const void* fn) {
   return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -648,6 +703,20 @@ cudaError_t row_resid(cx<R>* T, int tstride, int64_t tslice, int nx, int ny, con
   *nblocks = (int)(grid.x * grid.y);
   return launch_pdl(fn, grid, dim3(kThreads), smem_bytes<R, P>(), st, T, tstride, tslice, nx, ny, y,
                     y_stride, partials, tw, sm);
+}
+
+template <typename R, int P>
+cudaError_t row_c2r_step(const cx<R>* T, int tstride, int64_t tslice, int nx, int ny,
+                         int64_t plane, int S, const FistaStep& f, const cx<R>* tw,
+                         cudaStream_t st) {
+  using SH = Shape<P>;
+  cudaError_t e = set_smem_attr<R, P>((const void*)k_row_c2r_step<R, P>);
+  if (e != cudaSuccess) return e;
+  const int pairs = (ny + 1) / 2;
+  dim3 grid((pairs + SH::VPB - 1) / SH::VPB, S);
+  return launch_pdl(k_row_c2r_step<R, P>, grid, dim3(kThreads), smem_bytes<R, P>(), st, T, tstride,
+                    tslice, nx, ny, plane, static_cast<R*>(f.y), static_cast<R*>(f.xprev), f.scal,
+                    f.betas, f.iter, f.r2_cur, f.r2_hist, f.cap, f.done, tw);
 }
 
 #define PAT_P_SWITCH(PV, CALL)                           \
@@ -751,7 +820,36 @@ cudaError_t residual_t(const Plan& p, const cx<R>* in, int64_t in_stride, const 
   return colf();
 }
 
+template <typename R>
+cudaError_t image_step_t(const Plan& p, const cx<R>* in, int64_t in_stride, int S,
+                         const FistaStep& f, cudaStream_t st, const int* slot) {
+  const Layout& L = p.L;
+  cx<R>* T = static_cast<cx<R>*>(p.T);
+  const cx<R>* twx = static_cast<const cx<R>*>(p.twx);
+  const cx<R>* twy = static_cast<const cx<R>*>(p.twy);
+  cudaError_t e;
+  auto col = [&]() -> cudaError_t {
+    PAT_P_SWITCH(L.py, (col_inv<R, P_>(in, in_stride, L.px / 2 + 1, S, T, L.tstride, L.tslice, L.ny,
+                                        twy, st, slot)))
+  };
+  if ((e = col()) != cudaSuccess) return e;
+  const int64_t plane = (int64_t)L.ny * L.nx;
+  auto row = [&]() -> cudaError_t {
+    PAT_P_SWITCH(L.px, (row_c2r_step<R, P_>(T, L.tstride, L.tslice, L.nx, L.ny, plane, S, f, twx,
+                                             st)))
+  };
+  return row();
+}
+
 }  // namespace
+
+cudaError_t launch_image_step(const Plan& p, const void* in, int64_t in_stride, int S,
+                              const FistaStep& f, cudaStream_t s, const int* slot) {
+  if (S <= 0) return cudaSuccess;
+  if (p.L.fp64)
+    return image_step_t<double>(p, static_cast<const cx<double>*>(in), in_stride, S, f, s, slot);
+  return image_step_t<float>(p, static_cast<const cx<float>*>(in), in_stride, S, f, s, slot);
+}
 
 cudaError_t launch_residual(const Plan& p, const void* in, int64_t in_stride, const void* y,
                             int64_t y_stride, int S, double* sumsq, cudaStream_t s, int groups,

@@ -211,6 +211,8 @@ struct PlanExt {
   Slots slots;
 };
 
+struct FistaStep;  // below
+
 // d = H rho / rho = H* d on device buffers of the plan's precision; with `sub`,
 // the forward writes H rho - sub and sums its squares (FP64) into *sumsq, or,
 // with groups > 0, per group of nt slices into group_sums[groups].
@@ -222,7 +224,7 @@ cudaError_t adjoint_dev(const Plan& p, const void* d, void* rho, int batch, cuda
 // group of nt slices into group_sums[groups]; the residual stays on the chip.
 cudaError_t gradient_dev(const Plan& p, const void* x, const void* y, void* grad, int batch,
                          cudaStream_t s, double* sumsq, int groups = 0,
-                         double* group_sums = nullptr);
+                         double* group_sums = nullptr, const FistaStep* step = nullptr);
 // Records the kernel nodes of `graph`; instantiates it.
 cudaError_t instantiate_counted(cudaGraph_t graph, cudaGraphExec_t* exec, int* kernels);
 
@@ -273,6 +275,27 @@ cudaError_t launch_residual(const Plan& p, const void* in, int64_t in_stride, co
                             int64_t y_stride, int S, double* sumsq, cudaStream_t s, int groups,
                             double* group_sums, Samp samp, const int* slot, void* out,
                             int64_t out_stride);
+// FISTA step (Eq. 14-15) fused into the last stage of the gradient: with g =
+// H*(S H y_k - d) at a voxel, x_k = max(y_k - g/L - lambda/L, 0) and
+// y_{k+1} = x_k + beta_k (x_k - x_{k-1}), scal = {1/L, lambda/L}, beta_k =
+// betas[*iter] (device); y and xprev are updated in place. The last block to
+// finish records r2_hist[*iter] = *r2_cur (if *iter < cap) and advances *iter
+// (`done`: a zero-initialised block counter the kernel resets).
+struct FistaStep {
+  void* y;
+  void* xprev;
+  const double* scal;
+  const double* betas;
+  int* iter;
+  const double* r2_cur;
+  double* r2_hist;
+  int cap;
+  unsigned* done;
+};
+// Stage iii over the depth slices of `S` = batch * nz spectra with the FISTA
+// step in place of the gradient store.
+cudaError_t launch_image_step(const Plan& p, const void* in, int64_t in_stride, int S,
+                              const FistaStep& f, cudaStream_t s, const int* slot);
 // Contractions over the resident table (tensor cores when the plan has the
 // split tables and batch >= tc_min_batch).
 cudaError_t launch_contract_fwd(const Plan& p, const void* X, void* Y, int batch, cudaStream_t s);
@@ -330,13 +353,6 @@ cudaError_t launch_partials_sum(const double* partials, int n, double* out, cuda
 // out[g] = sum of partials[g * per, (g + 1) * per) for g < groups (in order, FP64).
 cudaError_t launch_group_sums(const double* partials, int per, int groups, double* out,
                               cudaStream_t s);
-// FISTA step; scal = {1/L, lambda/L}, beta_k = betas[*iter] (device memory);
-// then r2_hist[*iter] = *r2_cur (if *iter < cap) and ++*iter, by the last
-// block to finish (`done`: a zero-initialised counter the kernel resets).
-cudaError_t launch_fista_update(const Plan& p, void* y, void* xprev, const void* grad, int64_t n,
-                                const double* scal, const double* betas, int* iter,
-                                const double* r2_cur, double* r2_hist, int cap, unsigned* done,
-                                cudaStream_t s);
 cudaError_t launch_scale_by_inv_norm(const Plan& p, const void* in, void* out, int64_t n,
                                      const double* sumsq_dev, cudaStream_t s);
 cudaError_t launch_tick(int* counter, cudaStream_t s);

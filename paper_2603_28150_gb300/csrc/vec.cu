@@ -1,6 +1,7 @@
 // Vector kernels around the operator: FP64 inner products and norms (the
-// adjoint test of Eq. 9, FISTA residuals, the power iteration for ||H*H||),
-// the FISTA proximal/momentum update (Eq. 14-15), and small helpers.
+// adjoint test of Eq. 9, FISTA residuals, the power iteration for ||H*H||)
+// and small helpers. (The FISTA proximal/momentum update of Eq. 14-15 is
+// fused into the last FFT stage of the gradient, fft.cu.)
 // Reductions are deterministic: fixed grid, per-block tree sums, then one
 // block sums the partials in index order.
 #include "pat_internal.h"
@@ -57,69 +58,6 @@ __global__ void __launch_bounds__(256) k_group_sums(const double* __restrict__ p
   if (threadIdx.x == 0) out[blockIdx.x] = s;
 }
 
-// x_k = max(y - g/L - lambda/L, 0) (prox of Eq. 14 after the gradient step of
-// Eq. 15); y <- x_k + beta_k (x_k - x_{k-1}); xprev <- x_k. The scalars 1/L,
-// lambda/L (scal) and beta_k = betas[*iter] are read from device memory so one
-// captured graph serves every iteration. The last block to finish records
-// this iteration's ||H y_k - d||^2 (*r2_cur) in r2_hist[*iter] and advances
-// *iter (every block has read *iter before it counts itself done).
-template <typename R>
-__global__ void __launch_bounds__(kBlock) k_fista_update(R* __restrict__ y, R* __restrict__ xprev,
-                                                         const R* __restrict__ grad, int64_t n,
-                                                         const double* __restrict__ scal,
-                                                         const double* __restrict__ betas,
-                                                         int* __restrict__ iter,
-                                                         const double* __restrict__ r2_cur,
-                                                         double* __restrict__ r2_hist, int cap,
-                                                         unsigned* __restrict__ done) {
-  pdl_wait();
-  const R invL = (R)scal[0], lamL = (R)scal[1];
-  const int k = *iter;
-  const R beta = (R)betas[k];
-  auto step = [&](R yv, R g, R xp, R* yo, R* xo) {
-    R x = yv - g * invL - lamL;
-    x = x > (R)0 ? x : (R)0;
-    *yo = x + beta * (x - xp);
-    *xo = x;
-  };
-  const int64_t t0 = blockIdx.x * (int64_t)kBlock + threadIdx.x, nth = (int64_t)gridDim.x * kBlock;
-  int64_t head = 0;
-  if constexpr (sizeof(R) == 4) {  // 16-byte accesses (the plan's buffers are 256-byte aligned)
-    head = n & ~(int64_t)3;
-    float4* y4 = reinterpret_cast<float4*>(y);
-    float4* x4 = reinterpret_cast<float4*>(xprev);
-    const float4* g4 = reinterpret_cast<const float4*>(grad);
-    for (int64_t i = t0; i < head / 4; i += nth) {
-      const float4 yv = y4[i], g = __ldg(g4 + i), xp = x4[i];
-      float4 yo, xo;
-      step(yv.x, g.x, xp.x, &yo.x, &xo.x);
-      step(yv.y, g.y, xp.y, &yo.y, &xo.y);
-      step(yv.z, g.z, xp.z, &yo.z, &xo.z);
-      step(yv.w, g.w, xp.w, &yo.w, &xo.w);
-      y4[i] = yo;
-      x4[i] = xo;
-    }
-  }
-  for (int64_t i = head + t0; i < n; i += nth) {
-    R yo, xo;
-    step(y[i], grad[i], xprev[i], &yo, &xo);
-    y[i] = yo;
-    xprev[i] = xo;
-  }
-  __shared__ bool last;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    last = atomicAdd(done, 1u) == gridDim.x - 1;
-  }
-  __syncthreads();
-  if (last && threadIdx.x == 0) {
-    if (k < cap) r2_hist[k] = *r2_cur;
-    *iter = k + 1;
-    *done = 0;
-  }
-}
-
 template <typename R>
 __global__ void __launch_bounds__(kBlock) k_scale(const R* __restrict__ in, R* __restrict__ out,
                                                   int64_t n, const double* __restrict__ sumsq) {
@@ -158,21 +96,6 @@ cudaError_t launch_dot(const Plan& p, const void* a, const void* b, int64_t n, d
                             static_cast<const float*>(a), static_cast<const float*>(b), n, p.red);
   if (e != cudaSuccess) return e;
   return launch_partials_sum(p.red, g, out_dev, s);
-}
-
-cudaError_t launch_fista_update(const Plan& p, void* y, void* xprev, const void* grad, int64_t n,
-                                const double* scal, const double* betas, int* iter,
-                                const double* r2_cur, double* r2_hist, int cap, unsigned* done,
-                                cudaStream_t s) {
-  const int g = grid_for(p.L.fp64 ? n : (n + 3) / 4, 152 * 16);
-  if (p.L.fp64)
-    return launch_pdl(k_fista_update<double>, dim3(g), dim3(kBlock), 0, s,
-                      static_cast<double*>(y), static_cast<double*>(xprev),
-                      static_cast<const double*>(grad), n, scal, betas, iter, r2_cur, r2_hist, cap,
-                      done);
-  return launch_pdl(k_fista_update<float>, dim3(g), dim3(kBlock), 0, s, static_cast<float*>(y),
-                    static_cast<float*>(xprev), static_cast<const float*>(grad), n, scal, betas,
-                    iter, r2_cur, r2_hist, cap, done);
 }
 
 cudaError_t launch_scale_by_inv_norm(const Plan& p, const void* in, void* out, int64_t n,
