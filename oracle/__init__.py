@@ -200,6 +200,22 @@ def adjoint_fft(Hf, d, g: Grid) -> np.ndarray:
     return rho
 
 
+# ----------------------------------------------------------------------------- sensor response
+def apply_sensor_response(h, r) -> np.ndarray:
+    """Kernels with the sensors' temporal impulse response folded in (Sec. 2:
+    identical, spatially invariant sensor responses incorporated into the
+    kernels by temporal convolution): h'[z][t] = sum_{tau <= t} r[tau] h[z][t - tau]
+    over the recorded samples t < nt (causal, r[0] at lag 0), for every
+    transverse position. h: [nz][nt][py][px]."""
+    h, r = _f64(h), _f64(r).ravel()
+    nt = h.shape[1]
+    out = np.zeros_like(h)
+    for t in range(nt):
+        for tau in range(min(len(r), t + 1)):
+            out[:, t] += r[tau] * h[:, t - tau]
+    return out
+
+
 # ----------------------------------------------------------------------------- measurement
 def scan_positions(n: int, step: int, offset: int) -> list:
     """Sensor-grid indices of one scan axis: offset, offset + step, ... < n
