@@ -213,6 +213,17 @@ int pat_plan_set_tensor_batch(pat_plan* plan, int min_batch);
  * The diagnostic stage entry points are not affected. */
 int pat_plan_set_sampling(pat_plan* plan, int sx, int sy, int ox, int oy);
 
+/* Folds the sensors' temporal impulse response into the resident library
+ * (Sec. 2: identical, spatially invariant sensor responses incorporated into
+ * the kernels by temporal convolution): every kernel becomes
+ *   h'_z(., t) = sum_{tau = 0 .. min(nr - 1, t)} r[tau] h_z(., t - tau),
+ * causal, r[0] at lag 0, over the recorded samples t < nt, so H' rho is H rho
+ * convolved with r along time at every sensor position. r: host double[nr],
+ * nr >= 1. Calls compose (two calls fold the convolution of both responses).
+ * The split-BF16 tiles, if any, are rebuilt. pat_plan_info's table statistics
+ * keep describing the library as built. Synchronises `stream`. */
+int pat_plan_set_sensor_response(pat_plan* plan, const double* r, int nr, pat_stream stream);
+
 /* Synchronises the device and reports whether any bounded device-side wait of
  * the plan's kernels gave up since the last check (PAT_ERR_TIMEOUT; the flag
  * is cleared), else PAT_OK. */

@@ -552,6 +552,22 @@ int pat_plan_set_sampling(pat_plan* plan, int sx, int sy, int ox, int oy) {
   PAT_GUARD_END
 }
 
+int pat_plan_set_sensor_response(pat_plan* plan, const double* r, int nr, pat_stream stream) {
+  PAT_GUARD_BEGIN
+  if (!plan || !r || nr < 1) return fail(PAT_ERR_ARG, "need a plan, r != NULL and nr >= 1");
+  if (is_device_ptr(r)) return fail(PAT_ERR_ARG, "r must be host memory");
+  Plan& p = plan->p;
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = apply_sensor_response(p, r, nr, s);
+  if (rc != PAT_OK) return rc;
+  if (p.tc_fwd) {  // the split-BF16 tiles follow the table
+    PAT_CUDA(tc_build_tables(p, p.tc_fwd, p.tc_adj, s));
+    PAT_CUDA(cudaStreamSynchronize(s));
+  }
+  return PAT_OK;
+  PAT_GUARD_END
+}
+
 int pat_plan_check(pat_plan* plan) {
   PAT_GUARD_BEGIN
   if (!plan) return fail(PAT_ERR_ARG, "plan is NULL");

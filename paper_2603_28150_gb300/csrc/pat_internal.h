@@ -344,6 +344,9 @@ inline bool fold_possible(const Layout& L) { return L.real && !L.fp64 && L.px ==
 // Builds the folding maps of p (host enumeration, device copies) and sets
 // L.U / Upad / nub; rep_bins (optional) receives each representative's own bin.
 int build_fold_maps(Plan& p, std::vector<int>* rep_bins);
+// Folds the sensors' temporal response r[0..nr) into the resident table
+// (causal convolution along time); synchronises `s`.
+int apply_sensor_response(Plan& p, const double* r, int nr, cudaStream_t s);
 
 // Vector kernels (vec.cu).
 cudaError_t launch_dot(const Plan& p, const void* a, const void* b, int64_t n, double* out_dev,

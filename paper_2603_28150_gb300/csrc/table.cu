@@ -228,7 +228,51 @@ std::vector<double> twiddles(int n) {
   return w;
 }
 
+// Causal FIR along time of every scalar of the resident table, in place:
+// a[t] = sum_{tau < nr, tau <= t} r[tau] a[t - tau] (FP64 sums), computed for
+// t from nt - 1 down to 0 so every term still reads the unfiltered value. The
+// blocked layout keeps, per table block, nt rows of `inner` scalars (real and
+// imaginary parts alike: the response is real).
+template <typename S>
+__global__ void k_sensor_fir(S* __restrict__ table, int64_t blocks, int nt, int64_t inner,
+                             const double* __restrict__ r, int nr) {
+  const int64_t n = blocks * inner;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    S* a = table + (i / inner) * nt * inner + i % inner;
+    for (int t = nt - 1; t >= 0; --t) {
+      double acc = 0.0;
+      const int m = nr < t + 1 ? nr : t + 1;
+      for (int tau = 0; tau < m; ++tau) acc += r[tau] * (double)a[(int64_t)(t - tau) * inner];
+      a[(int64_t)t * inner] = (S)acc;
+    }
+  }
+}
+
 }  // namespace
+
+int apply_sensor_response(Plan& p, const double* r, int nr, cudaStream_t s) {
+  const Layout& L = p.L;
+  const int64_t blocks = L.fold ? L.nub : L.nkb;
+  const int64_t inner = (int64_t)L.nzg * 32 * 16 / (int64_t)L.rsize;
+  double* rd = nullptr;
+  PAT_CUDA(cudaMalloc(&rd, sizeof(double) * nr));
+  cudaError_t e = cudaMemcpyAsync(rd, r, sizeof(double) * nr, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) {
+    const int g = grid_for(blocks * inner);
+    if (L.fp64)
+      k_sensor_fir<double><<<g, 256, 0, s>>>(static_cast<double*>(p.table), blocks, L.nt, inner,
+                                             rd, nr);
+    else
+      k_sensor_fir<float><<<g, 256, 0, s>>>(static_cast<float*>(p.table), blocks, L.nt, inner, rd,
+                                            nr);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(rd);
+  if (e != cudaSuccess) return cuda_fail(e, "applying the sensor response");
+  return PAT_OK;
+}
 
 int build_fold_maps(Plan& p, std::vector<int>* rep_bins) {
   Layout& L = p.L;

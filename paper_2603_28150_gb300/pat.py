@@ -43,7 +43,7 @@ EXPORTS = (
     "pat_fista_solve", "pat_dot_f64", "pat_stage_spectrum", "pat_stage_image",
     "pat_stage_contract", "pat_spectrum_noalloc", "pat_plan_estimate", "pat_slot_load",
     "pat_slot_move", "pat_slots_step", "pat_slot_read", "pat_plan_set_tensor_batch",
-    "pat_plan_check", "pat_plan_set_sampling",
+    "pat_plan_check", "pat_plan_set_sampling", "pat_plan_set_sensor_response",
 )
 
 
@@ -129,6 +129,7 @@ def lib(build_if_missing: bool = True):
         "pat_plan_set_tensor_batch": ([P, I], I),
         "pat_plan_check": ([P], I),
         "pat_plan_set_sampling": ([P, I, I, I, I], I),
+        "pat_plan_set_sensor_response": ([P, D, I, P], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -239,6 +240,14 @@ class Plan:
         self.sampling = (sx, sy, ox, oy)
         self.mx = -(-(self.nx - ox) // sx)
         self.my = -(-(self.ny - oy) // sy)
+
+    def set_sensor_response(self, r, stream=None) -> None:
+        """Folds the sensors' temporal impulse response r (causal, r[0] at lag
+        0) into the resident library by temporal convolution (Sec. 2)."""
+        a = np.ascontiguousarray(np.asarray(r, dtype=np.float64).ravel())
+        _check(lib().pat_plan_set_sensor_response(
+            self._h, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(a.size),
+            _stream(stream)))
 
     def check(self) -> None:
         """Raises PatError(PAT_ERR_TIMEOUT) if a bounded device wait gave up."""
