@@ -71,7 +71,8 @@ enum {
                                  tcgen05 (BF16 hi/lo operands, FP32 accumulation).
                                  Needs a real table, nz = 128, nt in {128, 256, 384, 512},
                                  single precision; else pat_plan_create fails with
-                                 PAT_ERR_UNSUPPORTED. */
+                                 PAT_ERR_UNSUPPORTED. Folded plans keep one tile set
+                                 per representative and contract its bins together. */
 };
 
 /* Grid of one plan.
