@@ -154,7 +154,6 @@ struct Plan {
   void* dat_a = nullptr;  // [max_batch][nt][ny][nx] real: residual
   void* dat_b = nullptr;  // [max_batch][nt][ny][nx] real: measured data copy
   double* red = nullptr;  // reduction scratch: partials + results (see kReduce*)
-  unsigned int* red_counter = nullptr;
   double* betas = nullptr;  // FISTA momentum coefficients per iteration
   int betas_cap = 0;
   int* iter_dev = nullptr;  // [0] FISTA iteration counter (graph replay), [1] block counter
@@ -358,7 +357,5 @@ cudaError_t launch_group_sums(const double* partials, int per, int groups, doubl
                               cudaStream_t s);
 cudaError_t launch_scale_by_inv_norm(const Plan& p, const void* in, void* out, int64_t n,
                                      const double* sumsq_dev, cudaStream_t s);
-cudaError_t launch_tick(int* counter, cudaStream_t s);
-cudaError_t launch_fill_zero(void* ptr, size_t bytes, cudaStream_t s);
 
 }  // namespace pat

@@ -67,8 +67,6 @@ __global__ void __launch_bounds__(kBlock) k_scale(const R* __restrict__ in, R* _
     out[i] = in[i] * s;
 }
 
-__global__ void k_tick(int* c) { *c += 1; }
-
 int grid_for(int64_t n, int cap) {
   int64_t b = (n + kBlock - 1) / kBlock;
   if (b > cap) b = cap;
@@ -108,15 +106,6 @@ cudaError_t launch_scale_by_inv_norm(const Plan& p, const void* in, void* out, i
     k_scale<float><<<g, kBlock, 0, s>>>(static_cast<const float*>(in), static_cast<float*>(out), n,
                                          sumsq_dev);
   return cudaGetLastError();
-}
-
-cudaError_t launch_tick(int* counter, cudaStream_t s) {
-  k_tick<<<1, 1, 0, s>>>(counter);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_fill_zero(void* ptr, size_t bytes, cudaStream_t s) {
-  return cudaMemsetAsync(ptr, 0, bytes, s);
 }
 
 }  // namespace pat
