@@ -45,27 +45,49 @@ static void parallel_for(long n, F f) {
 }
 
 static bool is_pow2(long n) { return n > 0 && (n & (n - 1)) == 0; }
+// Transverse transform lengths: powers of two, or three times a power of two.
+static bool fft_len_ok(long n) { return is_pow2(n) || (n > 0 && n % 3 == 0 && is_pow2(n / 3)); }
 
 static const double kPi = 3.14159265358979323846264338327950288;
 
 // ---------------------------------------------------------------------------
 // FFT: iterative radix-2 Cooley-Tukey (bit-reversal permutation followed by
-// log2(n) butterfly passes). Twiddles w_n^k = exp(-+2 pi i k / n) come from
-// std::cos / std::sin in double precision, one table per transform length.
+// log2(n) butterfly passes) for powers of two; for other lengths the DFT of
+// its definition, sum_m a[m] w^(k m). Twiddles w_n^k = exp(-+2 pi i k / n)
+// come from std::cos / std::sin in double precision, one table per length.
 // ---------------------------------------------------------------------------
 struct Twiddle {
   long n = 0;
-  std::vector<cplx> w;  // w[k] = exp(-2 pi i k / n), k < n/2
-  explicit Twiddle(long n_) : n(n_), w(n_ / 2 > 0 ? n_ / 2 : 1) {
-    for (long k = 0; k < n / 2; ++k) {
+  std::vector<cplx> w;  // w[k] = exp(-2 pi i k / n), k < n
+  explicit Twiddle(long n_) : n(n_), w(n_ > 0 ? n_ : 1) {
+    for (long k = 0; k < n; ++k) {
       double a = -2.0 * kPi * (double)k / (double)n;
       w[k] = cplx(std::cos(a), std::sin(a));
     }
   }
 };
 
+static void dft_inplace(cplx* a, const Twiddle& tw, int inverse) {
+  const long n = tw.n;
+  std::vector<cplx> out(n);
+  for (long k = 0; k < n; ++k) {
+    cplx acc(0.0, 0.0);
+    for (long m = 0; m < n; ++m) {
+      cplx w = tw.w[(k * m) % n];
+      if (inverse) w = std::conj(w);
+      acc += a[m] * w;
+    }
+    out[k] = acc;
+  }
+  for (long k = 0; k < n; ++k) a[k] = out[k];
+}
+
 static void fft_inplace(cplx* a, const Twiddle& tw, int inverse) {
   const long n = tw.n;
+  if (!is_pow2(n)) {
+    dft_inplace(a, tw, inverse);
+    return;
+  }
   for (long i = 1, j = 0; i < n; ++i) {
     long bit = n >> 1;
     for (; j & bit; bit >>= 1) j ^= bit;
@@ -100,7 +122,7 @@ static void fft2_plane(cplx* a, long py, long px, const Twiddle& twx,
 }
 
 extern "C" int orc_fft1d(double* a, long n, int inverse) {
-  if (!is_pow2(n) || a == nullptr) return -1;
+  if (!fft_len_ok(n) || a == nullptr) return -1;
   Twiddle tw(n);
   fft_inplace(reinterpret_cast<cplx*>(a), tw, inverse);
   return 0;
@@ -124,7 +146,7 @@ extern "C" int orc_dft1d(const double* in, double* out, long n, int inverse) {
 }
 
 extern "C" int orc_fft2d(double* a, long py, long px, int inverse) {
-  if (!is_pow2(px) || !is_pow2(py) || a == nullptr) return -1;
+  if (!fft_len_ok(px) || !fft_len_ok(py) || a == nullptr) return -1;
   Twiddle twx(px), twy(py);
   std::vector<cplx> col;
   fft2_plane(reinterpret_cast<cplx*>(a), py, px, twx, twy, inverse, col);
@@ -132,7 +154,7 @@ extern "C" int orc_fft2d(double* a, long py, long px, int inverse) {
 }
 
 extern "C" int orc_fft3d(double* a, long mz, long py, long px, int inverse) {
-  if (!is_pow2(px) || !is_pow2(py) || !is_pow2(mz) || a == nullptr) return -1;
+  if (!fft_len_ok(px) || !fft_len_ok(py) || !is_pow2(mz) || a == nullptr) return -1;
   cplx* c = reinterpret_cast<cplx*>(a);
   Twiddle twx(px), twy(py), twz(mz);
   parallel_for(mz, [&](long z) {
@@ -154,7 +176,7 @@ extern "C" int orc_fft3d(double* a, long mz, long py, long px, int inverse) {
 // ---------------------------------------------------------------------------
 static bool geom_ok(long nx, long ny, long nz, long nt, long px, long py) {
   if (nx <= 0 || ny <= 0 || nz <= 0 || nt <= 0) return false;
-  if (!is_pow2(px) || !is_pow2(py)) return false;
+  if (!fft_len_ok(px) || !fft_len_ok(py)) return false;
   // linear (not circular) convolution needs P >= 2n - 1
   if (px < 2 * nx - 1 || py < 2 * ny - 1) return false;
   return true;
@@ -213,7 +235,7 @@ extern "C" int orc_adjoint_spatial(const double* h, const double* d, double* rho
 
 extern "C" int orc_table_spectrum(const double* h, double* Hf, long nz, long nt,
                                   long px, long py) {
-  if (nz <= 0 || nt <= 0 || !is_pow2(px) || !is_pow2(py) || !h || !Hf) return -1;
+  if (nz <= 0 || nt <= 0 || !fft_len_ok(px) || !fft_len_ok(py) || !h || !Hf) return -1;
   const long plane = px * py;
   Twiddle twx(px), twy(py);
   cplx* out = reinterpret_cast<cplx*>(Hf);
@@ -314,7 +336,7 @@ static inline double wavenumber(long m, long n, double step) {
 extern "C" int orc_kspace_solve(const double* p0, long px, long py, long mz,
                                 orc_medium med, long nt, int closed_form,
                                 const long* planes, long nplanes, double* rec) {
-  if (!is_pow2(px) || !is_pow2(py) || !is_pow2(mz) || nt <= 0 || nplanes <= 0 ||
+  if (!fft_len_ok(px) || !fft_len_ok(py) || !is_pow2(mz) || nt <= 0 || nplanes <= 0 ||
       !p0 || !planes || !rec)
     return -1;
   for (long p = 0; p < nplanes; ++p)
@@ -385,7 +407,7 @@ extern "C" int orc_table_kspace_solve(long px, long py, long mz, orc_medium med,
 extern "C" int orc_table_kspace_closed(long px, long py, long mz, orc_medium med,
                                        long z0, const long* t_idx, long n_t,
                                        const long* z_idx, long n_z, double* Hf) {
-  if (!is_pow2(px) || !is_pow2(py) || !is_pow2(mz) || n_t <= 0 || n_z <= 0 ||
+  if (!fft_len_ok(px) || !fft_len_ok(py) || !is_pow2(mz) || n_t <= 0 || n_z <= 0 ||
       !t_idx || !z_idx || !Hf)
     return -1;
   const long plane = px * py;

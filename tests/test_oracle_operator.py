@@ -19,7 +19,8 @@ def _setup(g, seed=0, even=False):
     return h, rho, d
 
 
-@pytest.mark.parametrize("g", [TINY, SMALL, oracle.Grid(nx=5, ny=7, nz=2, nt=3, px=16, py=16)])
+@pytest.mark.parametrize("g", [TINY, SMALL, oracle.Grid(nx=5, ny=7, nz=2, nt=3, px=16, py=16),
+                               oracle.Grid(nx=20, ny=11, nz=2, nt=3, px=48, py=24)])
 def test_spatial_and_fft_forms_agree(g):
     h, rho, d = _setup(g, 3)
     Hf = oracle.table_spectrum(h)
@@ -36,7 +37,7 @@ def test_spatial_and_fft_forms_agree_32x32x16x64():
     assert oracle.rel_l2(oracle.adjoint_fft(Hf, d, g), oracle.adjoint_spatial(h, d, g)) < 1e-12
 
 
-@pytest.mark.parametrize("n,p", [(6, 16), (8, 16), (9, 32)])
+@pytest.mark.parametrize("n,p", [(6, 16), (8, 16), (9, 32), (10, 24), (12, 48)])
 def test_single_depth_single_time_is_scipy_convolution(n, p):
     """Nz = Nt = 1: H is one 2D linear convolution with the kernel restricted to
     displacements |u| <= n - 1 (the wrapped table unwrapped)."""
