@@ -79,7 +79,8 @@ enum {
  *   nx, ny   transverse grid of rho and d (Sec. 2.2, G_xy)
  *   nz       depth planes of rho (G_z);  nt  time samples of d (T)
  *   px, py   padded transverse grid for linear convolution (Sec. 2.3, end):
- *            powers of two, 16 <= p <= 1024, px >= 2 nx - 1, py >= 2 ny - 1
+ *            2^k or 3 * 2^k (16, 24, 32, 48, ..., 768, 1024), px >= 2 nx - 1,
+ *            py >= 2 ny - 1; other lengths return PAT_ERR_UNSUPPORTED
  *   max_batch  largest `batch` any call on this plan may pass (sizes workspace)
  *   flags    PAT_FLAG_* */
 typedef struct {

@@ -35,8 +35,8 @@ int validate(const pat_geometry* g) {
   if (!g) return fail(PAT_ERR_ARG, "geometry is NULL");
   if (g->nx < 1 || g->ny < 1 || g->nz < 1 || g->nt < 1)
     return fail(PAT_ERR_ARG, "nx, ny, nz, nt must be >= 1");
-  if (!pow2_in(g->px, 16, 1024) || !pow2_in(g->py, 16, 1024))
-    return fail(PAT_ERR_UNSUPPORTED, "px and py must be powers of two in [16, 1024]");
+  if (!fft_len_ok(g->px) || !fft_len_ok(g->py))
+    return fail(PAT_ERR_UNSUPPORTED, "px and py must be 2^k or 3*2^k in [16, 1024]");
   if (g->px < 2 * g->nx - 1 || g->py < 2 * g->ny - 1)
     return fail(PAT_ERR_ARG, "padding too small for linear convolution: need px >= 2nx-1, py >= 2ny-1");
   if (g->max_batch < 1) return fail(PAT_ERR_ARG, "max_batch must be >= 1");

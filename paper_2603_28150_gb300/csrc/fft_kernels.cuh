@@ -1,0 +1,805 @@
+// Batched 2D real FFT stages of the operator (Sec. 3.2, Eq. 16 terms (i) and (iii)).
+//
+// A P-point complex DFT runs as a Stockham auto-sort FFT (Govindaraju et al.,
+// SC'08 formulation) over 1-3 passes of radix 2/4/8/16, or for P = 3 * 2^k a
+// first pass of radix 24 (3 x 8 in registers) then radix 2-8: each thread holds one
+// radix-R butterfly in registers, multiplies by exp(-2 pi i r k / (Ns R))
+// (twiddles from a host FP64 table staged in shared memory) and writes the
+// R outputs to their sorted positions. The first pass can read its inputs
+// straight from global memory and the last pass can write its outputs
+// straight to global memory (in both cases a vector's consecutive threads touch
+// consecutive elements), so shared memory carries each element once between
+// passes. The 2D real transform of a zero-padded n x n slice is split in two
+// kernels so every global access is contiguous:
+//   row pass    two real rows packed as one complex row (a + i b), FFT over x,
+//               untangled into the kx in [0, P/2] half spectra of both rows,
+//               written transposed: T[s][kx][y]
+//   column pass FFT over y of each kx column (only the n data rows are
+//               non-zero), written as X[s][kx][ky] = the contraction's layout.
+// The inverse runs the mirror image: column inverse FFT keeping the first n
+// rows (crop), then a packed complex-to-real row inverse keeping the first n
+// columns. No normalisation here: 1/(px py) is folded into the table.
+//
+// This header holds the kernels and their per-length launchers (FftLen<R, P>,
+// declared in fft_len.h); each fft_*.cu file includes it and instantiates the
+// launchers for a set of lengths, so the lengths compile in parallel.
+#pragma once
+#include "fft_len.h"
+#include "pat_internal.h"
+
+namespace pat {
+namespace {
+
+constexpr int kThreads = 256;
+
+template <int P>
+struct RadixPlan;
+template <> struct RadixPlan<16>   { static constexpr int NST = 1, RMAX = 16; static constexpr int R[3] = {16, 1, 1}; };
+template <> struct RadixPlan<32>   { static constexpr int NST = 2, RMAX = 8;  static constexpr int R[3] = {8, 4, 1}; };
+template <> struct RadixPlan<64>   { static constexpr int NST = 2, RMAX = 8;  static constexpr int R[3] = {8, 8, 1}; };
+template <> struct RadixPlan<128>  { static constexpr int NST = 2, RMAX = 16; static constexpr int R[3] = {16, 8, 1}; };
+template <> struct RadixPlan<256>  { static constexpr int NST = 2, RMAX = 16; static constexpr int R[3] = {16, 16, 1}; };
+template <> struct RadixPlan<512>  { static constexpr int NST = 3, RMAX = 8;  static constexpr int R[3] = {8, 8, 8}; };
+template <> struct RadixPlan<1024> { static constexpr int NST = 3, RMAX = 16; static constexpr int R[3] = {16, 8, 8}; };
+// three times a power of two: a 24-point first pass (every later radix divides 24)
+template <> struct RadixPlan<24>   { static constexpr int NST = 1, RMAX = 24; static constexpr int R[3] = {24, 1, 1}; };
+template <> struct RadixPlan<48>   { static constexpr int NST = 2, RMAX = 24; static constexpr int R[3] = {24, 2, 1}; };
+template <> struct RadixPlan<96>   { static constexpr int NST = 2, RMAX = 24; static constexpr int R[3] = {24, 4, 1}; };
+template <> struct RadixPlan<192>  { static constexpr int NST = 2, RMAX = 24; static constexpr int R[3] = {24, 8, 1}; };
+template <> struct RadixPlan<384>  { static constexpr int NST = 3, RMAX = 24; static constexpr int R[3] = {24, 8, 2}; };
+template <> struct RadixPlan<768>  { static constexpr int NST = 3, RMAX = 24; static constexpr int R[3] = {24, 8, 4}; };
+
+template <int P>
+struct Shape {
+  static constexpr int TPV = P / RadixPlan<P>::RMAX;  // threads per vector
+  static constexpr int VPB = kThreads / TPV;           // vectors per block
+  // padded vector stride: the extra element puts consecutive vectors in
+  // different banks for the transposed (vector-major) accesses of the row kernels
+  static constexpr int VSTR = P + P / 16 + 1;
+};
+
+// Radix of pass S and the product of the radices before it.
+template <int P, int S>
+struct PassOf {
+  static constexpr int RAD = RadixPlan<P>::R[S];
+  static constexpr int NS = S == 0 ? 1 : (S == 1 ? RadixPlan<P>::R[0] : RadixPlan<P>::R[0] * RadixPlan<P>::R[1]);
+};
+
+// One padding slot per 16 elements keeps the radix-16 scatter of the first
+// pass (stride 16) free of shared-memory bank conflicts.
+__device__ __forceinline__ int pidx(int i) { return i + (i >> 4); }
+
+// exp(-2 pi i m / 16) for m in [0, 8) (conjugated for the inverse); m is a
+// compile-time constant after unrolling, so the switch folds away.
+template <typename R, bool INV>
+__device__ __forceinline__ cx<R> mul_w16(cx<R> b, int m) {
+  const R c1 = (R)0.92387953251128675613;  // cos(pi/8)
+  const R s1 = (R)0.38268343236508977173;  // sin(pi/8)
+  const R h = (R)0.70710678118654752440;   // sqrt(2)/2
+  cx<R> w;
+  switch (m) {
+    case 0: return b;
+    case 4: return INV ? mk<R>(-b.y, b.x) : mk<R>(b.y, -b.x);  // * (+-i)
+    case 1: w = mk<R>(c1, -s1); break;
+    case 2: w = mk<R>(h, -h); break;
+    case 3: w = mk<R>(s1, -c1); break;
+    case 5: w = mk<R>(-s1, -c1); break;
+    case 6: w = mk<R>(-h, -h); break;
+    default: w = mk<R>(-c1, -s1); break;
+  }
+  if (INV) w.y = -w.y;
+  return cmul(b, w);
+}
+
+template <int N>
+__host__ __device__ constexpr int bitrev(int i) {
+  int r = 0;
+  for (int b = 1; b < N; b <<= 1) {
+    r = (r << 1) | (i & 1);
+    i >>= 1;
+  }
+  return r;
+}
+
+// Butterfly passes of span LEN, 2 LEN, ..., N (compile-time recursion keeps
+// every register index constant).
+template <typename R, int N, int LEN, bool INV>
+__device__ __forceinline__ void dit_passes(cx<R>* a) {
+#pragma unroll
+  for (int i = 0; i < N; i += LEN) {
+#pragma unroll
+    for (int k = 0; k < LEN / 2; ++k) {
+      cx<R> u = a[i + k];
+      cx<R> t = mul_w16<R, INV>(a[i + k + LEN / 2], k * (16 / LEN));
+      a[i + k] = cadd(u, t);
+      a[i + k + LEN / 2] = csub(u, t);
+    }
+  }
+  if constexpr (LEN < N) dit_passes<R, N, 2 * LEN, INV>(a);
+}
+
+// exp(-2 pi i m / 24) for m in [0, 15) (conjugated for the inverse), from
+// cos/sin of multiples of 15 degrees; m is a compile-time constant after
+// unrolling.
+template <typename R, bool INV>
+__device__ __forceinline__ cx<R> w24(int m) {
+  const R c15 = (R)0.96592582628906828675;  // cos 15 deg = (sqrt 6 + sqrt 2) / 4
+  const R s15 = (R)0.25881904510252076235;  // sin 15 deg = (sqrt 6 - sqrt 2) / 4
+  const R c30 = (R)0.86602540378443864676;  // cos 30 deg = sqrt 3 / 2
+  const R h = (R)0.70710678118654752440;    // cos 45 deg
+  R c, sn;
+  switch (m) {
+    case 0: c = 1; sn = 0; break;
+    case 1: c = c15; sn = s15; break;
+    case 2: c = c30; sn = (R)0.5; break;
+    case 3: c = h; sn = h; break;
+    case 4: c = (R)0.5; sn = c30; break;
+    case 5: c = s15; sn = c15; break;
+    case 6: c = 0; sn = 1; break;
+    case 7: c = -s15; sn = c15; break;
+    case 8: c = (R)-0.5; sn = c30; break;
+    case 9: c = -h; sn = h; break;
+    case 10: c = -c30; sn = (R)0.5; break;
+    case 11: c = -c15; sn = s15; break;
+    case 12: c = -1; sn = 0; break;
+    case 13: c = -c15; sn = -s15; break;
+    default: c = -c30; sn = (R)-0.5; break;
+  }
+  return mk<R>(c, INV ? sn : -sn);
+}
+
+template <typename R, int N, bool INV>
+__device__ __forceinline__ void dft_reg(cx<R>* a);
+
+// 24-point DFT as 3 x 8 (Cooley-Tukey): n = 3 n1 + n2, k = k1 + 8 k2;
+// X[k1 + 8 k2] = sum_{n2} W3^(n2 k2) W24^(n2 k1) DFT8(x[3 n1 + n2])[k1].
+template <typename R, bool INV>
+__device__ __forceinline__ void dft24(cx<R>* a) {
+  cx<R> y[3][8];
+#pragma unroll
+  for (int n2 = 0; n2 < 3; ++n2)
+#pragma unroll
+    for (int n1 = 0; n1 < 8; ++n1) y[n2][n1] = a[3 * n1 + n2];
+#pragma unroll
+  for (int n2 = 0; n2 < 3; ++n2) dft_reg<R, 8, INV>(y[n2]);
+  const R r3 = (R)0.86602540378443864676;  // sqrt 3 / 2
+#pragma unroll
+  for (int k1 = 0; k1 < 8; ++k1) {
+    const cx<R> p = y[0][k1];
+    const cx<R> q = cmul(y[1][k1], w24<R, INV>(k1));
+    const cx<R> r = cmul(y[2][k1], w24<R, INV>(2 * k1));
+    // 3-point DFT of (p, q, r): W3 = exp(-+2 pi i / 3) = -1/2 -+ i sqrt(3)/2
+    const cx<R> t1 = cadd(q, r), t2 = csub(q, r);
+    const cx<R> m = mk<R>(p.x - (R)0.5 * t1.x, p.y - (R)0.5 * t1.y);
+    const cx<R> sv = INV ? mk<R>(-r3 * t2.y, r3 * t2.x) : mk<R>(r3 * t2.y, -r3 * t2.x);
+    a[k1] = cadd(p, t1);
+    a[k1 + 8] = cadd(m, sv);
+    a[k1 + 16] = csub(m, sv);
+  }
+}
+
+// In-register N-point DFT: N = 2, 4, 8, 16 by radix-2 decimation in time,
+// N = 24 as 3 x 8.
+template <typename R, int N, bool INV>
+__device__ __forceinline__ void dft_reg(cx<R>* a) {
+  if constexpr (N == 24) {
+    dft24<R, INV>(a);
+  } else {
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      const int j = bitrev<N>(i);
+      if (i < j) {
+        cx<R> t = a[i];
+        a[i] = a[j];
+        a[j] = t;
+      }
+    }
+    dit_passes<R, N, 2, INV>(a);
+  }
+}
+
+// Pass S of a Stockham FFT of P points on the vector `buf` (shared memory,
+// padded indexing). With FROM_LOAD the first pass reads element i as ld(i)
+// instead of from buf; with TO_STORE the last pass hands element i to st(i, v)
+// instead of writing buf (in the last pass the output index is j + r Ns, so a
+// vector's consecutive threads store consecutive elements). Every thread of the
+// block calls every pass (they hold __syncthreads).
+template <typename R, int P, int S, bool INV, bool FROM_LOAD, bool TO_STORE, class LD, class ST>
+__device__ __forceinline__ void run_passes(cx<R>* buf, const cx<R>* tw, int tid, LD& ld, ST& st) {
+  constexpr int NST = RadixPlan<P>::NST;
+  constexpr int RAD = PassOf<P, S>::RAD;
+  constexpr int NS = PassOf<P, S>::NS;
+  constexpr int TPV = Shape<P>::TPV;
+  constexpr int NB = P / RAD;
+  constexpr int PER = NB / TPV;
+  constexpr bool first_ld = FROM_LOAD && S == 0;
+  constexpr bool last_st = TO_STORE && S == NST - 1;
+  cx<R> v[PER][RAD];
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int j = tid + q * TPV;
+#pragma unroll
+    for (int r = 0; r < RAD; ++r) {
+      if constexpr (first_ld)
+        v[q][r] = ld(j + r * NB);
+      else
+        v[q][r] = buf[pidx(j + r * NB)];
+    }
+    if constexpr (NS > 1) {
+      const int k = j % NS;
+#pragma unroll
+      for (int r = 1; r < RAD; ++r) {
+        cx<R> w = tw[r * k * (P / (NS * RAD))];  // r k < NS RAD: index < P
+        if (INV) w.y = -w.y;
+        v[q][r] = cmul(v[q][r], w);
+      }
+    }
+    dft_reg<R, RAD, INV>(v[q]);
+  }
+  if constexpr (last_st) {
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int j = tid + q * TPV;  // j < NS in the last pass: base index = j
+#pragma unroll
+      for (int r = 0; r < RAD; ++r) st(j + r * NS, v[q][r]);
+    }
+  } else {
+    if constexpr (!first_ld) __syncthreads();  // in place: every read before any write
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int j = tid + q * TPV;
+      const int k = j % NS;
+      const int base = (j - k) * RAD + k;
+#pragma unroll
+      for (int r = 0; r < RAD; ++r) buf[pidx(base + r * NS)] = v[q][r];
+    }
+    __syncthreads();
+  }
+  if constexpr (S + 1 < NST) run_passes<R, P, S + 1, INV, FROM_LOAD, TO_STORE>(buf, tw, tid, ld, st);
+}
+
+template <typename R>
+struct SmemLoad {  // unused placeholder type for passes that read buf
+  __device__ cx<R> operator()(int) const { return mk<R>(0, 0); }
+};
+template <typename R>
+struct NoStore {
+  __device__ void operator()(int, cx<R>) const {}
+};
+
+template <typename R, int P>
+__device__ __forceinline__ cx<R>* setup_smem(const cx<R>* tw_g, cx<R>** tw_s) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<R>* tw = reinterpret_cast<cx<R>*>(smem_raw);
+  for (int i = threadIdx.x; i < P; i += blockDim.x) tw[i] = tw_g[i];
+  *tw_s = tw;
+  return tw + P;
+}
+
+template <typename R, int P>
+constexpr size_t smem_bytes() {
+  return sizeof(cx<R>) * (size_t)(P + Shape<P>::VPB * Shape<P>::VSTR);
+}
+
+// Compact index of sensor coordinate c on a scan axis (offset o, stride st,
+// n samples), or -1 when c is not a scan position.
+__device__ __forceinline__ int scan_index(int c, int o, int st, int n) {
+  const int d = c - o;
+  if (d < 0 || d % st) return -1;
+  const int i = d / st;
+  return i < n ? i : -1;
+}
+
+// Input of one packed row pair (rows y0, y0 + 1 of a slice, a + i b),
+// zero-padded from nx_in: the plain [ny][nx] slice, or with SAMP the
+// zero-filled image of scan-grid data [my][mx] (the adjoint of the measurement
+// operator, Sec. 3.3). Rows at or past ny_in read as zero.
+template <typename R, bool SAMP>
+struct RowPairLoad {
+  const R* row0;
+  const R* row1;
+  bool ok0, ok1;
+  int nx_in;
+  Samp sm;
+  __device__ __forceinline__ RowPairLoad(const R* base, int y0, int nx, int ny_in, Samp s)
+      : nx_in(nx), sm(s) {
+    if (!SAMP) {
+      ok0 = y0 < ny_in;
+      ok1 = y0 + 1 < ny_in;
+      row0 = base + (int64_t)y0 * nx_in;
+      row1 = row0 + nx_in;
+    } else {
+      const int j0 = y0 < ny_in ? scan_index(y0, sm.oy, sm.sy, sm.my) : -1;
+      const int j1 = y0 + 1 < ny_in ? scan_index(y0 + 1, sm.oy, sm.sy, sm.my) : -1;
+      ok0 = j0 >= 0;
+      ok1 = j1 >= 0;
+      row0 = base + (int64_t)(ok0 ? j0 : 0) * sm.mx;
+      row1 = base + (int64_t)(ok1 ? j1 : 0) * sm.mx;
+    }
+  }
+  __device__ __forceinline__ cx<R> operator()(int x) const {
+    R a = 0, b = 0;
+    if (x < nx_in) {
+      int xi = x;
+      if (SAMP) xi = scan_index(x, sm.ox, sm.sx, sm.mx);
+      if (xi >= 0) {
+        if (ok0) a = row0[xi];
+        if (ok1) b = row1[xi];
+      }
+    }
+    return mk<R>(a, b);
+  }
+};
+
+// Output of one row pair of an image slice from the packed inverse transform
+// (Re -> row y0, Im -> row y0 + 1), columns [0, nx_out) kept; with `sub`,
+// writes image - sub and accumulates its squares (FP64) in acc. With SAMP
+// only the scan positions are kept, written compactly to [my][mx] (the
+// measurement operator of Sec. 3.3); `sub` has that layout. Rows at or past
+// ny_out are not written.
+template <typename R, bool SAMP>
+struct RowPairStore {
+  R* dslice;
+  const R* sslice;
+  int64_t off0, off1;
+  bool ok0, ok1;
+  int nx_out;
+  Samp sm;
+  double acc = 0.0;
+  __device__ __forceinline__ RowPairStore(R* out_slice, const R* sub_slice, int y0, int nx,
+                                          int ny_out, Samp s)
+      : dslice(out_slice), sslice(sub_slice), nx_out(nx), sm(s) {
+    if (!SAMP) {
+      ok0 = y0 < ny_out;
+      ok1 = y0 + 1 < ny_out;
+      off0 = (int64_t)y0 * nx_out;
+      off1 = off0 + nx_out;
+    } else {
+      const int j0 = y0 < ny_out ? scan_index(y0, sm.oy, sm.sy, sm.my) : -1;
+      const int j1 = y0 + 1 < ny_out ? scan_index(y0 + 1, sm.oy, sm.sy, sm.my) : -1;
+      ok0 = j0 >= 0;
+      ok1 = j1 >= 0;
+      off0 = (int64_t)(ok0 ? j0 : 0) * sm.mx;
+      off1 = (int64_t)(ok1 ? j1 : 0) * sm.mx;
+    }
+  }
+  __device__ __forceinline__ void operator()(int x, cx<R> z) {
+    if (x >= nx_out) return;
+    int xi = x;
+    if (SAMP) {
+      xi = scan_index(x, sm.ox, sm.sx, sm.mx);
+      if (xi < 0) return;
+    }
+    if (ok0) {
+      R r0 = z.x;
+      if (sslice) {
+        r0 -= sslice[off0 + xi];
+        acc += (double)r0 * (double)r0;
+      }
+      dslice[off0 + xi] = r0;
+    }
+    if (ok1) {
+      R r1 = z.y;
+      if (sslice) {
+        r1 -= sslice[off1 + xi];
+        acc += (double)r1 * (double)r1;
+      }
+      dslice[off1 + xi] = r1;
+    }
+  }
+};
+
+// Deterministic block sum of acc (warp shuffle tree, then warp 0 over the
+// warps) written by thread 0 to *dst. Every thread of the block calls it.
+__device__ __forceinline__ void block_sum_to(double acc, double* dst) {
+  __shared__ double wsum[kThreads / 32];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double w = threadIdx.x < kThreads / 32 ? wsum[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+    if (threadIdx.x == 0) *dst = w;
+  }
+}
+
+// Row pair (A, B) of half spectra at kx from the transform Z of the packed
+// pair a + i b: A = (Z + conj Zm) / 2, B = (Z - conj Zm) / (2i), Zm = Z[P - kx].
+template <typename R>
+__device__ __forceinline__ void untangle(cx<R> Z, cx<R> Zm, cx<R>* A, cx<R>* B) {
+  *A = mk<R>((R)0.5 * (Z.x + Zm.x), (R)0.5 * (Z.y - Zm.y));
+  *B = mk<R>((R)0.5 * (Z.y + Zm.y), (R)-0.5 * (Z.x - Zm.x));
+}
+
+// Inverse of untangle, written into a packed vector: Z[kx] = A + i B and
+// Z[P - kx] = conj(A) + i conj(B) (A, B the half spectra of two real rows).
+template <typename R, int P>
+__device__ __forceinline__ void pack_pair(cx<R>* b, int kx, cx<R> A, cx<R> B) {
+  b[pidx(kx)] = mk<R>(A.x - B.y, A.y + B.x);
+  if (kx > 0 && kx < P / 2) b[pidx(P - kx)] = mk<R>(A.x + B.y, B.x - A.y);
+}
+
+// Stage i, row pass: rows y0 = 2 pair, y0 + 1 of slice s packed as a + i b,
+// zero-padded from nx_in to P, transformed; half spectra written to
+// T[s][kx][y] for kx in [0, P/2]. With sampling on, the slice is the
+// zero-filled image of scan-grid data in[s][my][mx] (the adjoint of the
+// measurement operator, Sec. 3.3).
+template <typename R, int P, bool SAMP>
+__global__ void __launch_bounds__(kThreads) k_row_r2c(const R* __restrict__ in, int64_t in_stride,
+                                                      int nx_in, int ny_in, cx<R>* __restrict__ T,
+                                                      int tstride, int64_t tslice,
+                                                      const cx<R>* __restrict__ tw_g, Samp sm) {
+  using SH = Shape<P>;
+  cx<R>* tw;
+  cx<R>* bufs = setup_smem<R, P>(tw_g, &tw);
+  const int v = threadIdx.x / SH::TPV, tid = threadIdx.x % SH::TPV;
+  const int64_t s = blockIdx.y;
+  const int pair0 = blockIdx.x * SH::VPB;
+  RowPairLoad<R, SAMP> ld(in + s * in_stride, 2 * (pair0 + v), nx_in, ny_in, sm);
+  pdl_wait();
+  __syncthreads();  // twiddles staged
+  NoStore<R> st;
+  run_passes<R, P, 0, false, true, false>(bufs + v * SH::VSTR, tw, tid, ld, st);
+  cx<R>* dst = T + s * tslice;
+#pragma unroll 4
+  for (int i = threadIdx.x; i < SH::VPB * (P / 2 + 1); i += kThreads) {
+    const int vv = i % SH::VPB, kx = i / SH::VPB;
+    const int yy = 2 * (pair0 + vv);
+    if (yy >= ny_in) continue;
+    cx<R> A, B;
+    untangle(bufs[vv * SH::VSTR + pidx(kx)], bufs[vv * SH::VSTR + pidx((P - kx) % P)], &A,
+             &B);
+    cx<R>* o = dst + (int64_t)kx * tstride + yy;
+    o[0] = A;
+    o[1] = B;  // tstride is even, so yy + 1 < tstride
+  }
+}
+
+// Stage i, column pass: T[s][kx][0..n_in) zero-padded to P, FFT over y,
+// written to out[s][kx][0..P) (slice stride out_stride), or with `slot` to
+// out[s][slot[kx * P + ky]] (the representative-slot layout).
+template <typename R, int P, bool SLOT>
+__global__ void __launch_bounds__(kThreads) k_col_fwd(const cx<R>* __restrict__ T, int tstride,
+                                                      int64_t tslice, int n_in, int ncols,
+                                                      int64_t nvec, cx<R>* __restrict__ out,
+                                                      int64_t out_stride,
+                                                      const cx<R>* __restrict__ tw_g,
+                                                      const int* __restrict__ slot) {
+  using SH = Shape<P>;
+  cx<R>* tw;
+  cx<R>* bufs = setup_smem<R, P>(tw_g, &tw);
+  const int v = threadIdx.x / SH::TPV, tid = threadIdx.x % SH::TPV;
+  const int64_t g = (int64_t)blockIdx.x * SH::VPB + v;
+  const bool ok = g < nvec;
+  const int64_t s = ok ? g / ncols : 0, kx = ok ? g % ncols : 0;
+  const cx<R>* src = T + s * tslice + kx * tstride;
+  cx<R>* dst = out + s * out_stride;
+  const int* sl = SLOT ? slot + kx * P : nullptr;
+  pdl_wait();
+  __syncthreads();
+  auto ld = [&](int y) -> cx<R> { return (ok && y < n_in) ? src[y] : mk<R>(0, 0); };
+  auto st = [&](int y, cx<R> val) {
+    if (ok) dst[SLOT ? __ldg(sl + y) : kx * P + y] = val;
+  };
+  run_passes<R, P, 0, false, true, true>(bufs + v * SH::VSTR, tw, tid, ld, st);
+}
+
+// Stage iii, column pass: in[s][kx][0..P) (or with `slot`, in[s][slot[kx * P +
+// ky]]) inverse FFT over ky, rows [0, n_out) kept (crop) into T[s][kx][y].
+template <typename R, int P, bool SLOT>
+__global__ void __launch_bounds__(kThreads) k_col_inv(const cx<R>* __restrict__ in,
+                                                      int64_t in_stride, int ncols, int64_t nvec,
+                                                      cx<R>* __restrict__ T, int tstride,
+                                                      int64_t tslice, int n_out,
+                                                      const cx<R>* __restrict__ tw_g,
+                                                      const int* __restrict__ slot) {
+  using SH = Shape<P>;
+  cx<R>* tw;
+  cx<R>* bufs = setup_smem<R, P>(tw_g, &tw);
+  const int v = threadIdx.x / SH::TPV, tid = threadIdx.x % SH::TPV;
+  const int64_t g = (int64_t)blockIdx.x * SH::VPB + v;
+  const bool ok = g < nvec;
+  const int64_t s = ok ? g / ncols : 0, kx = ok ? g % ncols : 0;
+  const cx<R>* src = in + s * in_stride;
+  const int* sl = SLOT ? slot + kx * P : nullptr;
+  cx<R>* dst = T + s * tslice + kx * tstride;
+  pdl_wait();
+  __syncthreads();
+  auto ld = [&](int y) -> cx<R> {
+    return ok ? src[SLOT ? __ldg(sl + y) : kx * P + y] : mk<R>(0, 0);
+  };
+  auto st = [&](int y, cx<R> val) {
+    if (ok && y < n_out) dst[y] = val;
+  };
+  run_passes<R, P, 0, true, true, true>(bufs + v * SH::VSTR, tw, tid, ld, st);
+}
+
+// Stage iii row pass, first half: the half spectra A = T[kx][y0], B =
+// T[kx][y0 + 1] of the block's VPB row pairs, packed Hermitian-extended into
+// the work vectors. All global loads first (independent, in flight
+// together), then the packing into shared memory.
+template <typename R, int P>
+__device__ __forceinline__ void load_packed_pairs(const cx<R>* __restrict__ src, int tstride,
+                                                  int pair0, int ny_out, cx<R>* bufs) {
+  using SH = Shape<P>;
+  constexpr int NH = SH::VPB * (P / 2 + 1);
+  constexpr int NIT = (NH + kThreads - 1) / kThreads;
+  constexpr int CH = 4;  // loads in flight per thread (bounded to keep occupancy)
+#pragma unroll
+  for (int c0 = 0; c0 < NIT; c0 += CH) {
+    cx<R> Av[CH], Bv[CH];
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+      const int i = threadIdx.x + (c0 + c) * kThreads;
+      const int vv = i % SH::VPB, kx = i / SH::VPB;
+      const int yy = 2 * (pair0 + vv);
+      Av[c] = mk<R>(0, 0);
+      Bv[c] = mk<R>(0, 0);
+      if (c0 + c < NIT && i < NH && yy < ny_out) {
+        Av[c] = src[(int64_t)kx * tstride + yy];
+        if (yy + 1 < ny_out) Bv[c] = src[(int64_t)kx * tstride + yy + 1];
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+      const int i = threadIdx.x + (c0 + c) * kThreads;
+      if (c0 + c >= NIT || i >= NH) break;
+      const int vv = i % SH::VPB, kx = i / SH::VPB;
+      cx<R> A = Av[c], B = Bv[c];
+      if (kx == 0 || kx == P / 2) {  // spectra of real rows: real at DC and Nyquist
+        A.y = 0;
+        B.y = 0;
+      }
+      pack_pair<R, P>(bufs + vv * SH::VSTR, kx, A, B);
+    }
+  }
+}
+
+// Stage iii, row pass: half spectra A = T[s][kx][y0], B = T[s][kx][y0 + 1]
+// of two real rows, packed as Z = A + iB with the Hermitian extension
+// Z[P - kx] = conj(A) + i conj(B), inverse FFT over x; Re -> row y0,
+// Im -> row y0 + 1, columns [0, nx_out) kept. With `sub`, writes
+// image - sub and accumulates its squares (FP64) per block into partials.
+// With sampling on, only the scan positions are kept, written compactly to
+// out[s][my][mx] (the measurement operator of Sec. 3.3); `sub` has that layout.
+template <typename R, int P, bool SAMP>
+__global__ void __launch_bounds__(kThreads) k_row_c2r(const cx<R>* __restrict__ T, int tstride,
+                                                      int64_t tslice, int nx_out, int ny_out,
+                                                      R* __restrict__ out, int64_t out_stride,
+                                                      const R* __restrict__ sub,
+                                                      double* __restrict__ partials,
+                                                      const cx<R>* __restrict__ tw_g, Samp sm) {
+  using SH = Shape<P>;
+  cx<R>* tw;
+  cx<R>* bufs = setup_smem<R, P>(tw_g, &tw);
+  const int v = threadIdx.x / SH::TPV, tid = threadIdx.x % SH::TPV;
+  const int64_t s = blockIdx.y;
+  const int pair0 = blockIdx.x * SH::VPB;
+  const cx<R>* src = T + s * tslice;
+  pdl_wait();
+  load_packed_pairs<R, P>(src, tstride, pair0, ny_out, bufs);
+  __syncthreads();
+  RowPairStore<R, SAMP> st(out + s * out_stride, sub ? sub + s * out_stride : nullptr,
+                           2 * (pair0 + v), nx_out, ny_out, sm);
+  SmemLoad<R> ld;
+  run_passes<R, P, 0, true, false, true>(bufs + v * SH::VSTR, tw, tid, ld, st);
+  if (partials) block_sum_to(st.acc, partials + (int64_t)blockIdx.y * gridDim.x + blockIdx.x);
+}
+
+// Residual row pass between H and H* (the gradient of Eq. 15): for the
+// block's row pairs of slice s, the inverse row transform as k_row_c2r does
+// it, then r = image - y at the kept (scan) positions and zero elsewhere, its
+// squares summed in FP64 into partials, then the forward row transform of r as
+// k_row_r2c does it, its half spectra written back over the same rows of T
+// (each block reads its rows entirely before writing them). The residual
+// itself never leaves the chip.
+template <typename R, int P, bool SAMP>
+__global__ void __launch_bounds__(kThreads) k_row_resid(cx<R>* __restrict__ T, int tstride,
+                                                        int64_t tslice, int nx, int ny,
+                                                        const R* __restrict__ y,
+                                                        int64_t y_stride,
+                                                        double* __restrict__ partials,
+                                                        const cx<R>* __restrict__ tw_g, Samp sm) {
+  using SH = Shape<P>;
+  cx<R>* tw;
+  cx<R>* bufs = setup_smem<R, P>(tw_g, &tw);
+  const int v = threadIdx.x / SH::TPV, tid = threadIdx.x % SH::TPV;
+  const int64_t s = blockIdx.y;
+  const int pair0 = blockIdx.x * SH::VPB;
+  cx<R>* Ts = T + s * tslice;
+  pdl_wait();
+  load_packed_pairs<R, P>(Ts, tstride, pair0, ny, bufs);
+  __syncthreads();
+  cx<R>* b = bufs + v * SH::VSTR;
+  SmemLoad<R> sl;
+  NoStore<R> ns;
+  run_passes<R, P, 0, true, false, false>(b, tw, tid, sl, ns);  // image rows, natural order
+  // the layout of y: the row pair's offsets (scan rows with sampling on)
+  const int y0 = 2 * (pair0 + v);
+  RowPairStore<R, SAMP> rows(nullptr, y + s * y_stride, y0, nx, ny, sm);
+  double acc = 0.0;
+  for (int x = tid; x < P; x += SH::TPV) {
+    const cx<R> z = b[pidx(x)];
+    R r0 = 0, r1 = 0;
+    int xi = x < nx ? x : -1;
+    if (SAMP && xi >= 0) xi = scan_index(x, sm.ox, sm.sx, sm.mx);
+    if (xi >= 0) {
+      if (rows.ok0) {
+        r0 = z.x - rows.sslice[rows.off0 + xi];
+        acc += (double)r0 * (double)r0;
+      }
+      if (rows.ok1) {
+        r1 = z.y - rows.sslice[rows.off1 + xi];
+        acc += (double)r1 * (double)r1;
+      }
+    }
+    b[pidx(x)] = mk<R>(r0, r1);
+  }
+  __syncthreads();
+  run_passes<R, P, 0, false, false, false>(b, tw, tid, sl, ns);  // spectrum of r0 + i r1
+#pragma unroll 4
+  for (int i = threadIdx.x; i < SH::VPB * (P / 2 + 1); i += kThreads) {
+    const int vv = i % SH::VPB, kx = i / SH::VPB;
+    const int yy = 2 * (pair0 + vv);
+    if (yy >= ny) continue;
+    cx<R> A, B;
+    untangle(bufs[vv * SH::VSTR + pidx(kx)], bufs[vv * SH::VSTR + pidx((P - kx) % P)], &A,
+             &B);
+    cx<R>* o = Ts + (int64_t)kx * tstride + yy;
+    o[0] = A;
+    o[1] = B;  // tstride is even, so yy + 1 < tstride
+  }
+  if (partials) block_sum_to(acc, partials + (int64_t)blockIdx.y * gridDim.x + blockIdx.x);
+}
+
+// Stage iii row pass over the depth slices with the FISTA step (Eq. 14-15)
+// in place of the gradient store: each gradient value g of the kept columns
+// updates y (momentum point) and xprev (x_{k-1}) of its voxel in place; the
+// last block to finish advances the iteration (see FistaStep).
+template <typename R, int P>
+__global__ void __launch_bounds__(kThreads) k_row_c2r_step(
+    const cx<R>* __restrict__ T, int tstride, int64_t tslice, int nx, int ny, int64_t plane,
+    R* __restrict__ yv, R* __restrict__ xprev, const double* __restrict__ scal,
+    const double* __restrict__ betas, int* __restrict__ iter, const double* __restrict__ r2_cur,
+    double* __restrict__ r2_hist, int cap, unsigned* __restrict__ done,
+    const cx<R>* __restrict__ tw_g) {
+  using SH = Shape<P>;
+  cx<R>* tw;
+  cx<R>* bufs = setup_smem<R, P>(tw_g, &tw);
+  const int v = threadIdx.x / SH::TPV, tid = threadIdx.x % SH::TPV;
+  const int64_t s = blockIdx.y;
+  const int pair0 = blockIdx.x * SH::VPB;
+  pdl_wait();
+  const R invL = (R)scal[0], lamL = (R)scal[1];
+  const int k = *iter;
+  const R beta = (R)betas[k];
+  load_packed_pairs<R, P>(T + s * tslice, tstride, pair0, ny, bufs);
+  __syncthreads();
+  const int y0 = 2 * (pair0 + v);
+  const bool ok0 = y0 < ny, ok1 = y0 + 1 < ny;
+  R* ys = yv + s * plane + (int64_t)y0 * nx;
+  R* xs = xprev + s * plane + (int64_t)y0 * nx;
+  auto upd = [&](int64_t i, R g) {
+    const R ya = ys[i], xp = xs[i];
+    R x = ya - g * invL - lamL;
+    x = x > (R)0 ? x : (R)0;
+    ys[i] = x + beta * (x - xp);
+    xs[i] = x;
+  };
+  auto st = [&](int x, cx<R> z) {
+    if (x >= nx) return;
+    if (ok0) upd(x, z.x);
+    if (ok1) upd((int64_t)nx + x, z.y);
+  };
+  SmemLoad<R> ld;
+  run_passes<R, P, 0, true, false, true>(bufs + v * SH::VSTR, tw, tid, ld, st);
+  __shared__ bool last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(done, 1u) == gridDim.x * gridDim.y - 1;
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    if (k < cap) r2_hist[k] = *r2_cur;
+    *iter = k + 1;
+    *done = 0;
+  }
+}
+
+template <typename R, int P>
+cudaError_t set_smem_attr(const void* fn) {
+  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)smem_bytes<R, P>());
+}
+}  // namespace
+
+// ---- launchers, one per stage and length ---------------------------------------
+template <typename R, int P>
+cudaError_t FftLen<R, P>::row_r2c(const R* in, int64_t in_stride, int nx_in, int ny_in, cx<R>* T, int tstride,
+                                  int64_t tslice, int S, const cx<R>* tw, cudaStream_t st, Samp sm) {
+  using SH = Shape<P>;
+  auto fn = sm.on ? k_row_r2c<R, P, true> : k_row_r2c<R, P, false>;
+  cudaError_t e = set_smem_attr<R, P>((const void*)fn);
+  if (e != cudaSuccess) return e;
+  const int pairs = (ny_in + 1) / 2;
+  dim3 grid((pairs + SH::VPB - 1) / SH::VPB, S);
+  return launch_pdl(fn, grid, dim3(kThreads), smem_bytes<R, P>(), st, in, in_stride, nx_in, ny_in,
+                    T, tstride, tslice, tw, sm);
+}
+
+template <typename R, int P>
+cudaError_t FftLen<R, P>::col_fwd(const cx<R>* T, int tstride, int64_t tslice, int n_in, int ncols, int S,
+                                  cx<R>* out, int64_t out_stride, const cx<R>* tw, cudaStream_t st,
+                                  const int* slot) {
+  using SH = Shape<P>;
+  auto fn = slot ? k_col_fwd<R, P, true> : k_col_fwd<R, P, false>;
+  cudaError_t e = set_smem_attr<R, P>((const void*)fn);
+  if (e != cudaSuccess) return e;
+  const int64_t nvec = (int64_t)S * ncols;
+  const int64_t blocks = (nvec + SH::VPB - 1) / SH::VPB;
+  return launch_pdl(fn, dim3((unsigned)blocks), dim3(kThreads), smem_bytes<R, P>(), st,
+                    T, tstride, tslice, n_in, ncols, nvec, out, out_stride, tw, slot);
+}
+
+template <typename R, int P>
+cudaError_t FftLen<R, P>::col_inv(const cx<R>* in, int64_t in_stride, int ncols, int S, cx<R>* T, int tstride,
+                                  int64_t tslice, int n_out, const cx<R>* tw, cudaStream_t st, const int* slot) {
+  using SH = Shape<P>;
+  auto fn = slot ? k_col_inv<R, P, true> : k_col_inv<R, P, false>;
+  cudaError_t e = set_smem_attr<R, P>((const void*)fn);
+  if (e != cudaSuccess) return e;
+  const int64_t nvec = (int64_t)S * ncols;
+  const int64_t blocks = (nvec + SH::VPB - 1) / SH::VPB;
+  return launch_pdl(fn, dim3((unsigned)blocks), dim3(kThreads), smem_bytes<R, P>(), st,
+                    in, in_stride, ncols, nvec, T, tstride, tslice, n_out, tw, slot);
+}
+
+template <typename R, int P>
+cudaError_t FftLen<R, P>::row_c2r(const cx<R>* T, int tstride, int64_t tslice, int nx_out, int ny_out, R* out,
+                                  int64_t out_stride, int S, const R* sub, double* partials, const cx<R>* tw,
+                                  cudaStream_t st, int* nblocks, Samp sm) {
+  using SH = Shape<P>;
+  auto fn = sm.on ? k_row_c2r<R, P, true> : k_row_c2r<R, P, false>;
+  cudaError_t e = set_smem_attr<R, P>((const void*)fn);
+  if (e != cudaSuccess) return e;
+  const int pairs = (ny_out + 1) / 2;
+  dim3 grid((pairs + SH::VPB - 1) / SH::VPB, S);
+  *nblocks = (int)(grid.x * grid.y);
+  return launch_pdl(fn, grid, dim3(kThreads), smem_bytes<R, P>(), st, T, tstride, tslice, nx_out,
+                    ny_out, out, out_stride, sub, partials, tw, sm);
+}
+
+template <typename R, int P>
+cudaError_t FftLen<R, P>::row_resid(cx<R>* T, int tstride, int64_t tslice, int nx, int ny, const R* y,
+                                    int64_t y_stride, int S, double* partials, const cx<R>* tw, cudaStream_t st,
+                                    int* nblocks, Samp sm) {
+  using SH = Shape<P>;
+  auto fn = sm.on ? k_row_resid<R, P, true> : k_row_resid<R, P, false>;
+  cudaError_t e = set_smem_attr<R, P>((const void*)fn);
+  if (e != cudaSuccess) return e;
+  const int pairs = (ny + 1) / 2;
+  dim3 grid((pairs + SH::VPB - 1) / SH::VPB, S);
+  *nblocks = (int)(grid.x * grid.y);
+  return launch_pdl(fn, grid, dim3(kThreads), smem_bytes<R, P>(), st, T, tstride, tslice, nx, ny, y,
+                    y_stride, partials, tw, sm);
+}
+
+template <typename R, int P>
+cudaError_t FftLen<R, P>::row_c2r_step(const cx<R>* T, int tstride, int64_t tslice, int nx, int ny,
+                                       int64_t plane, int S, const FistaStep& f, const cx<R>* tw,
+                                       cudaStream_t st) {
+  using SH = Shape<P>;
+  cudaError_t e = set_smem_attr<R, P>((const void*)k_row_c2r_step<R, P>);
+  if (e != cudaSuccess) return e;
+  const int pairs = (ny + 1) / 2;
+  dim3 grid((pairs + SH::VPB - 1) / SH::VPB, S);
+  return launch_pdl(k_row_c2r_step<R, P>, grid, dim3(kThreads), smem_bytes<R, P>(), st, T, tstride,
+                    tslice, nx, ny, plane, static_cast<R*>(f.y), static_cast<R*>(f.xprev), f.scal,
+                    f.betas, f.iter, f.r2_cur, f.r2_hist, f.cap, f.done, tw);
+}
+
+// Explicit instantiation of every launcher for one (precision, length).
+#define PAT_FFT_INSTANTIATE(R, P) template struct FftLen<R, P>;
+
+}  // namespace pat

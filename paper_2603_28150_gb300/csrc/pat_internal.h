@@ -12,6 +12,14 @@
 
 namespace pat {
 
+// Transverse transform lengths the FFT stages support: 2^k or 3 * 2^k in
+// [16, 1024].
+inline bool fft_len_ok(int v) {
+  if (v < 16 || v > 1024) return false;
+  if (v % 3 == 0) v /= 3;
+  return (v & (v - 1)) == 0;
+}
+
 // ----------------------------------------------------------------------------
 // Complex numbers in registers / memory: (x = re, y = im), 8 or 16 bytes.
 // ----------------------------------------------------------------------------

@@ -37,10 +37,10 @@ def test_argument_errors_without_gpu():
     L = pat.lib()
     out = ctypes.c_void_p(0)
     assert L.pat_plan_create(None, None, 0, None, ctypes.byref(out)) == pat.PAT_ERR_ARG
-    g = pat.Geometry(32, 32, 4, 8, 48, 64, 1, 0)  # px not a power of two
+    g = pat.Geometry(32, 32, 4, 8, 80, 64, 1, 0)  # px = 80: neither 2^k nor 3 * 2^k
     buf = (ctypes.c_double * 4)()
     assert L.pat_plan_create(ctypes.byref(g), buf, 0, None, ctypes.byref(out)) == pat.PAT_ERR_UNSUPPORTED
-    assert b"power" in L.pat_last_error()
+    assert b"3*2^k" in L.pat_last_error()
     g = pat.Geometry(40, 32, 4, 8, 64, 64, 1, 0)  # 64 < 2*40-1: circular aliasing
     assert L.pat_plan_create(ctypes.byref(g), buf, 0, None, ctypes.byref(out)) == pat.PAT_ERR_ARG
     g = pat.Geometry(8, 8, 4, 8, 16, 16, 0, 0)  # max_batch 0

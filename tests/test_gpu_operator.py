@@ -17,6 +17,8 @@ CFG1 = oracle.Grid.square(32, 16, 64)            # 32^2 -> 64^2, 16 depths, 64 s
 RAGGED = oracle.Grid(nx=23, ny=17, nz=5, nt=9, px=64, py=64)   # odd sizes, several k-blocks
 RECT = oracle.Grid(nx=20, ny=9, nz=3, nt=7, px=64, py=32)      # px != py
 SMALLP = oracle.Grid(nx=5, ny=6, nz=3, nt=4, px=16, py=16)     # K = 9*16: ragged last k-block
+P48 = oracle.Grid(nx=20, ny=17, nz=4, nt=9, px=48, py=48)      # 3 * 2^k transforms
+RECT3 = oracle.Grid(nx=11, ny=40, nz=3, nt=5, px=24, py=96)    # 3 * 2^k, px != py
 
 
 def _tables(g, kind, seed=0):
@@ -38,7 +40,8 @@ def _ref_ops(h, g):
     return (lambda x: oracle.forward_fft(Hf, x, g)), (lambda y: oracle.adjoint_fft(Hf, y, g))
 
 
-@pytest.mark.parametrize("g", [CFG1, RAGGED, RECT, SMALLP], ids=["cfg1", "ragged", "rect", "p16"])
+@pytest.mark.parametrize("g", [CFG1, RAGGED, RECT, SMALLP, P48, RECT3],
+                         ids=["cfg1", "ragged", "rect", "p16", "p48", "rect24x96"])
 @pytest.mark.parametrize("kind", ["random", "even", "d4", "kspace"])
 @pytest.mark.parametrize("fp64", [False, True])
 def test_forward_and_adjoint_match_oracle(g, kind, fp64):
@@ -74,8 +77,9 @@ def test_forced_complex_equals_real_path(fp64):
     assert oracle.rel_l2(dr, dc) < (1e-13 if fp64 else 1e-6)
 
 
-@pytest.mark.parametrize("g", [CFG1, oracle.Grid.square(48, 12, 40), SMALLP],
-                         ids=["cfg1", "n48", "p16"])
+@pytest.mark.parametrize("g", [CFG1, oracle.Grid.square(48, 12, 40), SMALLP,
+                               oracle.Grid.square(40, 12, 20, pad=96)],
+                         ids=["cfg1", "n48", "p16", "p96"])
 @pytest.mark.parametrize("B", [1, 3])
 def test_folded_equals_unfolded(g, B):
     """One table row per representative {|kx|, |ky|} gives what one row per bin gives."""
@@ -300,6 +304,34 @@ def test_cfg2_sampled_outputs_full_size():
     y = synth.gaussian_field((g.nt, g.ny, g.nx), 1)
     a = host(plan.adjoint(cuda(y)))
     for j in (0, 63):
+        Hf = oracle.table_kspace_closed(g, med, mz, z_idx=[j])
+        gz = oracle.Grid(g.nx, g.ny, 1, g.nt, g.px, g.py)
+        ref = oracle.adjoint_fft(Hf, y, gz)[0]
+        assert oracle.rel_l2(a[j], ref) < 1e-5, j
+
+
+def test_three_times_power_of_two_sampled_outputs():
+    """96^2 -> 192^2 (a 3 * 2^k padded grid), 32 depths, 128 samples, table
+    generated on the device: sampled time samples of H rho and depths of H* d
+    against the oracle's closed-form library for those samples (the oracle's
+    192-point transforms are DFTs of the definition, so the grid stays modest;
+    the stage tests cover 384 and 768 against numpy's FFT)."""
+    g = oracle.Grid.square(96, 32, 128, pad=192)
+    med = MED_50UM
+    mz = oracle.mz_for(g.nz, g.nt, med)
+    plan = Plan(g.nx, g.ny, g.nz, g.nt, g.px, g.py,
+                medium=Medium(med.c, med.dx, med.dy, med.dz, med.dt, mz, 1))
+    assert plan.info()["folded"] == 1
+    rho = synth.vessel_phantom(g.nx, g.nz, seed=2)
+    d = host(plan.forward(cuda(rho)))
+    for t in (0, 77, 127):
+        Hf = oracle.table_kspace_closed(g, med, mz, t_idx=[t])
+        gt = oracle.Grid(g.nx, g.ny, g.nz, 1, g.px, g.py)
+        ref = oracle.forward_fft(Hf, rho, gt)[0]
+        assert np.abs(d[t] - ref).max() < 1e-5 * np.abs(d).max(), t
+    y = synth.gaussian_field((g.nt, g.ny, g.nx), 4)
+    a = host(plan.adjoint(cuda(y)))
+    for j in (0, 31):
         Hf = oracle.table_kspace_closed(g, med, mz, z_idx=[j])
         gz = oracle.Grid(g.nx, g.ny, 1, g.nt, g.px, g.py)
         ref = oracle.adjoint_fft(Hf, y, gz)[0]

@@ -9,12 +9,16 @@ from tests.helpers import cuda, host
 
 pytestmark = pytest.mark.gpu
 
-# (nx, ny, px, py): every supported transform length, odd/ragged sizes (odd
-# row counts, a single row), non-square.
+# (nx, ny, px, py): every supported transform length (2^k and 3 * 2^k),
+# odd/ragged sizes (odd row counts, a single row), non-square.
 GRIDS = [(5, 7, 16, 16), (16, 16, 32, 32), (32, 32, 64, 64), (64, 50, 128, 128),
          (128, 128, 256, 256), (100, 60, 256, 128), (256, 256, 512, 512), (17, 3, 1024, 16),
          (512, 400, 1024, 1024), (29, 31, 64, 64), (45, 13, 128, 128), (101, 77, 256, 256),
-         (3, 1, 256, 256), (200, 133, 512, 512)]
+         (3, 1, 256, 256), (200, 133, 512, 512),
+         # 3 * 2^k lengths (a 24-point first pass), square, mixed with 2^k, ragged
+         (12, 12, 24, 24), (20, 17, 48, 48), (48, 33, 96, 96), (96, 90, 192, 192),
+         (150, 101, 384, 384), (384, 300, 768, 768), (11, 40, 24, 96), (100, 60, 256, 192),
+         (30, 9, 768, 32)]
 
 
 def _plan(nx, ny, px, py, nslices, fp64=False):
@@ -59,3 +63,19 @@ def test_spectrum_then_image_round_trip():
     plan = _plan(nx, ny, px, py, 4)
     back = host(plan.stage_image(plan.stage_spectrum(cuda(x)))) / (px * py)
     assert np.abs(back - x).max() < 2e-6 * np.abs(x).max()
+
+
+@pytest.mark.parametrize("px,py", [(48, 48), (96, 384)])
+def test_round_trip_three_times_power_of_two(px, py):
+    nx, ny = px // 2, py // 2
+    x = synth.gaussian_field((3, ny, nx), seed=px)
+    plan = _plan(nx, ny, px, py, 3)
+    back = host(plan.stage_image(plan.stage_spectrum(cuda(x)))) / (px * py)
+    assert np.abs(back - x).max() < 2e-6 * np.abs(x).max()
+
+
+@pytest.mark.parametrize("p", [20, 40, 1536, 2048, 12])
+def test_unsupported_lengths_rejected(p):
+    from paper_2603_28150_gb300 import PatError
+    with pytest.raises(PatError):
+        _plan(5, 5, p, 16, 1)
