@@ -411,6 +411,29 @@ __device__ __forceinline__ void untangle(cx<R> Z, cx<R> Zm, cx<R>* A, cx<R>* B) 
   *B = mk<R>((R)0.5 * (Z.y + Zm.y), (R)-0.5 * (Z.x - Zm.x));
 }
 
+// Adjacent pair T[kx][y], T[kx][y + 1] (y even, row stride even, so the
+// pair is 16-byte aligned in FP32) as one vector access.
+template <typename R>
+__device__ __forceinline__ void load_pair(const cx<R>* p, cx<R>* a, cx<R>* b) {
+  if constexpr (sizeof(R) == 4) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    *a = mk<R>(v.x, v.y);
+    *b = mk<R>(v.z, v.w);
+  } else {
+    *a = p[0];
+    *b = p[1];
+  }
+}
+template <typename R>
+__device__ __forceinline__ void store_pair(cx<R>* p, cx<R> a, cx<R> b) {
+  if constexpr (sizeof(R) == 4) {
+    *reinterpret_cast<float4*>(p) = make_float4(a.x, a.y, b.x, b.y);
+  } else {
+    p[0] = a;
+    p[1] = b;
+  }
+}
+
 // Inverse of untangle, written into a packed vector: Z[kx] = A + i B and
 // Z[P - kx] = conj(A) + i conj(B) (A, B the half spectra of two real rows).
 template <typename R, int P>
@@ -449,9 +472,7 @@ __global__ void __launch_bounds__(kThreads) k_row_r2c(const R* __restrict__ in, 
     cx<R> A, B;
     untangle(bufs[vv * SH::VSTR + pidx(kx)], bufs[vv * SH::VSTR + pidx((P - kx) % P)], &A,
              &B);
-    cx<R>* o = dst + (int64_t)kx * tstride + yy;
-    o[0] = A;
-    o[1] = B;  // tstride is even, so yy + 1 < tstride
+    store_pair(dst + (int64_t)kx * tstride + yy, A, B);  // tstride even: yy + 1 < tstride
   }
 }
 
@@ -524,7 +545,8 @@ __device__ __forceinline__ void load_packed_pairs(const cx<R>* __restrict__ src,
   using SH = Shape<P>;
   constexpr int NH = SH::VPB * (P / 2 + 1);
   constexpr int NIT = (NH + kThreads - 1) / kThreads;
-  constexpr int CH = 4;  // loads in flight per thread (bounded to keep occupancy)
+  // loads in flight per thread: all of them in FP32 (one 16-byte load per pair)
+  constexpr int CH = sizeof(R) == 4 ? (NIT <= 13 ? NIT : 8) : 4;
 #pragma unroll
   for (int c0 = 0; c0 < NIT; c0 += CH) {
     cx<R> Av[CH], Bv[CH];
@@ -536,8 +558,9 @@ __device__ __forceinline__ void load_packed_pairs(const cx<R>* __restrict__ src,
       Av[c] = mk<R>(0, 0);
       Bv[c] = mk<R>(0, 0);
       if (c0 + c < NIT && i < NH && yy < ny_out) {
-        Av[c] = src[(int64_t)kx * tstride + yy];
-        if (yy + 1 < ny_out) Bv[c] = src[(int64_t)kx * tstride + yy + 1];
+        // the pair's second element exists even for odd ny_out (row stride even)
+        load_pair(src + (int64_t)kx * tstride + yy, &Av[c], &Bv[c]);
+        if (yy + 1 >= ny_out) Bv[c] = mk<R>(0, 0);
       }
     }
 #pragma unroll
@@ -645,9 +668,7 @@ __global__ void __launch_bounds__(kThreads) k_row_resid(cx<R>* __restrict__ T, i
     cx<R> A, B;
     untangle(bufs[vv * SH::VSTR + pidx(kx)], bufs[vv * SH::VSTR + pidx((P - kx) % P)], &A,
              &B);
-    cx<R>* o = Ts + (int64_t)kx * tstride + yy;
-    o[0] = A;
-    o[1] = B;  // tstride is even, so yy + 1 < tstride
+    store_pair(Ts + (int64_t)kx * tstride + yy, A, B);  // tstride even: yy + 1 < tstride
   }
   if (partials) block_sum_to(acc, partials + (int64_t)blockIdx.y * gridDim.x + blockIdx.x);
 }
