@@ -102,8 +102,9 @@ __host__ __device__ constexpr int bitrev(int i) {
 }
 
 // Butterfly passes of span LEN, 2 LEN, ..., N (compile-time recursion keeps
-// every register index constant).
-template <typename R, int N, int LEN, bool INV>
+// every register index constant). With HOUT only outputs [0, N/2) are needed,
+// so the last pass forms only the sums.
+template <typename R, int N, int LEN, bool INV, bool HOUT = false>
 __device__ __forceinline__ void dit_passes(cx<R>* a) {
 #pragma unroll
   for (int i = 0; i < N; i += LEN) {
@@ -112,10 +113,10 @@ __device__ __forceinline__ void dit_passes(cx<R>* a) {
       cx<R> u = a[i + k];
       cx<R> t = mul_w16<R, INV>(a[i + k + LEN / 2], k * (16 / LEN));
       a[i + k] = cadd(u, t);
-      a[i + k + LEN / 2] = csub(u, t);
+      if (!(HOUT && LEN == N)) a[i + k + LEN / 2] = csub(u, t);
     }
   }
-  if constexpr (LEN < N) dit_passes<R, N, 2 * LEN, INV>(a);
+  if constexpr (LEN < N) dit_passes<R, N, 2 * LEN, INV, HOUT>(a);
 }
 
 // exp(-2 pi i m / 24) for m in [0, 15) (conjugated for the inverse), from
@@ -148,12 +149,13 @@ __device__ __forceinline__ cx<R> w24(int m) {
   return mk<R>(c, INV ? sn : -sn);
 }
 
-template <typename R, int N, bool INV>
+template <typename R, int N, bool INV, bool ZIN = false, bool HOUT = false>
 __device__ __forceinline__ void dft_reg(cx<R>* a);
 
 // 24-point DFT as 3 x 8 (Cooley-Tukey): n = 3 n1 + n2, k = k1 + 8 k2;
 // X[k1 + 8 k2] = sum_{n2} W3^(n2 k2) W24^(n2 k1) DFT8(x[3 n1 + n2])[k1].
-template <typename R, bool INV>
+// With ZIN (inputs [12, 24) zero) each DFT8 has its upper half zero.
+template <typename R, bool INV, bool ZIN = false>
 __device__ __forceinline__ void dft24(cx<R>* a) {
   cx<R> y[3][8];
 #pragma unroll
@@ -161,7 +163,7 @@ __device__ __forceinline__ void dft24(cx<R>* a) {
 #pragma unroll
     for (int n1 = 0; n1 < 8; ++n1) y[n2][n1] = a[3 * n1 + n2];
 #pragma unroll
-  for (int n2 = 0; n2 < 3; ++n2) dft_reg<R, 8, INV>(y[n2]);
+  for (int n2 = 0; n2 < 3; ++n2) dft_reg<R, 8, INV, ZIN>(y[n2]);
   const R r3 = (R)0.86602540378443864676;  // sqrt 3 / 2
 #pragma unroll
   for (int k1 = 0; k1 < 8; ++k1) {
@@ -179,11 +181,13 @@ __device__ __forceinline__ void dft24(cx<R>* a) {
 }
 
 // In-register N-point DFT: N = 2, 4, 8, 16 by radix-2 decimation in time,
-// N = 24 as 3 x 8.
-template <typename R, int N, bool INV>
+// N = 24 as 3 x 8. ZIN: inputs [N/2, N) are zero (zero padding), so after
+// the bit reversal every odd slot is zero and the span-2 pass is a copy.
+// HOUT: only outputs [0, N/2) are used (crop); ignored for N = 24.
+template <typename R, int N, bool INV, bool ZIN, bool HOUT>
 __device__ __forceinline__ void dft_reg(cx<R>* a) {
   if constexpr (N == 24) {
-    dft24<R, INV>(a);
+    dft24<R, INV, ZIN>(a);
   } else {
 #pragma unroll
     for (int i = 0; i < N; ++i) {
@@ -194,7 +198,15 @@ __device__ __forceinline__ void dft_reg(cx<R>* a) {
         a[j] = t;
       }
     }
-    dit_passes<R, N, 2, INV>(a);
+    if constexpr (ZIN && N > 2) {
+#pragma unroll
+      for (int i = 0; i < N; i += 2) a[i + 1] = a[i];
+      dit_passes<R, N, 4, INV, HOUT>(a);
+    } else if constexpr (ZIN) {
+      a[1] = a[0];
+    } else {
+      dit_passes<R, N, 2, INV, HOUT>(a);
+    }
   }
 }
 
@@ -204,7 +216,15 @@ __device__ __forceinline__ void dft_reg(cx<R>* a) {
 // instead of writing buf (in the last pass the output index is j + r Ns, so a
 // vector's consecutive threads store consecutive elements). Every thread of the
 // block calls every pass (they hold __syncthreads).
-template <typename R, int P, int S, bool INV, bool FROM_LOAD, bool TO_STORE, class LD, class ST>
+//
+// ZIN: elements [P/2, P) of the input are zero (the zero padding of a slice of
+// at most P/2 rows or columns): the first pass, whose element r is
+// j + r P/RAD, neither reads nor adds its upper RAD/2 elements. HOUT: only
+// outputs [0, P/2) are used (the crop): the last pass, whose element r is
+// j + r P/RAD, neither forms nor writes its upper RAD/2 outputs (with a
+// shared-memory last pass those slots keep stale values).
+template <typename R, int P, int S, bool INV, bool FROM_LOAD, bool TO_STORE, bool ZIN = false,
+          bool HOUT = false, class LD, class ST>
 __device__ __forceinline__ void run_passes(cx<R>* buf, const cx<R>* tw, int tid, LD& ld, ST& st) {
   constexpr int NST = RadixPlan<P>::NST;
   constexpr int RAD = PassOf<P, S>::RAD;
@@ -214,13 +234,19 @@ __device__ __forceinline__ void run_passes(cx<R>* buf, const cx<R>* tw, int tid,
   constexpr int PER = NB / TPV;
   constexpr bool first_ld = FROM_LOAD && S == 0;
   constexpr bool last_st = TO_STORE && S == NST - 1;
+  constexpr bool zin = ZIN && S == 0;
+  constexpr bool hout = HOUT && S == NST - 1;
+  constexpr int RIN = zin ? RAD / 2 : RAD;    // elements read
+  constexpr int ROUT = hout ? RAD / 2 : RAD;  // outputs kept
   cx<R> v[PER][RAD];
 #pragma unroll
   for (int q = 0; q < PER; ++q) {
     const int j = tid + q * TPV;
 #pragma unroll
     for (int r = 0; r < RAD; ++r) {
-      if constexpr (first_ld)
+      if (r >= RIN)
+        v[q][r] = mk<R>(0, 0);
+      else if constexpr (first_ld)
         v[q][r] = ld(j + r * NB);
       else
         v[q][r] = buf[pidx(j + r * NB)];
@@ -234,14 +260,14 @@ __device__ __forceinline__ void run_passes(cx<R>* buf, const cx<R>* tw, int tid,
         v[q][r] = cmul(v[q][r], w);
       }
     }
-    dft_reg<R, RAD, INV>(v[q]);
+    dft_reg<R, RAD, INV, zin, hout>(v[q]);
   }
   if constexpr (last_st) {
 #pragma unroll
     for (int q = 0; q < PER; ++q) {
       const int j = tid + q * TPV;  // j < NS in the last pass: base index = j
 #pragma unroll
-      for (int r = 0; r < RAD; ++r) st(j + r * NS, v[q][r]);
+      for (int r = 0; r < ROUT; ++r) st(j + r * NS, v[q][r]);
     }
   } else {
     if constexpr (!first_ld) __syncthreads();  // in place: every read before any write
@@ -251,11 +277,12 @@ __device__ __forceinline__ void run_passes(cx<R>* buf, const cx<R>* tw, int tid,
       const int k = j % NS;
       const int base = (j - k) * RAD + k;
 #pragma unroll
-      for (int r = 0; r < RAD; ++r) buf[pidx(base + r * NS)] = v[q][r];
+      for (int r = 0; r < ROUT; ++r) buf[pidx(base + r * NS)] = v[q][r];
     }
     __syncthreads();
   }
-  if constexpr (S + 1 < NST) run_passes<R, P, S + 1, INV, FROM_LOAD, TO_STORE>(buf, tw, tid, ld, st);
+  if constexpr (S + 1 < NST)
+    run_passes<R, P, S + 1, INV, FROM_LOAD, TO_STORE, ZIN, HOUT>(buf, tw, tid, ld, st);
 }
 
 template <typename R>
@@ -447,7 +474,7 @@ __device__ __forceinline__ void pack_pair(cx<R>* b, int kx, cx<R> A, cx<R> B) {
 // T[s][kx][y] for kx in [0, P/2]. With sampling on, the slice is the
 // zero-filled image of scan-grid data in[s][my][mx] (the adjoint of the
 // measurement operator, Sec. 3.3).
-template <typename R, int P, bool SAMP>
+template <typename R, int P, bool SAMP, bool ZIN>
 __global__ void __launch_bounds__(kThreads) k_row_r2c(const R* __restrict__ in, int64_t in_stride,
                                                       int nx_in, int ny_in, cx<R>* __restrict__ T,
                                                       int tstride, int64_t tslice,
@@ -462,7 +489,7 @@ __global__ void __launch_bounds__(kThreads) k_row_r2c(const R* __restrict__ in, 
   pdl_wait();
   __syncthreads();  // twiddles staged
   NoStore<R> st;
-  run_passes<R, P, 0, false, true, false>(bufs + v * SH::VSTR, tw, tid, ld, st);
+  run_passes<R, P, 0, false, true, false, ZIN>(bufs + v * SH::VSTR, tw, tid, ld, st);
   cx<R>* dst = T + s * tslice;
 #pragma unroll 4
   for (int i = threadIdx.x; i < SH::VPB * (P / 2 + 1); i += kThreads) {
@@ -479,7 +506,7 @@ __global__ void __launch_bounds__(kThreads) k_row_r2c(const R* __restrict__ in, 
 // Stage i, column pass: T[s][kx][0..n_in) zero-padded to P, FFT over y,
 // written to out[s][kx][0..P) (slice stride out_stride), or with `slot` to
 // out[s][slot[kx * P + ky]] (the representative-slot layout).
-template <typename R, int P, bool SLOT>
+template <typename R, int P, bool SLOT, bool ZIN>
 __global__ void __launch_bounds__(kThreads) k_col_fwd(const cx<R>* __restrict__ T, int tstride,
                                                       int64_t tslice, int n_in, int ncols,
                                                       int64_t nvec, cx<R>* __restrict__ out,
@@ -492,7 +519,9 @@ __global__ void __launch_bounds__(kThreads) k_col_fwd(const cx<R>* __restrict__ 
   const int v = threadIdx.x / SH::TPV, tid = threadIdx.x % SH::TPV;
   const int64_t g = (int64_t)blockIdx.x * SH::VPB + v;
   const bool ok = g < nvec;
-  const int64_t s = ok ? g / ncols : 0, kx = ok ? g % ncols : 0;
+  // 32-bit quotient (nvec = slices x columns < 2^31): no 64-bit division
+  const unsigned gq = ok ? (unsigned)g / (unsigned)ncols : 0u;
+  const int64_t s = gq, kx = ok ? (int64_t)((unsigned)g - gq * (unsigned)ncols) : 0;
   const cx<R>* src = T + s * tslice + kx * tstride;
   cx<R>* dst = out + s * out_stride;
   const int* sl = SLOT ? slot + kx * P : nullptr;
@@ -502,12 +531,12 @@ __global__ void __launch_bounds__(kThreads) k_col_fwd(const cx<R>* __restrict__ 
   auto st = [&](int y, cx<R> val) {
     if (ok) dst[SLOT ? __ldg(sl + y) : kx * P + y] = val;
   };
-  run_passes<R, P, 0, false, true, true>(bufs + v * SH::VSTR, tw, tid, ld, st);
+  run_passes<R, P, 0, false, true, true, ZIN>(bufs + v * SH::VSTR, tw, tid, ld, st);
 }
 
 // Stage iii, column pass: in[s][kx][0..P) (or with `slot`, in[s][slot[kx * P +
 // ky]]) inverse FFT over ky, rows [0, n_out) kept (crop) into T[s][kx][y].
-template <typename R, int P, bool SLOT>
+template <typename R, int P, bool SLOT, bool HOUT>
 __global__ void __launch_bounds__(kThreads) k_col_inv(const cx<R>* __restrict__ in,
                                                       int64_t in_stride, int ncols, int64_t nvec,
                                                       cx<R>* __restrict__ T, int tstride,
@@ -520,7 +549,9 @@ __global__ void __launch_bounds__(kThreads) k_col_inv(const cx<R>* __restrict__ 
   const int v = threadIdx.x / SH::TPV, tid = threadIdx.x % SH::TPV;
   const int64_t g = (int64_t)blockIdx.x * SH::VPB + v;
   const bool ok = g < nvec;
-  const int64_t s = ok ? g / ncols : 0, kx = ok ? g % ncols : 0;
+  // 32-bit quotient (nvec = slices x columns < 2^31): no 64-bit division
+  const unsigned gq = ok ? (unsigned)g / (unsigned)ncols : 0u;
+  const int64_t s = gq, kx = ok ? (int64_t)((unsigned)g - gq * (unsigned)ncols) : 0;
   const cx<R>* src = in + s * in_stride;
   const int* sl = SLOT ? slot + kx * P : nullptr;
   cx<R>* dst = T + s * tslice + kx * tstride;
@@ -532,7 +563,7 @@ __global__ void __launch_bounds__(kThreads) k_col_inv(const cx<R>* __restrict__ 
   auto st = [&](int y, cx<R> val) {
     if (ok && y < n_out) dst[y] = val;
   };
-  run_passes<R, P, 0, true, true, true>(bufs + v * SH::VSTR, tw, tid, ld, st);
+  run_passes<R, P, 0, true, true, true, false, HOUT>(bufs + v * SH::VSTR, tw, tid, ld, st);
 }
 
 // Stage iii row pass, first half: the half spectra A = T[kx][y0], B =
@@ -585,7 +616,7 @@ __device__ __forceinline__ void load_packed_pairs(const cx<R>* __restrict__ src,
 // image - sub and accumulates its squares (FP64) per block into partials.
 // With sampling on, only the scan positions are kept, written compactly to
 // out[s][my][mx] (the measurement operator of Sec. 3.3); `sub` has that layout.
-template <typename R, int P, bool SAMP>
+template <typename R, int P, bool SAMP, bool HOUT>
 __global__ void __launch_bounds__(kThreads) k_row_c2r(const cx<R>* __restrict__ T, int tstride,
                                                       int64_t tslice, int nx_out, int ny_out,
                                                       R* __restrict__ out, int64_t out_stride,
@@ -605,7 +636,7 @@ __global__ void __launch_bounds__(kThreads) k_row_c2r(const cx<R>* __restrict__ 
   RowPairStore<R, SAMP> st(out + s * out_stride, sub ? sub + s * out_stride : nullptr,
                            2 * (pair0 + v), nx_out, ny_out, sm);
   SmemLoad<R> ld;
-  run_passes<R, P, 0, true, false, true>(bufs + v * SH::VSTR, tw, tid, ld, st);
+  run_passes<R, P, 0, true, false, true, false, HOUT>(bufs + v * SH::VSTR, tw, tid, ld, st);
   if (partials) block_sum_to(st.acc, partials + (int64_t)blockIdx.y * gridDim.x + blockIdx.x);
 }
 
@@ -615,7 +646,9 @@ __global__ void __launch_bounds__(kThreads) k_row_c2r(const cx<R>* __restrict__ 
 // squares summed in FP64 into partials, then the forward row transform of r as
 // k_row_r2c does it, its half spectra written back over the same rows of T
 // (each block reads its rows entirely before writing them). The residual
-// itself never leaves the chip.
+// itself never leaves the chip. A plan's nx is at most P/2 (P >= 2 nx - 1,
+// P even), so the inverse transform forms only x < P/2 and the forward one
+// skips the zero half.
 template <typename R, int P, bool SAMP>
 __global__ void __launch_bounds__(kThreads) k_row_resid(cx<R>* __restrict__ T, int tstride,
                                                         int64_t tslice, int nx, int ny,
@@ -636,7 +669,7 @@ __global__ void __launch_bounds__(kThreads) k_row_resid(cx<R>* __restrict__ T, i
   cx<R>* b = bufs + v * SH::VSTR;
   SmemLoad<R> sl;
   NoStore<R> ns;
-  run_passes<R, P, 0, true, false, false>(b, tw, tid, sl, ns);  // image rows, natural order
+  run_passes<R, P, 0, true, false, false, false, true>(b, tw, tid, sl, ns);  // image rows x < P/2
   // the layout of y: the row pair's offsets (scan rows with sampling on)
   const int y0 = 2 * (pair0 + v);
   RowPairStore<R, SAMP> rows(nullptr, y + s * y_stride, y0, nx, ny, sm);
@@ -659,7 +692,7 @@ __global__ void __launch_bounds__(kThreads) k_row_resid(cx<R>* __restrict__ T, i
     b[pidx(x)] = mk<R>(r0, r1);
   }
   __syncthreads();
-  run_passes<R, P, 0, false, false, false>(b, tw, tid, sl, ns);  // spectrum of r0 + i r1
+  run_passes<R, P, 0, false, false, false, true>(b, tw, tid, sl, ns);  // spectrum of r0 + i r1
 #pragma unroll 4
   for (int i = threadIdx.x; i < SH::VPB * (P / 2 + 1); i += kThreads) {
     const int vv = i % SH::VPB, kx = i / SH::VPB;
@@ -676,7 +709,8 @@ __global__ void __launch_bounds__(kThreads) k_row_resid(cx<R>* __restrict__ T, i
 // Stage iii row pass over the depth slices with the FISTA step (Eq. 14-15)
 // in place of the gradient store: each gradient value g of the kept columns
 // updates y (momentum point) and xprev (x_{k-1}) of its voxel in place; the
-// last block to finish advances the iteration (see FistaStep).
+// last block to finish advances the iteration (see FistaStep). Only x < P/2
+// is formed (a plan's nx is at most P/2).
 template <typename R, int P>
 __global__ void __launch_bounds__(kThreads) k_row_c2r_step(
     const cx<R>* __restrict__ T, int tstride, int64_t tslice, int nx, int ny, int64_t plane,
@@ -713,7 +747,7 @@ __global__ void __launch_bounds__(kThreads) k_row_c2r_step(
     if (ok1) upd((int64_t)nx + x, z.y);
   };
   SmemLoad<R> ld;
-  run_passes<R, P, 0, true, false, true>(bufs + v * SH::VSTR, tw, tid, ld, st);
+  run_passes<R, P, 0, true, false, true, false, true>(bufs + v * SH::VSTR, tw, tid, ld, st);
   __shared__ bool last;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -740,7 +774,9 @@ template <typename R, int P>
 cudaError_t FftLen<R, P>::row_r2c(const R* in, int64_t in_stride, int nx_in, int ny_in, cx<R>* T, int tstride,
                                   int64_t tslice, int S, const cx<R>* tw, cudaStream_t st, Samp sm) {
   using SH = Shape<P>;
-  auto fn = sm.on ? k_row_r2c<R, P, true> : k_row_r2c<R, P, false>;
+  const bool zin = 2 * nx_in <= P;  // the zero padding covers [P/2, P)
+  auto fn = sm.on ? (zin ? k_row_r2c<R, P, true, true> : k_row_r2c<R, P, true, false>)
+                  : (zin ? k_row_r2c<R, P, false, true> : k_row_r2c<R, P, false, false>);
   cudaError_t e = set_smem_attr<R, P>((const void*)fn);
   if (e != cudaSuccess) return e;
   const int pairs = (ny_in + 1) / 2;
@@ -754,7 +790,9 @@ cudaError_t FftLen<R, P>::col_fwd(const cx<R>* T, int tstride, int64_t tslice, i
                                   cx<R>* out, int64_t out_stride, const cx<R>* tw, cudaStream_t st,
                                   const int* slot) {
   using SH = Shape<P>;
-  auto fn = slot ? k_col_fwd<R, P, true> : k_col_fwd<R, P, false>;
+  const bool zin = 2 * n_in <= P;
+  auto fn = slot ? (zin ? k_col_fwd<R, P, true, true> : k_col_fwd<R, P, true, false>)
+                 : (zin ? k_col_fwd<R, P, false, true> : k_col_fwd<R, P, false, false>);
   cudaError_t e = set_smem_attr<R, P>((const void*)fn);
   if (e != cudaSuccess) return e;
   const int64_t nvec = (int64_t)S * ncols;
@@ -767,7 +805,9 @@ template <typename R, int P>
 cudaError_t FftLen<R, P>::col_inv(const cx<R>* in, int64_t in_stride, int ncols, int S, cx<R>* T, int tstride,
                                   int64_t tslice, int n_out, const cx<R>* tw, cudaStream_t st, const int* slot) {
   using SH = Shape<P>;
-  auto fn = slot ? k_col_inv<R, P, true> : k_col_inv<R, P, false>;
+  const bool hout = 2 * n_out <= P;  // rows [P/2, P) are cropped away
+  auto fn = slot ? (hout ? k_col_inv<R, P, true, true> : k_col_inv<R, P, true, false>)
+                 : (hout ? k_col_inv<R, P, false, true> : k_col_inv<R, P, false, false>);
   cudaError_t e = set_smem_attr<R, P>((const void*)fn);
   if (e != cudaSuccess) return e;
   const int64_t nvec = (int64_t)S * ncols;
@@ -781,7 +821,9 @@ cudaError_t FftLen<R, P>::row_c2r(const cx<R>* T, int tstride, int64_t tslice, i
                                   int64_t out_stride, int S, const R* sub, double* partials, const cx<R>* tw,
                                   cudaStream_t st, int* nblocks, Samp sm) {
   using SH = Shape<P>;
-  auto fn = sm.on ? k_row_c2r<R, P, true> : k_row_c2r<R, P, false>;
+  const bool hout = 2 * nx_out <= P;
+  auto fn = sm.on ? (hout ? k_row_c2r<R, P, true, true> : k_row_c2r<R, P, true, false>)
+                  : (hout ? k_row_c2r<R, P, false, true> : k_row_c2r<R, P, false, false>);
   cudaError_t e = set_smem_attr<R, P>((const void*)fn);
   if (e != cudaSuccess) return e;
   const int pairs = (ny_out + 1) / 2;
