@@ -65,6 +65,23 @@ struct PassOf {
   static constexpr int NS = S == 0 ? 1 : (S == 1 ? RadixPlan<P>::R[0] : RadixPlan<P>::R[0] * RadixPlan<P>::R[1]);
 };
 
+// Shared-memory twiddles, one block per pass S >= 1 laid out [r - 1][k]
+// (r in [1, RAD), k in [0, NS)): the RAD - 1 twiddles W_P^(r k P / (NS RAD))
+// a thread needs sit at stride NS, and the threads of a vector (consecutive
+// k) read consecutive words, free of bank conflicts.
+template <int P>
+struct TwPlan {
+  static constexpr int len(int S) {
+    return S >= RadixPlan<P>::NST || S == 0
+               ? 0
+               : (RadixPlan<P>::R[S] - 1) * (S == 1 ? RadixPlan<P>::R[0]
+                                                    : RadixPlan<P>::R[0] * RadixPlan<P>::R[1]);
+  }
+  static constexpr int OFF1 = 0, OFF2 = len(1);
+  static constexpr int TOTAL = len(1) + len(2);
+  static constexpr int N = (TOTAL + 1) & ~1;  // even: the work buffers stay 16-byte aligned
+};
+
 // One padding slot per 16 elements keeps the radix-16 scatter of the first
 // pass (stride 16) free of shared-memory bank conflicts.
 __device__ __forceinline__ int pidx(int i) { return i + (i >> 4); }
@@ -253,9 +270,10 @@ __device__ __forceinline__ void run_passes(cx<R>* buf, const cx<R>* tw, int tid,
     }
     if constexpr (NS > 1) {
       const int k = j % NS;
+      const cx<R>* tws = tw + (S == 1 ? TwPlan<P>::OFF1 : TwPlan<P>::OFF2) + k;
 #pragma unroll
       for (int r = 1; r < RAD; ++r) {
-        cx<R> w = tw[r * k * (P / (NS * RAD))];  // r k < NS RAD: index < P
+        cx<R> w = tws[(r - 1) * NS];
         if (INV) w.y = -w.y;
         v[q][r] = cmul(v[q][r], w);
       }
@@ -297,15 +315,26 @@ struct NoStore {
 template <typename R, int P>
 __device__ __forceinline__ cx<R>* setup_smem(const cx<R>* tw_g, cx<R>** tw_s) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  using TP = TwPlan<P>;
   cx<R>* tw = reinterpret_cast<cx<R>*>(smem_raw);
-  for (int i = threadIdx.x; i < P; i += blockDim.x) tw[i] = tw_g[i];
+  for (int i = threadIdx.x; i < TP::TOTAL; i += blockDim.x) {
+    const bool second = i >= TP::OFF2;
+    const int rem = second ? i - TP::OFF2 : i;
+    constexpr int NS1 = PassOf<P, 1>::NS, RAD1 = PassOf<P, 1>::RAD;
+    constexpr int NS2 = RadixPlan<P>::NST > 2 ? PassOf<P, 2>::NS : 1;
+    constexpr int RAD2 = RadixPlan<P>::NST > 2 ? PassOf<P, 2>::RAD : 1;
+    const int ns = second ? NS2 : NS1;
+    const int r = rem / ns + 1, k = rem % ns;
+    const int step = second ? P / (NS2 * RAD2) : P / (NS1 * RAD1);
+    tw[i] = tw_g[r * k * step];  // r k < NS RAD: index < P
+  }
   *tw_s = tw;
-  return tw + P;
+  return tw + TP::N;
 }
 
 template <typename R, int P>
 constexpr size_t smem_bytes() {
-  return sizeof(cx<R>) * (size_t)(P + Shape<P>::VPB * Shape<P>::VSTR);
+  return sizeof(cx<R>) * (size_t)(TwPlan<P>::N + Shape<P>::VPB * Shape<P>::VSTR);
 }
 
 // Compact index of sensor coordinate c on a scan axis (offset o, stride st,
