@@ -336,3 +336,18 @@ def test_three_times_power_of_two_sampled_outputs():
         gz = oracle.Grid(g.nx, g.ny, 1, g.nt, g.px, g.py)
         ref = oracle.adjoint_fft(Hf, y, gz)[0]
         assert oracle.rel_l2(a[j], ref) < 1e-5, j
+
+
+def test_in_vivo_geometry_768():
+    """The in vivo scan grid (384 x 326 transverse, padded to 768 x 768, a
+    3 * 2^k length) with an asymmetric random library: H and H* against the
+    FP64 oracle (few depths and samples keep the oracle's 768-point DFTs
+    within seconds)."""
+    g = oracle.Grid(nx=384, ny=326, nz=2, nt=3, px=768, py=768)
+    h = synth.random_kernels(g.nz, g.nt, g.px, g.py, seed=5)
+    A, AT = _ref_ops(h, g)
+    plan = Plan(g.nx, g.ny, g.nz, g.nt, g.px, g.py, table=h)
+    rho = synth.blobs(g.nx, g.ny, g.nz, count=6, seed=1)
+    y = synth.gaussian_field((g.nt, g.ny, g.nx), seed=2)
+    assert oracle.rel_l2(host(plan.forward(cuda(rho))), A(rho)) < 1e-5
+    assert oracle.rel_l2(host(plan.adjoint(cuda(y))), AT(y)) < 1e-5
