@@ -162,8 +162,8 @@ int alloc_workspace(pat_plan* pp) {
   PAT_CUDA(cudaMalloc(&p.red, sizeof(double) * x.c2r_partials));
   PAT_CUDA(cudaMalloc(&x.res, sizeof(double) * 8));
   PAT_CUDA(cudaMalloc(&x.scal, sizeof(double) * 2));
-  PAT_CUDA(cudaMalloc(&p.iter_dev, 2 * sizeof(int)));
-  PAT_CUDA(cudaMemset(p.iter_dev, 0, 2 * sizeof(int)));
+  PAT_CUDA(cudaMalloc(&p.iter_dev, 3 * sizeof(int)));
+  PAT_CUDA(cudaMemset(p.iter_dev, 0, 3 * sizeof(int)));
   const size_t sb = sizeof(double) * L.max_batch;
   PAT_CUDA(cudaMalloc(&x.slots.t, sb));
   PAT_CUDA(cudaMalloc(&x.slots.beta, sb));

@@ -82,13 +82,16 @@ cudaError_t residual_t(const Plan& p, const cx<R>* in, int64_t in_stride, const 
   };
   if ((e = col()) != cudaSuccess) return e;
   auto row = [&]() -> cudaError_t {
+    // one sum (not per group): the pass's last block reduces the partials itself
+    double* total = grouped ? nullptr : sumsq;
+    unsigned* count = reinterpret_cast<unsigned*>(p.iter_dev + 2);
     PAT_P_SWITCH(L.px, (FftLen<R, P_>::row_resid(T, L.tstride, L.tslice, L.nx, L.ny, y, y_stride, S,
-                                          partials, twx, st, &nblocks, sm)))
+                                          partials, total, count, twx, st, &nblocks, sm)))
   };
   if ((e = row()) != cudaSuccess) return e;
-  if (grouped) e = launch_group_sums(p.red, nblocks / groups, groups, group_sums, st);
-  else if (sumsq) e = launch_partials_sum(p.red, nblocks, sumsq, st);
-  if (e != cudaSuccess) return e;
+  if (grouped && (e = launch_group_sums(p.red, nblocks / groups, groups, group_sums, st)) !=
+                     cudaSuccess)
+    return e;
   auto colf = [&]() -> cudaError_t {
     PAT_P_SWITCH(L.py, (FftLen<R, P_>::col_fwd(T, L.tstride, L.tslice, L.ny, L.px / 2 + 1, S, out,
                                         out_stride, twy, st, slot)))

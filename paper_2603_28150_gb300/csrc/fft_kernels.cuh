@@ -675,7 +675,9 @@ __global__ void __launch_bounds__(kThreads) k_row_c2r(const cx<R>* __restrict__ 
 // squares summed in FP64 into partials, then the forward row transform of r as
 // k_row_r2c does it, its half spectra written back over the same rows of T
 // (each block reads its rows entirely before writing them). The residual
-// itself never leaves the chip. A plan's nx is at most P/2 (P >= 2 nx - 1,
+// itself never leaves the chip. With `total`, the last block to finish (block
+// counter `count`, zero on entry and re-armed) also sums the partials into
+// *total. A plan's nx is at most P/2 (P >= 2 nx - 1,
 // P even), so the inverse transform forms only x < P/2 and the forward one
 // skips the zero half.
 template <typename R, int P, bool SAMP>
@@ -684,6 +686,8 @@ __global__ void __launch_bounds__(kThreads) k_row_resid(cx<R>* __restrict__ T, i
                                                         const R* __restrict__ y,
                                                         int64_t y_stride,
                                                         double* __restrict__ partials,
+                                                        double* __restrict__ total,
+                                                        unsigned* __restrict__ count,
                                                         const cx<R>* __restrict__ tw_g, Samp sm) {
   using SH = Shape<P>;
   cx<R>* tw;
@@ -733,6 +737,25 @@ __global__ void __launch_bounds__(kThreads) k_row_resid(cx<R>* __restrict__ T, i
     store_pair(Ts + (int64_t)kx * tstride + yy, A, B);  // tstride even: yy + 1 < tstride
   }
   if (partials) block_sum_to(acc, partials + (int64_t)blockIdx.y * gridDim.x + blockIdx.x);
+  if (total) {
+    // the last block to finish sums every block's partial in a fixed order
+    // into *total (FP64, deterministic) and re-arms the counter
+    __shared__ bool last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      last = atomicAdd(count, 1u) == gridDim.x * gridDim.y - 1;
+    }
+    __syncthreads();
+    if (last) {
+      __threadfence();
+      const int n = (int)(gridDim.x * gridDim.y);
+      double sum = 0.0;
+      for (int i = threadIdx.x; i < n; i += blockDim.x) sum += __ldcg(partials + i);
+      block_sum_to(sum, total);
+      if (threadIdx.x == 0) *count = 0u;
+    }
+  }
 }
 
 // Stage iii row pass over the depth slices with the FISTA step (Eq. 14-15)
@@ -864,8 +887,9 @@ cudaError_t FftLen<R, P>::row_c2r(const cx<R>* T, int tstride, int64_t tslice, i
 
 template <typename R, int P>
 cudaError_t FftLen<R, P>::row_resid(cx<R>* T, int tstride, int64_t tslice, int nx, int ny, const R* y,
-                                    int64_t y_stride, int S, double* partials, const cx<R>* tw, cudaStream_t st,
-                                    int* nblocks, Samp sm) {
+                                    int64_t y_stride, int S, double* partials, double* total,
+                                    unsigned* count, const cx<R>* tw, cudaStream_t st, int* nblocks,
+                                    Samp sm) {
   using SH = Shape<P>;
   auto fn = sm.on ? k_row_resid<R, P, true> : k_row_resid<R, P, false>;
   cudaError_t e = set_smem_attr<R, P>((const void*)fn);
@@ -874,7 +898,7 @@ cudaError_t FftLen<R, P>::row_resid(cx<R>* T, int tstride, int64_t tslice, int n
   dim3 grid((pairs + SH::VPB - 1) / SH::VPB, S);
   *nblocks = (int)(grid.x * grid.y);
   return launch_pdl(fn, grid, dim3(kThreads), smem_bytes<R, P>(), st, T, tstride, tslice, nx, ny, y,
-                    y_stride, partials, tw, sm);
+                    y_stride, partials, partials ? total : nullptr, count, tw, sm);
 }
 
 template <typename R, int P>

@@ -22,10 +22,12 @@ struct FftLen {
   static cudaError_t row_c2r(const cx<R>* T, int tstride, int64_t tslice, int nx_out, int ny_out, R* out,
                              int64_t out_stride, int S, const R* sub, double* partials, const cx<R>* tw,
                              cudaStream_t st, int* nblocks, Samp sm);
-  // fused residual pass between H and H* (inverse row, r = S H x - y, forward row)
+  // fused residual pass between H and H* (inverse row, r = S H x - y, forward row);
+  // with `total` its last block also sums the FP64 partials (block counter `count`)
   static cudaError_t row_resid(cx<R>* T, int tstride, int64_t tslice, int nx, int ny, const R* y,
-                               int64_t y_stride, int S, double* partials, const cx<R>* tw, cudaStream_t st,
-                               int* nblocks, Samp sm);
+                               int64_t y_stride, int S, double* partials, double* total,
+                               unsigned* count, const cx<R>* tw, cudaStream_t st, int* nblocks,
+                               Samp sm);
   // stage iii row pass with the FISTA step in place of the gradient store
   static cudaError_t row_c2r_step(const cx<R>* T, int tstride, int64_t tslice, int nx, int ny,
                                   int64_t plane, int S, const FistaStep& f, const cx<R>* tw,

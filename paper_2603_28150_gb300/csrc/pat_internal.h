@@ -165,6 +165,7 @@ struct Plan {
   double* betas = nullptr;  // FISTA momentum coefficients per iteration
   int betas_cap = 0;
   int* iter_dev = nullptr;  // [0] FISTA iteration counter (graph replay), [1] block counter
+                            // of the FISTA step pass, [2] block counter of the residual pass
   double* r2_dev = nullptr; // FISTA residual norms per iteration
   int r2_cap = 0;
   Graph* graphs = nullptr;
