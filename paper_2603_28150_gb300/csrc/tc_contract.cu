@@ -27,6 +27,7 @@
 // MMA's N dimension (N = 4 x 32); their spectra use the representative-slot
 // layout (a representative's 4 bins in one 32-byte sector of every row), so
 // the gathers and stores of the batched operands stay whole sectors.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
 
@@ -381,6 +382,9 @@ constexpr int kFS = 3;                    // table slots
 constexpr int kFThreads = 192;
 constexpr int kFN = 128;                  // MMA N: 4 members x (re, im) x 16 volumes
 constexpr int kFBBytes = kFN * kTile * 2;  // one part (hi or lo) of a B chunk: 32 KB
+// staged FP32 operand chunk: 16 volumes x 128 rows x one representative's 4
+// complex members (32 bytes)
+constexpr int kStageBytes = kVB * kTile * 32;
 
 struct FoldParams {
   const unsigned char* table;  // split tiles of this direction, per representative
@@ -415,18 +419,31 @@ __device__ __forceinline__ int member(int4 v, int m) {
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
+// 3D tiled tensor copy global -> shared completing on `bar`; x (the innermost
+// coordinate, in floats) is a multiple of 8, so it starts on a 32-byte boundary.
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
 
 template <bool ADJ>
-__global__ void __launch_bounds__(kFThreads, 1) k_tc_fold(FoldParams p) {
+__global__ void __launch_bounds__(kFThreads, 1)
+    k_tc_fold(FoldParams p, const __grid_constant__ CUtensorMap tin) {
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char* slots = smem;                               // [kFS][32 KB]
-  unsigned char* bbuf = smem + (size_t)kFS * kTileBytes;     // [2][hi 32 KB | lo 32 KB]
-  uint64_t* bars = reinterpret_cast<uint64_t*>(bbuf + 2 * 2 * (size_t)kFBBytes);
+  unsigned char* bbuf = smem + (size_t)kFS * kTileBytes;     // [hi 32 KB | lo 32 KB]
+  unsigned char* stage = bbuf + 2 * (size_t)kFBBytes;        // [16 b][128 rows][8 floats]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(stage + kStageBytes);
   uint64_t* full = bars;             // [kFS] tile landed
   uint64_t* empty = bars + kFS;      // [kFS] tile consumed by the MMAs
-  uint64_t* bready = bars + 2 * kFS;  // [2] B chunk written (128 arrivals)
-  uint64_t* bfree = bready + 2;       // [2] B chunk consumed by the MMAs
-  uint64_t* afull = bfree + 2;        // [2] accumulator buffer complete
+  uint64_t* bready = bars + 2 * kFS;  // [1] B chunk written (128 arrivals)
+  uint64_t* bfree = bready + 1;       // [1] B chunk consumed by the MMAs
+  uint64_t* sfull = bfree + 1;        // [1] operand chunk staged by the tensor copy
+  uint64_t* afull = sfull + 1;        // [2] accumulator buffer complete
   uint64_t* aempty = afull + 2;       // [2] accumulator buffer drained (128 arrivals)
   uint64_t* drainb = aempty + 2;      // [1] all MMAs done (teardown)
   uint32_t* tmem_base_s = reinterpret_cast<uint32_t*>(drainb + 1);
@@ -445,9 +462,10 @@ __global__ void __launch_bounds__(kFThreads, 1) k_tc_fold(FoldParams p) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
+    mbar_init(bready, 128);
+    mbar_init(bfree, 1);
+    mbar_init(sfull, 1);
     for (int i = 0; i < 2; ++i) {
-      mbar_init(&bready[i], 128);
-      mbar_init(&bfree[i], 1);
       mbar_init(&afull[i], 1);
       mbar_init(&aempty[i], 128);
     }
@@ -467,6 +485,7 @@ __global__ void __launch_bounds__(kFThreads, 1) k_tc_fold(FoldParams p) {
   tc_fence_after();
   const uint32_t tmem = *tmem_base_s;
   int64_t issued = 0;  // table tiles copied (warp 0)
+  int64_t staged = 0;  // operand chunks staged (warp 1)
 
   if (warp == 0) {
     // ---- producer: the tiles of this CTA's representatives, in MMA order
@@ -485,21 +504,40 @@ __global__ void __launch_bounds__(kFThreads, 1) k_tc_fold(FoldParams p) {
       __syncwarp();
     }
   } else if (warp == 1) {
-    // ---- MMA issuer (lane 0); tile j of representative i is (r, part) = (j / 2, j % 2)
+    // ---- MMA issuer (lane 0); tile j of representative i is (r, part) = (j / 2, j % 2).
+    // It also stages the operand chunks: chunk c = (representative i, K chunk
+    // kc), c = i * NB + kc, is one 3D tensor copy (8 floats x 128 rows x 16
+    // volumes: the 32-byte member groups of one representative; volumes past
+    // the batch read as zero) into the staging buffer, issued once the gather
+    // warps have read chunk c - 1 out of it (B chunk c - 1 ready).
     constexpr uint32_t idesc = idesc_bf16(kTile, kFN);
+    const int64_t nchunks = nmine * NB;
+    auto stage_chunk = [&](int64_t c) {
+      if (lane == 0) {
+        const int64_t u = blockIdx.x + (c / NB) * gridDim.x;
+        mbar_arrive_expect_tx(sfull, kStageBytes);
+        tma_load_3d(stage, &tin, (int)(8 * u), (int)(c % NB) * kTile, 0, sfull);
+      }
+      staged = c + 1;
+      __syncwarp();
+    };
+    if (nchunks > 0) stage_chunk(0);
     int64_t j = 0;
     for (int64_t i = 0; i < nmine && !*abort_s; ++i) {
       bool ok = true;
       for (int r = 0; r < R && ok; ++r) {
         const int64_t c = ADJ ? i * NB + r : i;  // B chunk
-        if (ADJ || r == 0) ok = fwait_warp(&bready[c & 1], (uint32_t)((c >> 1) & 1), abort_s);
+        if (ADJ || r == 0) {
+          ok = fwait_warp(bready, (uint32_t)(c & 1), abort_s);
+          if (ok && c + 1 < nchunks) stage_chunk(c + 1);
+        }
         const int64_t q = ADJ ? i : i * NA + r / 2;  // accumulator unit
         const bool unit_start = ADJ ? r == 0 : (r % 2 == 0);
         if (ok && unit_start && q >= 2)
           ok = fwait_warp(&aempty[q & 1], (uint32_t)(((q >> 1) - 1) & 1), abort_s);
         if (!ok) break;
         tc_fence_after();
-        const unsigned char* bh = bbuf + (size_t)(c & 1) * 2 * kFBBytes;
+        const unsigned char* bh = bbuf;
         const unsigned char* bl = bh + kFBBytes;
         const uint32_t d = tmem + (uint32_t)((q & 1) * 256 + (ADJ ? 0 : (r % 2) * 128));
         for (int part = 0; part < 2 && ok; ++part, ++j) {
@@ -525,7 +563,7 @@ __global__ void __launch_bounds__(kFThreads, 1) k_tc_fold(FoldParams p) {
         if (!ok) break;
         const bool unit_end = ADJ ? r == R - 1 : (r % 2 == 1 || r == R - 1);
         if (lane == 0) {
-          if (ADJ || r == R - 1) mma_commit(&bfree[c & 1]);
+          if (ADJ || r == R - 1) mma_commit(bfree);
           if (unit_end) mma_commit(&afull[q & 1]);
         }
         __syncwarp();
@@ -538,26 +576,27 @@ __global__ void __launch_bounds__(kFThreads, 1) k_tc_fold(FoldParams p) {
     // Operands in the slot layout: row (b, r) of X / D holds the 4 members of
     // representative u at [4u, 4u + 4) of its srow complex values (32 bytes).
     auto gather = [&](int64_t i, int kc, int64_t c) -> bool {
-      if (c >= 2 && !fwait_warp(&bfree[c & 1], (uint32_t)(((c >> 1) - 1) & 1), abort_s))
-        return false;
+      (void)kc;
+      // the B buffer is free once the MMAs of chunk c - 1 are done
+      if (c >= 1 && !fwait_warp(bfree, (uint32_t)((c - 1) & 1), abort_s)) return false;
+      if (!fwait_warp(sfull, (uint32_t)(c & 1), abort_s)) return false;
       tc_fence_after();
       const int64_t u = blockIdx.x + i * gridDim.x;
       const int4 mem = p.members[u];
-      unsigned char* bh = bbuf + (size_t)(c & 1) * 2 * kFBBytes;
-      // items (b, octet of rows): 16 x 16, two per thread, all loads in flight
+      unsigned char* bh = bbuf;
+      const float* sf = reinterpret_cast<const float*>(stage);
+      // items (b, octet of rows): 16 x 16, two per thread
 #pragma unroll
       for (int k = 0; k < 2; ++k) {
         const int it = ct + k * 128;
         const int b = it & 15, oct = it >> 4;
-        const bool live = b < p.batch;
         float4 lo4[8], hi4[8];  // members (0, 1) and (2, 3) of 8 rows
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
-          const int row = kc * kTile + oct * 8 + q;
-          const float4* src = reinterpret_cast<const float4*>(
-              p.in + ((int64_t)b * p.rows_in + row) * p.srow + 4 * u);
-          lo4[q] = live ? __ldg(src) : make_float4(0.f, 0.f, 0.f, 0.f);
-          hi4[q] = live ? __ldg(src + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
+          const float4* src =
+              reinterpret_cast<const float4*>(sf + ((size_t)b * kTile + oct * 8 + q) * 8);
+          lo4[q] = src[0];
+          hi4[q] = src[1];
         }
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
@@ -578,8 +617,10 @@ __global__ void __launch_bounds__(kFThreads, 1) k_tc_fold(FoldParams p) {
           *reinterpret_cast<uint4*>(bh + kFBBytes + core_off(m * 32 + 16 + b, oct * 8)) = l;
         }
       }
+      // B visible to the MMAs; the staging reads ordered before the next copy
+      // (the MMA warp stages chunk c + 1 once all 128 threads have arrived)
       fence_proxy_async();
-      mbar_arrive(&bready[c & 1]);
+      mbar_arrive(bready);
       return true;
     };
     // Accumulator columns m * 32 + b (real) and m * 32 + 16 + b (imaginary) of
@@ -611,10 +652,14 @@ __global__ void __launch_bounds__(kFThreads, 1) k_tc_fold(FoldParams p) {
     };
     bool ok = true;
     if (!ADJ) {
+      // the next representative's B goes in after the first accumulator unit
+      // is drained, so its MMAs overlap the drain of the second unit
       if (nmine > 0) ok = gather(0, 0, 0);
       for (int64_t i = 0; i < nmine && ok; ++i) {
-        if (i + 1 < nmine) ok = gather(i + 1, 0, i + 1);
-        for (int a = 0; a < NA && ok; ++a) ok = epilogue(i, a, i * NA + a);
+        for (int a = 0; a < NA && ok; ++a) {
+          ok = epilogue(i, a, i * NA + a);
+          if (ok && a == 0 && i + 1 < nmine) ok = gather(i + 1, 0, i + 1);
+        }
       }
     } else {
       for (int64_t i = 0; i < nmine && ok; ++i) {
@@ -636,6 +681,8 @@ __global__ void __launch_bounds__(kFThreads, 1) k_tc_fold(FoldParams p) {
   if (warp == 1 && lane == 0 && *abort_s) {
     mma_commit(drainb);  // arrives once every MMA issued so far has completed
     mbar_wait(drainb, 0);
+    // the last staging copy issued lands before the shared memory is released
+    if (staged > 0) mbar_wait(sfull, (uint32_t)((staged - 1) & 1));
   }
   tc_fence_before();
   __syncthreads();
@@ -646,7 +693,7 @@ __global__ void __launch_bounds__(kFThreads, 1) k_tc_fold(FoldParams p) {
 }
 
 size_t fold_smem() {
-  return (size_t)kFS * kTileBytes + 4 * (size_t)kFBBytes + 8 * (2 * kFS + 9) + 16;
+  return (size_t)kFS * kTileBytes + 2 * (size_t)kFBBytes + kStageBytes + 8 * (2 * kFS + 8) + 16;
 }
 
 template <int G, int S>
@@ -713,6 +760,43 @@ cudaError_t tc_build_tables(const Plan& p, void* fwd, void* adj, cudaStream_t s)
   return cudaGetLastError();
 }
 
+namespace {
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// Tensor map of the operand spectra of one pass of up to 16 volumes in the
+// representative-slot layout, seen as FP32 [nb][rows][2 srow]: a box of 8
+// floats x 128 rows x 16 volumes is one representative's operand chunk
+// (volumes past nb read as zero). The encoder comes from the driver at run
+// time (the library does not link the driver API).
+cudaError_t encode_operand_map(CUtensorMap* map, const void* base, int64_t srow, int rows,
+                               int nb) {
+  static EncodeTiledFn encode = nullptr;
+  if (!encode) {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    cudaError_t e =
+        cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess) return e;
+    if (q != cudaDriverEntryPointSuccess || !f) return cudaErrorNotSupported;
+    encode = reinterpret_cast<EncodeTiledFn>(f);
+  }
+  const cuuint64_t dims[3] = {(cuuint64_t)(2 * srow), (cuuint64_t)rows, (cuuint64_t)nb};
+  const cuuint64_t strides[2] = {(cuuint64_t)(srow * 8), (cuuint64_t)(srow * 8 * rows)};
+  const cuuint32_t box[3] = {8, (cuuint32_t)tc::kTile, (cuuint32_t)tc::kVB};
+  const cuuint32_t step[3] = {1, 1, 1};
+  const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(base), dims,
+                            strides, box, step, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+}  // namespace
+
 // Forward (adjoint = false) or adjoint contraction of `batch` volumes in
 // passes of 16 through the tensor cores.
 cudaError_t tc_contract(const Plan& p, const void* tables_fwd, const void* tables_adj,
@@ -743,8 +827,10 @@ cudaError_t tc_contract(const Plan& p, const void* tables_fwd, const void* table
       q.rows_out = rows_out;
       q.R = L.nt / tc::kTile;
       q.err = err;
+      CUtensorMap map;
+      if ((e = encode_operand_map(&map, q.in, q.srow, rows_in, q.batch)) != cudaSuccess) return e;
       const int grid = (int)std::min<int64_t>(L.U, sms);
-      fn<<<grid, tc::kFThreads, smem, s>>>(q);
+      fn<<<grid, tc::kFThreads, smem, s>>>(q, map);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return cudaSuccess;
