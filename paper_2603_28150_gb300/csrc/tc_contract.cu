@@ -419,6 +419,21 @@ __device__ __forceinline__ int member(int4 v, int m) {
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
+// 3D tiled tensor copy shared -> global (volumes past the tensor's extent are
+// not written), committed as a bulk group; x is a multiple of 8 floats.
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap* map, const void* src, int x, int y,
+                                             int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(
+          reinterpret_cast<uint64_t>(map)),
+      "r"(x), "r"(y), "r"(z), "r"(smem_u32(src))
+      : "memory");
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+// Waits until every committed bulk store has finished reading shared memory.
+__device__ __forceinline__ void bulk_wait_read() {
+  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
 // 3D tiled tensor copy global -> shared completing on `bar`; x (the innermost
 // coordinate, in floats) is a multiple of 8, so it starts on a 32-byte boundary.
 __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z,
@@ -432,7 +447,8 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
 
 template <bool ADJ>
 __global__ void __launch_bounds__(kFThreads, 1)
-    k_tc_fold(FoldParams p, const __grid_constant__ CUtensorMap tin) {
+    k_tc_fold(FoldParams p, const __grid_constant__ CUtensorMap tin,
+              const __grid_constant__ CUtensorMap tout) {
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char* slots = smem;                               // [kFS][32 KB]
   unsigned char* bbuf = smem + (size_t)kFS * kTileBytes;     // [hi 32 KB | lo 32 KB]
@@ -446,7 +462,8 @@ __global__ void __launch_bounds__(kFThreads, 1)
   uint64_t* afull = sfull + 1;        // [2] accumulator buffer complete
   uint64_t* aempty = afull + 2;       // [2] accumulator buffer drained (128 arrivals)
   uint64_t* drainb = aempty + 2;      // [1] all MMAs done (teardown)
-  uint32_t* tmem_base_s = reinterpret_cast<uint32_t*>(drainb + 1);
+  uint64_t* gbar = drainb + 1;        // [1] barrier of the 4 gather warps (128 arrivals)
+  uint32_t* tmem_base_s = reinterpret_cast<uint32_t*>(gbar + 1);
   volatile int* abort_s = reinterpret_cast<volatile int*>(tmem_base_s + 1);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -470,6 +487,7 @@ __global__ void __launch_bounds__(kFThreads, 1)
       mbar_init(&aempty[i], 128);
     }
     mbar_init(drainb, 1);
+    mbar_init(gbar, 128);
     *abort_s = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -521,7 +539,7 @@ __global__ void __launch_bounds__(kFThreads, 1)
       staged = c + 1;
       __syncwarp();
     };
-    if (nchunks > 0) stage_chunk(0);
+    if (ADJ && nchunks > 0) stage_chunk(0);
     int64_t j = 0;
     for (int64_t i = 0; i < nmine && !*abort_s; ++i) {
       bool ok = true;
@@ -529,7 +547,7 @@ __global__ void __launch_bounds__(kFThreads, 1)
         const int64_t c = ADJ ? i * NB + r : i;  // B chunk
         if (ADJ || r == 0) {
           ok = fwait_warp(bready, (uint32_t)(c & 1), abort_s);
-          if (ok && c + 1 < nchunks) stage_chunk(c + 1);
+          if (ADJ && ok && c + 1 < nchunks) stage_chunk(c + 1);
         }
         const int64_t q = ADJ ? i : i * NA + r / 2;  // accumulator unit
         const bool unit_start = ADJ ? r == 0 : (r % 2 == 0);
@@ -650,16 +668,82 @@ __global__ void __launch_bounds__(kFThreads, 1)
       mbar_arrive(&aempty[q & 1]);
       return true;
     };
+    // ---- forward: the staging buffer alternates between the X chunk of the
+    // next representative and the output tiles of the current one, which
+    // leave by 3D tensor stores (one per 128-sample tile: 16 volumes x 128
+    // rows x 32 bytes; volumes past the batch are not written).
+    uint32_t gph = 0;  // phase of the gather-warp barrier
+    auto gsync = [&]() -> bool {
+      mbar_arrive(gbar);
+      const bool ok = fwait_warp(gbar, gph & 1, abort_s);
+      ++gph;
+      return ok;
+    };
+    int64_t fstaged = 0;  // forward X chunks staged (thread ct 0)
+    auto stage_x = [&](int64_t i) {
+      if (ct == 0) {
+        const int64_t u = blockIdx.x + i * gridDim.x;
+        mbar_arrive_expect_tx(sfull, kStageBytes);
+        tma_load_3d(stage, &tin, (int)(8 * u), 0, 0, sfull);
+        fstaged = i + 1;
+      }
+    };
+    auto epilogue_fwd = [&](int64_t i, int a, int64_t q) -> bool {
+      if (!fwait_warp(&afull[q & 1], (uint32_t)((q >> 1) & 1), abort_s)) return false;
+      tc_fence_after();
+      const int64_t u = blockIdx.x + i * gridDim.x;
+      const int nmt = min(2, R - 2 * a);
+      const int r = quarter * 32 + lane;  // row of the 128-sample tile
+      float* sf = reinterpret_cast<float*>(stage);
+      for (int h = 0; h < nmt; ++h) {
+        float v[4][32];
+        const uint32_t col = (uint32_t)((q & 1) * 256 + h * 128);
+#pragma unroll
+        for (int m = 0; m < 4; ++m)
+          tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + col + (uint32_t)(m * 32), v[m]);
+        // the staging buffer is free (X read out, previous tile's store read)
+        if (!gsync()) return false;
+#pragma unroll
+        for (int bb = 0; bb < kVB; ++bb) {
+          float4* o = reinterpret_cast<float4*>(sf + ((size_t)bb * kTile + r) * 8);
+          o[0] = make_float4(v[0][bb], v[0][16 + bb], v[1][bb], v[1][16 + bb]);
+          o[1] = make_float4(v[2][bb], v[2][16 + bb], v[3][bb], v[3][16 + bb]);
+        }
+        fence_proxy_async();
+        if (!gsync()) return false;
+        if (ct == 0) {
+          tma_store_3d(&tout, stage, (int)(8 * u), (2 * a + h) * kTile, 0);
+          bulk_wait_read();
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(&aempty[q & 1]);
+      return true;
+    };
     bool ok = true;
     if (!ADJ) {
-      // the next representative's B goes in after the first accumulator unit
-      // is drained, so its MMAs overlap the drain of the second unit
-      if (nmine > 0) ok = gather(0, 0, 0);
-      for (int64_t i = 0; i < nmine && ok; ++i) {
-        for (int a = 0; a < NA && ok; ++a) {
-          ok = epilogue(i, a, i * NA + a);
-          if (ok && a == 0 && i + 1 < nmine) ok = gather(i + 1, 0, i + 1);
+      // X(0) staged, read out; X(1) staged; then per representative i: read
+      // out X(i + 1), drain i through the staging buffer, stage X(i + 2)
+      if (nmine > 0) {
+        stage_x(0);
+        ok = gather(0, 0, 0);
+        if (ok && nmine > 1) {
+          ok = gsync();
+          if (ok) stage_x(1);
         }
+      }
+      for (int64_t i = 0; i < nmine && ok; ++i) {
+        if (i + 1 < nmine) ok = gather(i + 1, 0, i + 1);
+        for (int a = 0; a < NA && ok; ++a) ok = epilogue_fwd(i, a, i * NA + a);
+        // thread ct 0 waited for its last store's read; the others wrote the
+        // tile before the barrier that preceded it
+        if (ok && i + 2 < nmine) stage_x(i + 2);
+      }
+      // after an abort: the staging copy still in flight lands before the
+      // shared memory is released, and every store has read its tile
+      if (ct == 0) {
+        if (*abort_s && fstaged > 0) mbar_wait(sfull, (uint32_t)((fstaged - 1) & 1));
+        asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
       }
     } else {
       for (int64_t i = 0; i < nmine && ok; ++i) {
@@ -693,7 +777,7 @@ __global__ void __launch_bounds__(kFThreads, 1)
 }
 
 size_t fold_smem() {
-  return (size_t)kFS * kTileBytes + 2 * (size_t)kFBBytes + kStageBytes + 8 * (2 * kFS + 8) + 16;
+  return (size_t)kFS * kTileBytes + 2 * (size_t)kFBBytes + kStageBytes + 8 * (2 * kFS + 9) + 16;
 }
 
 template <int G, int S>
@@ -767,7 +851,7 @@ using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t
                                    const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
                                    CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-// Tensor map of the operand spectra of one pass of up to 16 volumes in the
+// Tensor map of the operand (or result) spectra of one pass of up to 16 volumes in the
 // representative-slot layout, seen as FP32 [nb][rows][2 srow]: a box of 8
 // floats x 128 rows x 16 volumes is one representative's operand chunk
 // (volumes past nb read as zero). The encoder comes from the driver at run
@@ -827,10 +911,12 @@ cudaError_t tc_contract(const Plan& p, const void* tables_fwd, const void* table
       q.rows_out = rows_out;
       q.R = L.nt / tc::kTile;
       q.err = err;
-      CUtensorMap map;
-      if ((e = encode_operand_map(&map, q.in, q.srow, rows_in, q.batch)) != cudaSuccess) return e;
+      CUtensorMap map_in, map_out;
+      if ((e = encode_operand_map(&map_in, q.in, q.srow, rows_in, q.batch)) != cudaSuccess ||
+          (e = encode_operand_map(&map_out, q.out, q.srow, rows_out, q.batch)) != cudaSuccess)
+        return e;
       const int grid = (int)std::min<int64_t>(L.U, sms);
-      fn<<<grid, tc::kFThreads, smem, s>>>(q, map);
+      fn<<<grid, tc::kFThreads, smem, s>>>(q, map_in, map_out);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return cudaSuccess;
