@@ -452,7 +452,7 @@ __global__ void __launch_bounds__(kFThreads, 1)
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char* slots = smem;                               // [kFS][32 KB]
   unsigned char* bbuf = smem + (size_t)kFS * kTileBytes;     // [hi 32 KB | lo 32 KB]
-  unsigned char* stage = bbuf + 2 * (size_t)kFBBytes;        // [16 b][128 rows][8 floats]
+  unsigned char* stage = bbuf + 2 * (size_t)kFBBytes;        // in: [128 rows][16 b][8 floats]; out: [16 b][128 rows][8 floats]
   uint64_t* bars = reinterpret_cast<uint64_t*>(stage + kStageBytes);
   uint64_t* full = bars;             // [kFS] tile landed
   uint64_t* empty = bars + kFS;      // [kFS] tile consumed by the MMAs
@@ -534,7 +534,7 @@ __global__ void __launch_bounds__(kFThreads, 1)
       if (lane == 0) {
         const int64_t u = blockIdx.x + (c / NB) * gridDim.x;
         mbar_arrive_expect_tx(sfull, kStageBytes);
-        tma_load_3d(stage, &tin, (int)(8 * u), (int)(c % NB) * kTile, 0, sfull);
+        tma_load_3d(stage, &tin, (int)(8 * u), 0, (int)(c % NB) * kTile, sfull);
       }
       staged = c + 1;
       __syncwarp();
@@ -612,7 +612,7 @@ __global__ void __launch_bounds__(kFThreads, 1)
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
           const float4* src =
-              reinterpret_cast<const float4*>(sf + ((size_t)b * kTile + oct * 8 + q) * 8);
+              reinterpret_cast<const float4*>(sf + ((size_t)(oct * 8 + q) * kVB + b) * 8);
           lo4[q] = src[0];
           hi4[q] = src[1];
         }
@@ -854,10 +854,13 @@ using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t
 // Tensor map of the operand (or result) spectra of one pass of up to 16 volumes in the
 // representative-slot layout, seen as FP32 [nb][rows][2 srow]: a box of 8
 // floats x 128 rows x 16 volumes is one representative's operand chunk
-// (volumes past nb read as zero). The encoder comes from the driver at run
+// (volumes past nb read as zero). With rows_outer the map's dimensions are
+// ordered (x, volume, row), so the box lands in shared memory as
+// [row][volume][8 floats] and the gather threads of one row octet read
+// neighbouring 32-byte groups. The encoder comes from the driver at run
 // time (the library does not link the driver API).
 cudaError_t encode_operand_map(CUtensorMap* map, const void* base, int64_t srow, int rows,
-                               int nb) {
+                               int nb, bool rows_outer = false) {
   static EncodeTiledFn encode = nullptr;
   if (!encode) {
     void* f = nullptr;
@@ -868,9 +871,17 @@ cudaError_t encode_operand_map(CUtensorMap* map, const void* base, int64_t srow,
     if (q != cudaDriverEntryPointSuccess || !f) return cudaErrorNotSupported;
     encode = reinterpret_cast<EncodeTiledFn>(f);
   }
-  const cuuint64_t dims[3] = {(cuuint64_t)(2 * srow), (cuuint64_t)rows, (cuuint64_t)nb};
-  const cuuint64_t strides[2] = {(cuuint64_t)(srow * 8), (cuuint64_t)(srow * 8 * rows)};
-  const cuuint32_t box[3] = {8, (cuuint32_t)tc::kTile, (cuuint32_t)tc::kVB};
+  cuuint64_t dims[3] = {(cuuint64_t)(2 * srow), (cuuint64_t)rows, (cuuint64_t)nb};
+  cuuint64_t strides[2] = {(cuuint64_t)(srow * 8), (cuuint64_t)(srow * 8 * rows)};
+  cuuint32_t box[3] = {8, (cuuint32_t)tc::kTile, (cuuint32_t)tc::kVB};
+  if (rows_outer) {
+    dims[1] = (cuuint64_t)nb;
+    dims[2] = (cuuint64_t)rows;
+    strides[0] = (cuuint64_t)(srow * 8 * rows);
+    strides[1] = (cuuint64_t)(srow * 8);
+    box[1] = (cuuint32_t)tc::kVB;
+    box[2] = (cuuint32_t)tc::kTile;
+  }
   const cuuint32_t step[3] = {1, 1, 1};
   const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(base), dims,
                             strides, box, step, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -912,7 +923,7 @@ cudaError_t tc_contract(const Plan& p, const void* tables_fwd, const void* table
       q.R = L.nt / tc::kTile;
       q.err = err;
       CUtensorMap map_in, map_out;
-      if ((e = encode_operand_map(&map_in, q.in, q.srow, rows_in, q.batch)) != cudaSuccess ||
+      if ((e = encode_operand_map(&map_in, q.in, q.srow, rows_in, q.batch, true)) != cudaSuccess ||
           (e = encode_operand_map(&map_out, q.out, q.srow, rows_out, q.batch)) != cudaSuccess)
         return e;
       const int grid = (int)std::min<int64_t>(L.U, sms);
