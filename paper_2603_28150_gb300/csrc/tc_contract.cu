@@ -459,7 +459,8 @@ __global__ void __launch_bounds__(kFThreads, 1)
   uint64_t* bready = bars + 2 * kFS;  // [1] B chunk written (128 arrivals)
   uint64_t* bfree = bready + 1;       // [1] B chunk consumed by the MMAs
   uint64_t* sfull = bfree + 1;        // [1] operand chunk staged by the tensor copy
-  uint64_t* afull = sfull + 1;        // [2] accumulator buffer complete
+  uint64_t* sfree = sfull + 1;        // [1] staged chunk read out (128 arrivals; adjoint)
+  uint64_t* afull = sfree + 1;        // [2] accumulator buffer complete
   uint64_t* aempty = afull + 2;       // [2] accumulator buffer drained (128 arrivals)
   uint64_t* drainb = aempty + 2;      // [1] all MMAs done (teardown)
   uint64_t* gbar = drainb + 1;        // [1] barrier of the 4 gather warps (128 arrivals)
@@ -482,6 +483,7 @@ __global__ void __launch_bounds__(kFThreads, 1)
     mbar_init(bready, 128);
     mbar_init(bfree, 1);
     mbar_init(sfull, 1);
+    mbar_init(sfree, 128);
     for (int i = 0; i < 2; ++i) {
       mbar_init(&afull[i], 1);
       mbar_init(&aempty[i], 128);
@@ -545,10 +547,12 @@ __global__ void __launch_bounds__(kFThreads, 1)
       bool ok = true;
       for (int r = 0; r < R && ok; ++r) {
         const int64_t c = ADJ ? i * NB + r : i;  // B chunk
-        if (ADJ || r == 0) {
-          ok = fwait_warp(bready, (uint32_t)(c & 1), abort_s);
-          if (ADJ && ok && c + 1 < nchunks) stage_chunk(c + 1);
+        if (ADJ) {
+          // chunk c read out of the staging buffer: stage chunk c + 1
+          ok = fwait_warp(sfree, (uint32_t)(c & 1), abort_s);
+          if (ok && c + 1 < nchunks) stage_chunk(c + 1);
         }
+        if (ok && (ADJ || r == 0)) ok = fwait_warp(bready, (uint32_t)(c & 1), abort_s);
         const int64_t q = ADJ ? i : i * NA + r / 2;  // accumulator unit
         const bool unit_start = ADJ ? r == 0 : (r % 2 == 0);
         if (ok && unit_start && q >= 2)
@@ -595,27 +599,40 @@ __global__ void __launch_bounds__(kFThreads, 1)
     // representative u at [4u, 4u + 4) of its srow complex values (32 bytes).
     auto gather = [&](int64_t i, int kc, int64_t c) -> bool {
       (void)kc;
-      // the B buffer is free once the MMAs of chunk c - 1 are done
-      if (c >= 1 && !fwait_warp(bfree, (uint32_t)((c - 1) & 1), abort_s)) return false;
       if (!fwait_warp(sfull, (uint32_t)(c & 1), abort_s)) return false;
       tc_fence_after();
       const int64_t u = blockIdx.x + i * gridDim.x;
       const int4 mem = p.members[u];
       unsigned char* bh = bbuf;
       const float* sf = reinterpret_cast<const float*>(stage);
-      // items (b, octet of rows): 16 x 16, two per thread
+      // items (b, octet of rows): 16 x 16, two per thread; both read out of
+      // the staging buffer first, so (adjoint) the next chunk's copy can start
+      // while this one is converted
+      float4 lo4s[2][8], hi4s[2][8];  // members (0, 1) and (2, 3) of 8 rows
 #pragma unroll
       for (int k = 0; k < 2; ++k) {
         const int it = ct + k * 128;
         const int b = it & 15, oct = it >> 4;
-        float4 lo4[8], hi4[8];  // members (0, 1) and (2, 3) of 8 rows
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
           const float4* src =
               reinterpret_cast<const float4*>(sf + ((size_t)(oct * 8 + q) * kVB + b) * 8);
-          lo4[q] = src[0];
-          hi4[q] = src[1];
+          lo4s[k][q] = src[0];
+          hi4s[k][q] = src[1];
         }
+      }
+      if (ADJ) {
+        fence_proxy_async();
+        mbar_arrive(sfree);
+      }
+      // the B buffer is free once the MMAs of chunk c - 1 are done
+      if (c >= 1 && !fwait_warp(bfree, (uint32_t)((c - 1) & 1), abort_s)) return false;
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const int it = ct + k * 128;
+        const int b = it & 15, oct = it >> 4;
+        const float4* lo4 = lo4s[k];
+        const float4* hi4 = hi4s[k];
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
           const bool present = member(mem, m) >= 0;
@@ -635,9 +652,7 @@ __global__ void __launch_bounds__(kFThreads, 1)
           *reinterpret_cast<uint4*>(bh + kFBBytes + core_off(m * 32 + 16 + b, oct * 8)) = l;
         }
       }
-      // B visible to the MMAs; the staging reads ordered before the next copy
-      // (the MMA warp stages chunk c + 1 once all 128 threads have arrived)
-      fence_proxy_async();
+      fence_proxy_async();  // B visible to the MMAs
       mbar_arrive(bready);
       return true;
     };
@@ -777,7 +792,7 @@ __global__ void __launch_bounds__(kFThreads, 1)
 }
 
 size_t fold_smem() {
-  return (size_t)kFS * kTileBytes + 2 * (size_t)kFBBytes + kStageBytes + 8 * (2 * kFS + 9) + 16;
+  return (size_t)kFS * kTileBytes + 2 * (size_t)kFBBytes + kStageBytes + 8 * (2 * kFS + 10) + 16;
 }
 
 template <int G, int S>
