@@ -26,7 +26,8 @@
 // |ky|} (a quarter of the bytes) and put its up to 4 bins side by side in the
 // MMA's N dimension (N = 4 x 32); their spectra use the representative-slot
 // layout (a representative's 4 bins in one 32-byte sector of every row), so
-// the gathers and stores of the batched operands stay whole sectors.
+// a representative's operand chunk is a 3D box (32 bytes x 128 rows x 16
+// volumes) that one tensor copy moves.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
@@ -370,10 +371,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_contract(Params p) {
 // volume b at bin members[u][m], so one pass over u's tiles serves all 4 bins
 // (the table is read once per representative instead of once per bin).
 // Warp roles (192 threads): warp 0 streams the table tiles (cp.async.bulk,
-// kFS-slot ring), warp 1 issues the MMAs, warps 2-5 gather and split the B
-// operand into two alternating buffers and drain the accumulators (two
-// alternating TMEM buffers of 256 columns) to Y / Z, so gathering, MMAs and
-// the epilogue of consecutive representatives overlap.
+// kFS-slot ring); warp 1 issues the MMAs (and, in the adjoint, stages each
+// operand chunk by one 3D tensor copy as soon as the previous one has been
+// read out); warps 2-5 convert the staged FP32 operand chunk into the BF16
+// hi / lo B operand and drain the accumulators (two alternating TMEM buffers
+// of 256 columns): the forward through the staging buffer and 3D tensor
+// stores, the adjoint by direct stores spread over the next representative's
+// chunks. Table streaming, conversion, MMAs and drains of consecutive
+// representatives overlap.
 //   forward: M = 128 time samples of tile mt, K = nz = 128, accumulator units
 //            of two time tiles; one B chunk per representative;
 //   adjoint: M = nz = 128 depths, K = 128-sample chunks kc of nt, one
@@ -656,31 +661,32 @@ __global__ void __launch_bounds__(kFThreads, 1)
       mbar_arrive(bready);
       return true;
     };
-    // Accumulator columns m * 32 + b (real) and m * 32 + 16 + b (imaginary) of
-    // row r go to out row (b, r) at [4u, 4u + 4) as two 16-byte stores.
-    auto epilogue = [&](int64_t i, int a, int64_t q) -> bool {
-      if (!fwait_warp(&afull[q & 1], (uint32_t)((q >> 1) & 1), abort_s)) return false;
+    // Adjoint drain of representative i in `parts` shares of the volumes:
+    // share `part` stores volumes [part * 16 / parts, (part + 1) * 16 / parts).
+    auto epilogue_adj = [&](int64_t i, int part, int parts) -> bool {
+      if (part == 0 && !fwait_warp(&afull[i & 1], (uint32_t)((i >> 1) & 1), abort_s))
+        return false;
       tc_fence_after();
       const int64_t u = blockIdx.x + i * gridDim.x;
-      const int nmt = ADJ ? 1 : min(2, R - 2 * a);
-      for (int h = 0; h < nmt; ++h) {
-        const int row = (ADJ ? 0 : (2 * a + h) * kTile) + quarter * 32 + lane;
-        float v[4][32];
-        const uint32_t col = (uint32_t)((q & 1) * 256 + h * 128);
+      const int row = quarter * 32 + lane;
+      const int b0 = part * kVB / parts, b1 = (part + 1) * kVB / parts;
+      float v[4][32];
+      const uint32_t col = (uint32_t)((i & 1) * 256);
 #pragma unroll
-        for (int m = 0; m < 4; ++m)
-          tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + col + (uint32_t)(m * 32), v[m]);
+      for (int m = 0; m < 4; ++m)
+        tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + col + (uint32_t)(m * 32), v[m]);
 #pragma unroll
-        for (int bb = 0; bb < kVB; ++bb) {
-          if (bb >= p.batch) break;
-          float4* o =
-              reinterpret_cast<float4*>(p.out + ((int64_t)bb * p.rows_out + row) * p.srow + 4 * u);
-          o[0] = make_float4(v[0][bb], v[0][16 + bb], v[1][bb], v[1][16 + bb]);
-          o[1] = make_float4(v[2][bb], v[2][16 + bb], v[3][bb], v[3][16 + bb]);
-        }
+      for (int bb = 0; bb < kVB; ++bb) {
+        if (bb < b0 || bb >= b1 || bb >= p.batch) continue;
+        float4* o =
+            reinterpret_cast<float4*>(p.out + ((int64_t)bb * p.rows_out + row) * p.srow + 4 * u);
+        o[0] = make_float4(v[0][bb], v[0][16 + bb], v[1][bb], v[1][16 + bb]);
+        o[1] = make_float4(v[2][bb], v[2][16 + bb], v[3][bb], v[3][16 + bb]);
       }
-      tc_fence_before();
-      mbar_arrive(&aempty[q & 1]);
+      if (part == parts - 1) {
+        tc_fence_before();
+        mbar_arrive(&aempty[i & 1]);
+      }
       return true;
     };
     // ---- forward: the staging buffer alternates between the X chunk of the
@@ -761,11 +767,17 @@ __global__ void __launch_bounds__(kFThreads, 1)
         asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
       }
     } else {
+      // the drain of representative i - 1 is spread over the K chunks of i
+      // (a share of the volumes after each gather), filling the waits for the
+      // staged chunks
       for (int64_t i = 0; i < nmine && ok; ++i) {
-        for (int kc = 0; kc < NB && ok; ++kc) ok = gather(i, kc, i * NB + kc);
-        if (ok && i >= 1) ok = epilogue(i - 1, 0, i - 1);
+        for (int kc = 0; kc < NB && ok; ++kc) {
+          ok = gather(i, kc, i * NB + kc);
+          if (ok && i >= 1) ok = epilogue_adj(i - 1, kc, NB);
+        }
       }
-      if (ok && nmine > 0) ok = epilogue(nmine - 1, 0, nmine - 1);
+      for (int part = 0; part < NB && ok && nmine > 0; ++part)
+        ok = epilogue_adj(nmine - 1, part, NB);
     }
   }
 
