@@ -533,8 +533,10 @@ __global__ void __launch_bounds__(kFThreads, 1)
     // It also stages the operand chunks: chunk c = (representative i, K chunk
     // kc), c = i * NB + kc, is one 3D tensor copy (8 floats x 128 rows x 16
     // volumes: the 32-byte member groups of one representative; volumes past
-    // the batch read as zero) into the staging buffer, issued once the gather
-    // warps have read chunk c - 1 out of it (B chunk c - 1 ready).
+    // the batch read as zero) into the staging buffer, issued as soon as the
+    // gather warps have read chunk c - 1 out of it (before they convert it).
+    // The forward stages its one chunk per representative from the gather
+    // warps instead (the staging buffer also carries its output tiles).
     constexpr uint32_t idesc = idesc_bf16(kTile, kFN);
     const int64_t nchunks = nmine * NB;
     auto stage_chunk = [&](int64_t c) {
