@@ -1,7 +1,7 @@
 // Batched 2D real FFT stages of the operator (Sec. 3.2, Eq. 16 terms (i) and (iii)).
 //
 // A P-point complex DFT runs as a Stockham auto-sort FFT (Govindaraju et al.,
-// SC'08 formulation) over 1-3 passes of radix 2/4/8/16, or for P = 3 * 2^k a
+// SC'08 formulation) over 1-3 passes of radix 2/4/8/16/32, or for P = 3 * 2^k a
 // first pass of radix 24 (3 x 8 in registers) then radix 2-8: each thread holds one
 // radix-R butterfly in registers, multiplies by exp(-2 pi i r k / (Ns R))
 // (twiddles from a host FP64 table staged in shared memory) and writes the
@@ -39,8 +39,8 @@ template <> struct RadixPlan<32>   { static constexpr int NST = 2, RMAX = 8;  st
 template <> struct RadixPlan<64>   { static constexpr int NST = 2, RMAX = 8;  static constexpr int R[3] = {8, 8, 1}; };
 template <> struct RadixPlan<128>  { static constexpr int NST = 2, RMAX = 16; static constexpr int R[3] = {16, 8, 1}; };
 template <> struct RadixPlan<256>  { static constexpr int NST = 2, RMAX = 16; static constexpr int R[3] = {16, 16, 1}; };
-template <> struct RadixPlan<512>  { static constexpr int NST = 3, RMAX = 8;  static constexpr int R[3] = {8, 8, 8}; };
-template <> struct RadixPlan<1024> { static constexpr int NST = 3, RMAX = 16; static constexpr int R[3] = {16, 8, 8}; };
+template <> struct RadixPlan<512>  { static constexpr int NST = 2, RMAX = 32; static constexpr int R[3] = {32, 16, 1}; };
+template <> struct RadixPlan<1024> { static constexpr int NST = 2, RMAX = 32; static constexpr int R[3] = {32, 32, 1}; };
 // three times a power of two: a 24-point first pass (every later radix divides 24)
 template <> struct RadixPlan<24>   { static constexpr int NST = 1, RMAX = 24; static constexpr int R[3] = {24, 1, 1}; };
 template <> struct RadixPlan<48>   { static constexpr int NST = 2, RMAX = 24; static constexpr int R[3] = {24, 2, 1}; };
@@ -108,6 +108,31 @@ __device__ __forceinline__ cx<R> mul_w16(cx<R> b, int m) {
   return cmul(b, w);
 }
 
+// exp(-2 pi i m / 32) for m in [0, 16) (conjugated for the inverse): even m
+// are the 16th roots above; the odd ones from cos / sin of odd multiples of
+// pi / 16.
+template <typename R, bool INV>
+__device__ __forceinline__ cx<R> mul_w32(cx<R> b, int m) {
+  if (!(m & 1)) return mul_w16<R, INV>(b, m >> 1);
+  const R c1 = (R)0.98078528040323044913;  // cos(pi/16)
+  const R s1 = (R)0.19509032201612826785;  // sin(pi/16)
+  const R c3 = (R)0.83146961230254523708;  // cos(3 pi/16)
+  const R s3 = (R)0.55557023301960222474;  // sin(3 pi/16)
+  cx<R> w;
+  switch (m) {
+    case 1: w = mk<R>(c1, -s1); break;
+    case 3: w = mk<R>(c3, -s3); break;
+    case 5: w = mk<R>(s3, -c3); break;
+    case 7: w = mk<R>(s1, -c1); break;
+    case 9: w = mk<R>(-s1, -c1); break;
+    case 11: w = mk<R>(-s3, -c3); break;
+    case 13: w = mk<R>(-c3, -s3); break;
+    default: w = mk<R>(-c1, -s1); break;  // 15
+  }
+  if (INV) w.y = -w.y;
+  return cmul(b, w);
+}
+
 template <int N>
 __host__ __device__ constexpr int bitrev(int i) {
   int r = 0;
@@ -128,7 +153,7 @@ __device__ __forceinline__ void dit_passes(cx<R>* a) {
 #pragma unroll
     for (int k = 0; k < LEN / 2; ++k) {
       cx<R> u = a[i + k];
-      cx<R> t = mul_w16<R, INV>(a[i + k + LEN / 2], k * (16 / LEN));
+      cx<R> t = mul_w32<R, INV>(a[i + k + LEN / 2], k * (32 / LEN));
       a[i + k] = cadd(u, t);
       if (!(HOUT && LEN == N)) a[i + k + LEN / 2] = csub(u, t);
     }
@@ -197,7 +222,7 @@ __device__ __forceinline__ void dft24(cx<R>* a) {
   }
 }
 
-// In-register N-point DFT: N = 2, 4, 8, 16 by radix-2 decimation in time,
+// In-register N-point DFT: N = 2, 4, 8, 16, 32 by radix-2 decimation in time,
 // N = 24 as 3 x 8. ZIN: inputs [N/2, N) are zero (zero padding), so after
 // the bit reversal every odd slot is zero and the span-2 pass is a copy.
 // HOUT: only outputs [0, N/2) are used (crop); ignored for N = 24.
