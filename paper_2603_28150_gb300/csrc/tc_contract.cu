@@ -888,18 +888,20 @@ using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t
 // [row][volume][8 floats] and the gather threads of one row octet read
 // neighbouring 32-byte groups. The encoder comes from the driver at run
 // time (the library does not link the driver API).
+EncodeTiledFn load_encoder() {
+  void* f = nullptr;
+  cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
+                                       &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess)
+    return nullptr;
+  return reinterpret_cast<EncodeTiledFn>(f);
+}
+
 cudaError_t encode_operand_map(CUtensorMap* map, const void* base, int64_t srow, int rows,
                                int nb, bool rows_outer = false) {
-  static EncodeTiledFn encode = nullptr;
-  if (!encode) {
-    void* f = nullptr;
-    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
-    cudaError_t e =
-        cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q);
-    if (e != cudaSuccess) return e;
-    if (q != cudaDriverEntryPointSuccess || !f) return cudaErrorNotSupported;
-    encode = reinterpret_cast<EncodeTiledFn>(f);
-  }
+  static const EncodeTiledFn encode = load_encoder();  // resolved once, thread-safe
+  if (!encode) return cudaErrorNotSupported;
   cuuint64_t dims[3] = {(cuuint64_t)(2 * srow), (cuuint64_t)rows, (cuuint64_t)nb};
   cuuint64_t strides[2] = {(cuuint64_t)(srow * 8), (cuuint64_t)(srow * 8 * rows)};
   cuuint32_t box[3] = {8, (cuuint32_t)tc::kTile, (cuuint32_t)tc::kVB};
