@@ -143,10 +143,39 @@ __host__ __device__ constexpr int bitrev(int i) {
   return r;
 }
 
+// Complex add / subtract, with PAIRED in FP32 as one f32x2 instruction (each
+// lane rounded as the scalar operation is, so the values are identical).
+template <bool PAIRED, typename R>
+__device__ __forceinline__ cx<R> padd(cx<R> a, cx<R> b) {
+  if constexpr (PAIRED && sizeof(R) == 4) {
+    cx<R> d;
+    asm("{\n .reg .b64 ra, rb, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n"
+        " add.rn.f32x2 rd, ra, rb;\n mov.b64 {%0, %1}, rd;\n}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+  } else {
+    return cadd(a, b);
+  }
+}
+template <bool PAIRED, typename R>
+__device__ __forceinline__ cx<R> psub(cx<R> a, cx<R> b) {
+  if constexpr (PAIRED && sizeof(R) == 4) {
+    cx<R> d;
+    asm("{\n .reg .b64 ra, rb, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n"
+        " sub.rn.f32x2 rd, ra, rb;\n mov.b64 {%0, %1}, rd;\n}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+  } else {
+    return csub(a, b);
+  }
+}
+
 // Butterfly passes of span LEN, 2 LEN, ..., N (compile-time recursion keeps
 // every register index constant). With HOUT only outputs [0, N/2) are needed,
 // so the last pass forms only the sums.
-template <typename R, int N, int LEN, bool INV, bool HOUT = false>
+template <typename R, int N, int LEN, bool INV, bool HOUT = false, bool PAIRED = false>
 __device__ __forceinline__ void dit_passes(cx<R>* a) {
 #pragma unroll
   for (int i = 0; i < N; i += LEN) {
@@ -154,11 +183,11 @@ __device__ __forceinline__ void dit_passes(cx<R>* a) {
     for (int k = 0; k < LEN / 2; ++k) {
       cx<R> u = a[i + k];
       cx<R> t = mul_w32<R, INV>(a[i + k + LEN / 2], k * (32 / LEN));
-      a[i + k] = cadd(u, t);
-      if (!(HOUT && LEN == N)) a[i + k + LEN / 2] = csub(u, t);
+      a[i + k] = padd<PAIRED>(u, t);
+      if (!(HOUT && LEN == N)) a[i + k + LEN / 2] = psub<PAIRED>(u, t);
     }
   }
-  if constexpr (LEN < N) dit_passes<R, N, 2 * LEN, INV, HOUT>(a);
+  if constexpr (LEN < N) dit_passes<R, N, 2 * LEN, INV, HOUT, PAIRED>(a);
 }
 
 // exp(-2 pi i m / 24) for m in [0, 15) (conjugated for the inverse), from
@@ -191,7 +220,7 @@ __device__ __forceinline__ cx<R> w24(int m) {
   return mk<R>(c, INV ? sn : -sn);
 }
 
-template <typename R, int N, bool INV, bool ZIN = false, bool HOUT = false>
+template <typename R, int N, bool INV, bool ZIN = false, bool HOUT = false, bool PAIRED = false>
 __device__ __forceinline__ void dft_reg(cx<R>* a);
 
 // 24-point DFT as 3 x 8 (Cooley-Tukey): n = 3 n1 + n2, k = k1 + 8 k2;
@@ -226,7 +255,7 @@ __device__ __forceinline__ void dft24(cx<R>* a) {
 // N = 24 as 3 x 8. ZIN: inputs [N/2, N) are zero (zero padding), so after
 // the bit reversal every odd slot is zero and the span-2 pass is a copy.
 // HOUT: only outputs [0, N/2) are used (crop); ignored for N = 24.
-template <typename R, int N, bool INV, bool ZIN, bool HOUT>
+template <typename R, int N, bool INV, bool ZIN, bool HOUT, bool PAIRED>
 __device__ __forceinline__ void dft_reg(cx<R>* a) {
   if constexpr (N == 24) {
     dft24<R, INV, ZIN>(a);
@@ -243,11 +272,11 @@ __device__ __forceinline__ void dft_reg(cx<R>* a) {
     if constexpr (ZIN && N > 2) {
 #pragma unroll
       for (int i = 0; i < N; i += 2) a[i + 1] = a[i];
-      dit_passes<R, N, 4, INV, HOUT>(a);
+      dit_passes<R, N, 4, INV, HOUT, PAIRED>(a);
     } else if constexpr (ZIN) {
       a[1] = a[0];
     } else {
-      dit_passes<R, N, 2, INV, HOUT>(a);
+      dit_passes<R, N, 2, INV, HOUT, PAIRED>(a);
     }
   }
 }
@@ -303,7 +332,10 @@ __device__ __forceinline__ void run_passes(cx<R>* buf, const cx<R>* tw, int tid,
         v[q][r] = cmul(v[q][r], w);
       }
     }
-    dft_reg<R, RAD, INV, zin, hout>(v[q]);
+    // paired FP32 adds in the radix-2 butterflies of the plans with radices up
+    // to 16 (P <= 256: measured faster; the radix-32 and 3 * 2^k plans were
+    // slower with them and keep scalar adds)
+    dft_reg<R, RAD, INV, zin, hout, (RadixPlan<P>::RMAX <= 16)>(v[q]);
   }
   if constexpr (last_st) {
 #pragma unroll
