@@ -66,6 +66,14 @@ __device__ __forceinline__ void mac(cx<R>& acc, R h, cx<R> x) {
   acc.x = fma(h, x.x, acc.x);
   acc.y = fma(h, x.y, acc.y);
 }
+// Real coefficient times complex value in FP32 as one paired FMA
+// (fma.rn.f32x2: each lane rounded once, as the scalar FMAs are).
+__device__ __forceinline__ void mac(cx<float>& acc, float h, cx<float> x) {
+  asm("{\n .reg .b64 rh, rx, ra;\n mov.b64 rh, {%2, %2};\n mov.b64 rx, {%3, %4};\n"
+      " mov.b64 ra, {%0, %1};\n fma.rn.f32x2 ra, rh, rx, ra;\n mov.b64 {%0, %1}, ra;\n}"
+      : "+f"(acc.x), "+f"(acc.y)
+      : "f"(h), "f"(x.x), "f"(x.y));
+}
 template <typename R>
 __device__ __forceinline__ void mac(cx<R>& acc, cx<R> h, cx<R> x) {
   acc.x = fma(h.x, x.x, acc.x);
