@@ -51,6 +51,31 @@ def test_argument_errors_without_gpu():
     assert L.pat_plan_destroy(None) == pat.PAT_OK
 
 
+@pytest.mark.parametrize("p", [16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512, 768, 1024,
+                               12, 20, 40, 80, 1536, 2048])
+def test_transform_lengths_validated(p):
+    """2^k and 3 * 2^k in [16, 1024] pass the geometry check (without a GPU the
+    call then fails on the device allocation); other lengths are rejected as
+    unsupported before anything else happens."""
+    import numpy as np
+    L = pat.lib()
+    out = ctypes.c_void_p(0)
+    n = max(1, p // 2)
+    g = pat.Geometry(n, n, 1, 1, p, p, 1, 0)
+    table = np.zeros(p * p)  # h[z][t][py][px], FP64, one depth and sample
+    rc = L.pat_plan_create(ctypes.byref(g), table.ctypes.data_as(ctypes.c_void_p), 0, None,
+                           ctypes.byref(out))
+    n2 = p // 3 if p % 3 == 0 else p
+    supported = 16 <= p <= 1024 and (n2 & (n2 - 1)) == 0
+    if supported:
+        assert rc != pat.PAT_ERR_UNSUPPORTED, L.pat_last_error()
+        if rc == pat.PAT_OK:
+            assert L.pat_plan_destroy(out) == pat.PAT_OK
+    else:
+        assert rc == pat.PAT_ERR_UNSUPPORTED
+        assert b"3*2^k" in L.pat_last_error()
+
+
 def test_medium_validation_without_gpu():
     L = pat.lib()
     out = ctypes.c_void_p(0)
