@@ -78,6 +78,7 @@ class FistaResult:
     x: np.ndarray
     objective: list = field(default_factory=list)   # F(x_k) = f(x_k) + g(x_k)
     resid2: list = field(default_factory=list)      # ||H y_k - d||^2 of each gradient step
+    t: list = field(default_factory=list)           # t_1, t_2, ... of the momentum recurrence
 
 
 def prox_g(v, step: float, lam: float):
@@ -85,6 +86,17 @@ def prox_g(v, step: float, lam: float):
     the minimiser of ||x - v||^2 / 2 + step lam ||x||_1 over x >= 0 is
     max(v - step lam, 0) componentwise."""
     return np.maximum(v - step * lam, 0.0)
+
+
+def next_t(t: float) -> float:
+    """Beck & Teboulle's momentum parameter: t_{k+1} = (1 + sqrt(1 + 4 t_k^2)) / 2."""
+    return (1.0 + np.sqrt(1.0 + 4.0 * t * t)) / 2.0
+
+
+def momentum(t: float, t_next: float) -> float:
+    """Extrapolation weight of y_{k+1} = x_k + beta_k (x_k - x_{k-1}):
+    beta_k = (t_k - 1) / t_{k+1}."""
+    return (t - 1.0) / t_next
 
 
 def fista(op: Operator, d, L: float, iters: int, lam: float = 0.0, x0=None,
@@ -95,19 +107,22 @@ def fista(op: Operator, d, L: float, iters: int, lam: float = 0.0, x0=None,
         t_{k+1} = (1 + sqrt(1 + 4 t_k^2)) / 2
         y_{k+1} = x_k + ((t_k - 1) / t_{k+1}) (x_k - x_{k-1})
     x_0 = 0 unless given. Returns x_iters (and, with track, F(x_k) and the
-    residual norms of the gradient steps)."""
+    residual norms of the gradient steps and t_1 .. t_{iters+1})."""
     d = np.asarray(d, np.float64)
     x_prev = np.zeros(op.obj_shape) if x0 is None else np.asarray(x0, np.float64).copy()
     y = x_prev.copy()
     t = 1.0
     out = FistaResult(x=x_prev)
+    if track:
+        out.t.append(t)
     for _ in range(iters):
         r = op.A(y) - d
         grad = op.AT(r)
         x = prox_g(y - grad / L, 1.0 / L, lam)
-        t_next = (1.0 + np.sqrt(1.0 + 4.0 * t * t)) / 2.0
-        y = x + ((t - 1.0) / t_next) * (x - x_prev)
+        t_next = next_t(t)
+        y = x + momentum(t, t_next) * (x - x_prev)
         if track:
+            out.t.append(float(t_next))
             out.resid2.append(float(np.dot(r.ravel(), r.ravel())))
             rx = op.A(x) - d
             out.objective.append(0.5 * float(np.dot(rx.ravel(), rx.ravel()))

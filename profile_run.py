@@ -2,7 +2,7 @@
 device footprint): builds a plan with a device-generated real library and
 applies `--pairs` gradients H*(H x - y) (one forward and one adjoint each).
 
-  python -m paper_2603_28150_gb300.profile_run [--n 128] [--nz 64] [--nt 256]
+  python profile_run.py [--n 128] [--nz 64] [--nt 256]
          [--pairs 3] [--batch 1] [--no-fold] [--complex] [--tensor]
 
 The data y = H x come first (4 FFT launches, 1 contraction). Each pair then
@@ -14,10 +14,14 @@ skipping 12 FFT launches (or 3 contractions) starts at the second pair.
 from __future__ import annotations
 
 import argparse
+import os
+import sys
 
-import torch
+sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
 
-from . import Medium, Plan, synth
+import torch  # noqa: E402
+
+from paper_2603_28150_gb300 import Medium, Plan, synth  # noqa: E402
 
 
 def main(argv=None):

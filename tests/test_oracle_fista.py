@@ -104,3 +104,133 @@ def test_fista_zero_iterations_and_zero_data(n):
     L = np.linalg.svd(M, compute_uv=False)[0] ** 2
     assert np.all(oracle.fista(op, d, L, iters=0).x == 0)
     assert np.all(oracle.fista(op, np.zeros_like(d), L, iters=n).x == 0)
+
+
+# --------------------------------------------------------------------------------------
+# Pins of the momentum step (t-recurrence and beta_k): the fixed-point and KKT pins
+# above hold for any convergent scheme, so these target the acceleration itself.
+
+class _Dense:
+    """A dense matrix in the operator interface the oracle's FISTA takes."""
+
+    def __init__(self, M):
+        self.M = M
+        self.obj_shape = (M.shape[1],)
+
+    def A(self, x):
+        return self.M @ x
+
+    def AT(self, y):
+        return self.M.T @ y
+
+
+def _difference_problem(n):
+    """f(x) = 1/2 ||M x - e_1||^2 with M the (n+1) x n first-difference matrix, so
+    M^T M is the 1-D Laplacian tridiag(-1, 2, -1) (Nesterov's worst case for
+    first-order methods; condition number ~ 4 n^2 / pi^2). Its minimiser has the
+    closed form x*_i = (n - i) / (n + 1) > 0, so the non-negativity of Eq. 14 is
+    inactive there and F* = f(x*)."""
+    M = np.zeros((n + 1, n))
+    for i in range(n):
+        M[i, i], M[i + 1, i] = 1.0, -1.0
+    b = np.zeros(n + 1)
+    b[0] = 1.0
+    xs = (n - np.arange(n)) / (n + 1.0)
+    return M, b, xs
+
+
+def _rate_gap(n=200, iters=200):
+    """max_k (F(x_k) - F*) / (2 L ||x_0 - x*||^2 / (k + 1)^2) of the oracle's FISTA."""
+    M, b, xs = _difference_problem(n)
+    assert np.abs(M.T @ (M @ xs - b)).max() < 1e-12  # the closed form is the minimiser
+    L = np.linalg.svd(M, compute_uv=False)[0] ** 2
+    Fs = 0.5 * float(np.sum((M @ xs - b) ** 2))
+    res = oracle.fista(_Dense(M), b, L, iters=iters, track=True)
+    k = np.arange(1, iters + 1)
+    bound = 2.0 * L * float(xs @ xs) / (k + 1.0) ** 2
+    return float(np.max((np.array(res.objective) - Fs) / bound))
+
+
+def test_fista_rate_bound_ill_conditioned():
+    """Beck & Teboulle (2009), Thm 4.4 on a problem with condition number ~1.6e4
+    where the bound is tight to a factor ~5 and plain proximal gradient (ISTA,
+    F - F* ~ 1/k) exceeds it within 200 iterations."""
+    M, _, _ = _difference_problem(200)
+    s = np.linalg.svd(M, compute_uv=False)
+    assert (s[0] / s[-1]) ** 2 > 1e4
+    assert _rate_gap() <= 1.0
+
+
+@pytest.mark.parametrize("slip", ["ista", "t_update_without_square"])
+def test_rate_bound_catches_planted_momentum_slips(monkeypatch, slip):
+    """The same bound fails when a mistake is planted in the oracle's momentum:
+    no extrapolation (ISTA), or t_{k+1} = (1 + sqrt(1 + 4 t_k)) / 2."""
+    if slip == "ista":
+        monkeypatch.setattr(oracle.solvers, "momentum", lambda t, tn: 0.0)
+    else:
+        monkeypatch.setattr(oracle.solvers, "next_t", lambda t: (1.0 + np.sqrt(1.0 + 4.0 * t)) / 2.0)
+    assert _rate_gap() > 1.0
+
+
+def _three_sequence_iterates(M, b, L, lam, x0, iters):
+    """FISTA in Tseng's three-sequence form (Tseng 2008; Beck & Teboulle's scheme
+    rewritten with z_k = x_{k-1} + t_k (x_k - x_{k-1}) and theta_k = 1 / t_k):
+        y_k = (1 - theta_k) x_{k-1} + theta_k z_{k-1}
+        x_k = y_k - G(y_k) / L,   z_k = z_{k-1} - t_k G(y_k) / L,
+    G = grad f + lambda. It never forms an extrapolation weight beta_k. While the
+    iterates stay positive the prox of Eq. 14 is the shift by lambda / L, so this
+    equals the oracle's x_k exactly (to rounding)."""
+    x, z, t, out = x0.copy(), x0.copy(), 1.0, []
+    for _ in range(iters):
+        y = (1.0 - 1.0 / t) * x + (1.0 / t) * z
+        G = M.T @ (M @ y - b) + lam
+        x = y - G / L
+        z = z - t * G / L
+        out.append(x.copy())
+        t = (1.0 + np.sqrt(1.0 + 4.0 * t * t)) / 2.0
+    return out
+
+
+def _three_sequence_gap(iters=60):
+    n = 40
+    M, _, _ = _difference_problem(n)
+    i = np.arange(n)
+    b = M @ (42.0 + np.sin(i))
+    L = np.linalg.svd(M, compute_uv=False)[0] ** 2
+    lam = 0.05
+    x0 = 40.0 + np.sin(i) + 0.5 * np.cos(0.7 * i)
+    ref = _three_sequence_iterates(M, b, L, lam, x0, iters)
+    assert min(r.min() for r in ref) > 1.0  # positive throughout: the prox is a shift
+    gap = 0.0
+    for k in (1, 2, 3, 4, 7, 20, iters):
+        xo = oracle.fista(_Dense(M), b, L, iters=k, lam=lam, x0=x0).x
+        gap = max(gap, float(np.abs(xo - ref[k - 1]).max() / np.abs(ref[k - 1]).max()))
+    return gap
+
+
+def test_fista_equals_three_sequence_form():
+    assert _three_sequence_gap() < 1e-12
+
+
+@pytest.mark.parametrize("beta", [
+    lambda t, tn: (tn - 1.0) / tn,                           # beta from t_{k+1} alone
+    lambda t, tn: (t - 1.0) / t,                             # beta from t_k alone
+    lambda t, tn: (tn - 1.0) / oracle.solvers.next_t(tn),    # beta one step ahead
+    lambda t, tn: t / tn,                                    # (t_k - 1) written as t_k
+], ids=["t_next_only", "t_only", "one_ahead", "dropped_minus_one"])
+def test_three_sequence_form_catches_planted_beta_slips(monkeypatch, beta):
+    """A mis-indexed extrapolation weight still converges at the accelerated rate
+    (the bound above does not see it) but leaves the exact trajectory."""
+    monkeypatch.setattr(oracle.solvers, "momentum", beta)
+    assert _three_sequence_gap() > 1e-6
+
+
+def test_momentum_sequence_identities():
+    """t_{k+1}^2 - t_{k+1} = t_k^2 (the defining equation of the update), t_1 = 1,
+    and t_k >= (k + 1) / 2 (Beck & Teboulle, Lemma 4.3)."""
+    M, b, _ = _difference_problem(8)
+    t = np.array(oracle.fista(_Dense(M), b, 4.0, iters=300, track=True).t)
+    assert len(t) == 301 and t[0] == 1.0
+    assert np.abs(t[1:] ** 2 - t[1:] - t[:-1] ** 2).max() <= 1e-12 * t[-1] ** 2
+    k = np.arange(1, len(t) + 1)
+    assert np.all(t >= (k + 1) / 2.0)
