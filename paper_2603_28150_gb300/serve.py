@@ -51,6 +51,34 @@ class Geometry:
         return m
 
 
+class QueueTrace:
+    """Queue depth (requests arrived but not yet started) sampled at most every
+    `every` seconds of the run; summarised as mean / max / last and a coarse
+    timeline (max depth per `bucket` seconds)."""
+
+    def __init__(self, every: float = 0.1, bucket: float = 5.0):
+        self.every, self.bucket = every, bucket
+        self.samples = []
+
+    def sample(self, now: float, depth: int, active: int = 0) -> None:
+        if not self.samples or now - self.samples[-1][0] >= self.every:
+            self.samples.append((now, depth, active))
+
+    def summary(self) -> dict:
+        if not self.samples:
+            return {"samples": 0}
+        d = np.array([s[1] for s in self.samples], dtype=np.float64)
+        a = np.array([s[2] for s in self.samples], dtype=np.float64)
+        nb = int(self.samples[-1][0] // self.bucket) + 1
+        line = [0] * nb
+        for t, q, _ in self.samples:
+            b = int(t // self.bucket)
+            line[b] = max(line[b], q)
+        return {"samples": len(self.samples), "mean": float(d.mean()), "max": int(d.max()),
+                "last": int(d[-1]), "mean_active": float(a.mean()),
+                f"max_per_{self.bucket:g}s": line}
+
+
 @dataclass
 class Request:
     rid: int
@@ -162,6 +190,7 @@ class Server:
         self.done, self.rejected = [], []
         self.used = 0
         self.max_queue = 0
+        self.trace = QueueTrace()
         self.t0 = None
 
     # -------------------------------------------------------------- admission
@@ -272,6 +301,7 @@ class Server:
                 self.queue.append(pending.popleft())
             self.max_queue = max(self.max_queue, len(self.queue))
             self.admit()
+            self.trace.sample(now, len(self.queue), sum(len(a) for a in self.active.values()))
             if not self.step_all():
                 # nothing could step (idle, or every engine's queue is full)
                 wait = idle_sleep
@@ -293,7 +323,7 @@ class Server:
         end = self.now()
         out = {"requests": len(requests), "completed": int(lat.size),
                "unfinished": len(unfinished), "rejected": len(self.rejected),
-               "max_queue": self.max_queue}
+               "max_queue": self.max_queue, "queue_depth": self.trace.summary()}
         if lat.size:
             out["p50_ms"] = float(np.percentile(lat, 50) * 1e3)
             out["p99_ms"] = float(np.percentile(lat, 99) * 1e3)
@@ -333,10 +363,18 @@ def serve_one_at_a_time(plans, requests, drain_seconds: float = 60.0):
     last_arrival = pending[-1].arrival if pending else 0.0
     inflight = collections.deque()
     done = []
+    trace = QueueTrace()
     while pending:
         now = time.perf_counter() - t0
         if now > last_arrival + drain_seconds:
             break
+        # arrived but not yet started (the request being issued counts as started)
+        arrived = 0
+        for q in pending:          # sorted by arrival
+            if q.arrival > now:
+                break
+            arrived += 1
+        trace.sample(now, max(0, arrived - 1) if arrived else 0, 1 if inflight else 0)
         r = pending[0]
         if r.arrival > now and not inflight:
             time.sleep(min(0.0005, r.arrival - now))
@@ -361,7 +399,8 @@ def serve_one_at_a_time(plans, requests, drain_seconds: float = 60.0):
         r.finish = ref.elapsed_time(r.handle) / 1e3
     lat = np.array([r.finish - r.arrival for r in done])
     unfinished = [r for r in requests if r.finish is None]
-    out = {"requests": len(requests), "completed": int(lat.size), "unfinished": len(unfinished)}
+    out = {"requests": len(requests), "completed": int(lat.size), "unfinished": len(unfinished),
+           "queue_depth": trace.summary()}
     if lat.size:
         out["p50_ms"] = float(np.percentile(lat, 50) * 1e3)
         out["p99_ms"] = float(np.percentile(lat, 99) * 1e3)

@@ -351,3 +351,32 @@ def test_in_vivo_geometry_768():
     y = synth.gaussian_field((g.nt, g.ny, g.nx), seed=2)
     assert oracle.rel_l2(host(plan.forward(cuda(rho))), A(rho)) < 1e-5
     assert oracle.rel_l2(host(plan.adjoint(cuda(y))), AT(y)) < 1e-5
+
+
+def test_fista_100_cfg2_matches_oracle():
+    """The benchmarked reconstruction: 128^2 -> 256^2, 64 depths, 256 samples,
+    dx = 50 um, dt = 10 ns, vessel phantom + 5 % noise, 100 FISTA iterations
+    (lambda = 0, x0 = 0) on the plan the bench uses (library generated on the
+    device, real spectra, D4-folded: the radix-16 x 16 transforms, the folded
+    contraction grid and the fused residual / step passes at full size).
+    The oracle runs the same iterations on its closed-form library (complex128
+    full planes, ~17 GB of host memory) with the same L."""
+    g = oracle.Grid.square(128, 64, 256)
+    med = MED_50UM
+    mz = oracle.mz_for(g.nz, g.nt, med)
+    Hf = oracle.table_kspace_closed(g, med, mz)
+    op = oracle.Operator(g, Hf=Hf)
+    p0 = synth.vessel_phantom(g.nx, g.nz, seed=0)
+    clean = op.A(p0)
+    y = clean + 0.05 * np.sqrt(np.mean(clean ** 2)) * synth.gaussian_field(clean.shape, seed=1000)
+    L = 1.01 * oracle.power_norm(op, synth.gaussian_field(op.obj_shape, 3), 20)
+    ref = oracle.fista(op, y, L, iters=100, track=True)
+    del op, Hf
+    plan = Plan(g.nx, g.ny, g.nz, g.nt, g.px, g.py,
+                medium=Medium(med.c, med.dx, med.dy, med.dz, med.dt, mz, 1))
+    assert plan.info()["folded"] == 1 and plan.info()["real_table"] == 1
+    x, rep = plan.fista(cuda(y), iters=100, L=L)
+    err = oracle.rel_l2(host(x), ref.x)
+    assert err < 1e-5, err
+    assert abs(rep["resid2_first"] - ref.resid2[0]) < 1e-5 * ref.resid2[0]
+    assert abs(rep["resid2_last"] - ref.resid2[-1]) < 1e-4 * ref.resid2[-1]

@@ -94,3 +94,61 @@ def test_server_mixed_trace_equals_alone():
                                drain_seconds=30)
     assert base["completed"] == len(reqs)
     srv.close()
+
+
+def test_served_tensor_path_equals_alone_and_oracle():
+    """Slots on a split-BF16 plan (128 depths, so steps with >= 2 active slots
+    contract on the tcgen05 tensor cores, BF16 hi/lo operands): FISTA-50
+    requests that enter and leave at different times give, within the
+    split-BF16 tolerance of 1e-3, what each gives alone (pat_fista_solve,
+    batch 1: the FP32 CUDA-core path) and what the FP64 oracle gives."""
+    import torch
+
+    import oracle
+    from tests.helpers import MED_50UM, cuda, host
+    g = oracle.Grid.square(32, 128, 256)
+    med = MED_50UM
+    mz = oracle.mz_for(g.nz, g.nt, med)
+    plan = Plan(g.nx, g.ny, g.nz, g.nt, g.px, g.py, max_batch=4, bf16_split=True,
+                medium=Medium(med.c, med.dx, med.dy, med.dz, med.dt, mz, 1))
+    assert plan.info()["tensor_min_batch"] == 2
+    op = oracle.Operator(g, Hf=oracle.table_kspace_closed(g, med, mz))
+    L = 1.01 * oracle.power_norm(op, synth.gaussian_field(op.obj_shape, 7), 30)
+    ys = []
+    for s in range(3):
+        clean = op.A(synth.vessel_phantom(g.nx, g.nz, seed=60 + s))
+        ys.append(clean + 0.05 * np.sqrt(np.mean(clean ** 2))
+                  * synth.gaussian_field(clean.shape, seed=70 + s))
+    lams = [0.0, 1e-3 * float(np.abs(op.AT(ys[1])).max()), 0.0]
+    yd = [cuda(y) for y in ys]
+    # A alone for 5 steps; B joins (20 steps of 2); C joins (25 steps of 3): A done
+    plan.slot_load(0, yd[0], lams[0], L)
+    for _ in range(5):
+        plan.slots_step(1)
+    plan.slot_load(1, yd[1], lams[1], L)
+    for _ in range(20):
+        plan.slots_step(2)
+    plan.slot_load(2, yd[2], lams[2], L)
+    for _ in range(25):
+        plan.slots_step(3)
+    xa = plan.slot_read(0)[0].clone()
+    plan.slot_move(0, 2)           # C takes A's slot
+    for _ in range(5):
+        plan.slots_step(2)         # B done (50), C at 30
+    xb = plan.slot_read(1)[0].clone()
+    for _ in range(20):
+        plan.slots_step(1)         # C done
+    xc = plan.slot_read(0)[0].clone()
+    plan.check()
+    torch.cuda.synchronize()
+    for x, y, lam in zip((xa, xb, xc), yd, lams):
+        alone = _alone(plan, y, 50, lam, L)
+        assert _rel(x, alone) < 1e-3
+    for x, y, lam in zip((xa, xb, xc), ys, lams):
+        ref = oracle.fista(op, y, L, iters=50, lam=lam).x
+        assert oracle.rel_l2(host(x), ref) < 1e-3
+    # the same three requests as one batched solve on the tensor path
+    xs, _ = plan.fista(torch.stack(yd), iters=50, lam=0.0, L=L)
+    plan.check()
+    for v in (0, 2):
+        assert oracle.rel_l2(host(xs[v]), oracle.fista(op, ys[v], L, iters=50).x) < 1e-3
