@@ -28,7 +28,10 @@
  *   through plan-owned device staging buffers and the call returns after the
  *   result is back in host memory.
  *   The caller owns every array it passes; the library keeps no pointer to
- *   them after a call returns. A plan owns its table copy and its workspace.
+ *   them after a call returns. A plan owns its table copy (the resident
+ *   spectral layout, built at creation). Its workspace (every per-call buffer)
+ *   is either allocated by the plan (pat_plan_create*) or caller-owned device
+ *   memory sized by pat_workspace_size (pat_plan_create*_with_workspace).
  *   `stream` is a cudaStream_t (0 = legacy default stream).
  *   Calls on one plan must not overlap (one plan = one stream of work); plans
  *   are independent of each other.
@@ -130,6 +133,7 @@ typedef struct {
   int32_t tensor_min_batch;   /* batches >= this use the tensor-core contraction (0: never) */
   int32_t folded;             /* 1: one table row per D4 representative {|kx|, |ky|} */
   int64_t table_rows;         /* stored frequency rows: representatives if folded, else bins */
+  int32_t workspace_external; /* 1: the workspace is caller-owned memory */
 } pat_plan_info_t;
 
 /* FISTA settings (Eq. 12-14; Beck & Teboulle's constant-step scheme).
@@ -181,7 +185,34 @@ int pat_plan_create(const pat_geometry* g, const void* table, pat_table_format f
 int pat_plan_create_kspace(const pat_geometry* g, const pat_medium* m,
                            pat_stream stream, pat_plan** out);
 
-/* Frees the plan's device memory (synchronises the device first). NULL is a no-op. */
+/* Device bytes of the workspace of a plan for `g` (Sec. 3.2's three stages
+ * need the slice spectra X / Y of Eq. 16 terms (i)-(iii) between the stages,
+ * plus the FISTA state of Eq. 12-14): the spectra and FFT intermediate, three
+ * object and two data buffers, FP64 reduction scratch, scalars, the slot
+ * state, the FISTA history for up to 4096 iterations per solve, and the
+ * host-pointer staging buffers. Returns the bytes (>= 0), or a negative
+ * pat_status for an invalid geometry. No device call is made. */
+int64_t pat_workspace_size(const pat_geometry* g);
+
+/* pat_plan_create / pat_plan_create_kspace on a caller-owned workspace:
+ * `workspace` is device memory of `ws_bytes` >= pat_workspace_size(g) bytes,
+ * 256-byte aligned (e.g. a torch tensor's storage), which the plan uses for
+ * all its per-call buffers and never frees; it must stay allocated and
+ * untouched by the caller until pat_plan_destroy returns. The plan still
+ * allocates its resident table (and, during creation only, the temporaries of
+ * table preparation). Such a plan runs at most 4096 FISTA iterations per
+ * pat_fista_solve call (PAT_ERR_ARG beyond). Errors as pat_plan_create, plus
+ * PAT_ERR_ARG for a workspace that is not device memory, misaligned or too
+ * small. */
+int pat_plan_create_with_workspace(const pat_geometry* g, const void* table, pat_table_format fmt,
+                                   void* workspace, size_t ws_bytes, pat_stream stream,
+                                   pat_plan** out);
+int pat_plan_create_kspace_with_workspace(const pat_geometry* g, const pat_medium* m,
+                                          void* workspace, size_t ws_bytes, pat_stream stream,
+                                          pat_plan** out);
+
+/* Frees the plan's device memory (synchronises the device first); a
+ * caller-owned workspace is left alone. NULL is a no-op. */
 int pat_plan_destroy(pat_plan* plan);
 
 int pat_plan_info(const pat_plan* plan, pat_plan_info_t* info);
@@ -231,6 +262,29 @@ int pat_plan_set_sensor_response(pat_plan* plan, const double* r, int nr, pat_st
  * is cleared), else PAT_OK. */
 int pat_plan_check(pat_plan* plan);
 
+/* Limit of the pipeline waits of the tensor-core contraction (the mbarrier
+ * waits between its table stream, operand staging, MMAs and accumulator
+ * drain): each tests its barrier at most `polls` times (< 2^32; each test may
+ * suspend the thread for a short, hardware-defined time) before the kernel
+ * gives up: it then records the timeout for pat_plan_check, lets every copy
+ * and MMA it has issued finish (bounded by 2 s of device time), frees its
+ * tensor memory and returns, leaving that call's output undefined. polls < 0
+ * restores the default PAT_WAIT_LIMIT_DEFAULT (a few seconds per wait);
+ * polls = 0 makes every pipeline wait give up at once, which exercises that
+ * path without a device fault. Synchronises the device; cached graphs are
+ * rebuilt on next use. Not described in the paper (a property of this
+ * implementation's kernels). */
+#define PAT_WAIT_LIMIT_DEFAULT 4194304
+int pat_plan_set_wait_limit(pat_plan* plan, int64_t polls);
+
+/* Device allocations the library currently holds over all plans (diagnostic:
+ * a failed pat_plan_create* leaves this count unchanged). Setting the
+ * environment variable PAT_DEBUG_FAIL_ALLOC = n (n >= 1) before a
+ * pat_plan_create* call makes the n-th device allocation of that call fail as
+ * if the device were out of memory (PAT_ERR_OOM), to test the clean-up path;
+ * unset it for normal use. */
+int64_t pat_debug_live_allocations(void);
+
 /* --- operators ----------------------------------------------------------------- */
 
 /* d = H rho (Eq. 7-8) for `batch` volumes. rho: real_t[batch][nz][ny][nx] in,
@@ -254,6 +308,16 @@ int pat_gradient(pat_plan* plan, const void* x, const void* y, void* grad, int b
  * ||H*H v|| of the last step. Norms accumulate in FP64. Synchronises `stream`. */
 int pat_power_norm(pat_plan* plan, const void* v0, int iters, double* L_out,
                    pat_stream stream);
+
+/* pat_power_norm from a seeded start vector generated on the device:
+ *   v0[i] = 2 u_i - 1,  u_i = (splitmix64(seed + (i + 1) * 0x9E3779B97F4A7C15) >> 11) * 2^-53,
+ * i = 0 .. nz*ny*nx - 1 in the object's memory order (x fastest), splitmix64
+ * the finaliser of Steele, Lea & Flood (2014): z ^= z >> 30; z *= 0xBF58476D1CE4E5B9;
+ * z ^= z >> 27; z *= 0x94D049BB133111EB; z ^= z >> 31; then rounded to real_t.
+ * The same generator is what pat_fista_solve uses (seed 0x5EED) when it
+ * estimates L itself. Synchronises `stream`. */
+int pat_power_norm_seed(pat_plan* plan, int iters, uint64_t seed, double* L_out,
+                        pat_stream stream);
 
 /* FISTA for Eq. 12 with f of Eq. 13 and g of Eq. 14, per volume:
  *   y_1 = x_0, t_1 = 1;  x_k = max(y_k - (H*(H y_k - d))/L - lambda/L, 0);
@@ -340,6 +404,8 @@ int pat_stage_contract(pat_plan* plan, const void* in, void* out, int batch, int
  * Same result as pat_stage_spectrum, without a plan and without allocating:
  * zero-pads `slices` real float [ny][nx] slices (in, device) to py x px and
  * writes their 2D real DFT to out (device), complex float [slices][px/2+1][py].
+ * Both arrays must be on the calling thread's current device (PAT_ERR_ARG
+ * otherwise); the work runs there, on `stream`, which must belong to it.
  * The row-pass intermediate lives in a static device array of 64 MiB that
  * every GPU loading the library holds until the process exits; requests with
  * slices * (px/2 + 1) * (ny rounded up to even) * 8 > 64 MiB return

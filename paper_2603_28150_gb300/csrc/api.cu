@@ -1,10 +1,13 @@
 // C ABI of libpat (declared in include/pat.h): plans, the operator H (Eq. 7-8),
 // its adjoint H* (Eq. 11), the gradient of Eq. 15, the power iteration for
 // ||H*H|| and FISTA (Eq. 12-14) composed from the stage kernels.
+#include <atomic>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "pat_internal.h"
@@ -22,6 +25,26 @@ int cuda_fail(cudaError_t e, const char* what) {
   g_err = std::string(what) + ": " + cudaGetErrorString(e);
   return e == cudaErrorMemoryAllocation ? PAT_ERR_OOM : PAT_ERR_CUDA;
 }
+
+static std::atomic<int64_t> g_live_allocs{0};
+static thread_local long g_fail_countdown = 0;  // 0: no injected failure pending
+
+cudaError_t dev_alloc_raw(void** p, size_t bytes) {
+  *p = nullptr;
+  if (g_fail_countdown > 0 && --g_fail_countdown == 0) return cudaErrorMemoryAllocation;
+  const cudaError_t e = cudaMalloc(p, bytes);
+  if (e == cudaSuccess) g_live_allocs.fetch_add(1);
+  return e;
+}
+void dev_free(void* p) {
+  if (p && cudaFree(p) == cudaSuccess) g_live_allocs.fetch_sub(1);
+}
+void alloc_hook_arm() {
+  const char* v = std::getenv("PAT_DEBUG_FAIL_ALLOC");
+  const long n = v ? std::strtol(v, nullptr, 10) : 0;
+  g_fail_countdown = n > 0 ? n : 0;
+}
+void alloc_hook_disarm() { g_fail_countdown = 0; }
 
 }  // namespace pat
 
@@ -79,16 +102,25 @@ void free_plan(pat_plan* pp) {
     delete g;
     g = n;
   }
-  void* bufs[] = {p.table, p.twx,    p.twy,     p.X,         p.Y,      p.T,       p.vol_a,
-                  p.vol_b, p.vol_c,  p.dat_a,   p.dat_b,     p.red,    p.betas,   p.iter_dev,
-                  p.r2_dev, x.io_obj[0], x.io_obj[1], x.io_dat, x.res, x.scal,
-                  p.tc_fwd, p.tc_adj, p.tc_err, p.fold_members, p.fold_rep, p.fold_slot,
-                  x.slots.t, x.slots.beta, x.slots.invL, x.slots.lamL, x.slots.r2, x.slots.k};
-  for (void* b : bufs) cudaFree(b);
+  // the plan's own memory: the table side, buffers allocated on first use,
+  // and the workspace arena unless the caller owns it
+  void* owned[] = {p.table, p.tc_fwd, p.tc_adj, p.fold_members, p.fold_rep, p.fold_slot};
+  for (void* b : owned) dev_free(b);
+  if (x.io_heap) {
+    dev_free(x.io_obj[0]);
+    dev_free(x.io_obj[1]);
+    dev_free(x.io_dat);
+  }
+  if (p.hist_heap) {
+    dev_free(p.betas);
+    dev_free(p.r2_dev);
+  }
+  if (!p.ws_external) dev_free(p.ws_base);
   if (x.cap) cudaStreamDestroy(x.cap);
   delete pp;
 }
 
+// Fills the twiddle tables exp(-2 pi i k / n) (already carved from the workspace).
 int upload_twiddles(Plan& p) {
   const double pi = 3.14159265358979323846;
   for (int a = 0; a < 2; ++a) {
@@ -98,14 +130,12 @@ int upload_twiddles(Plan& p) {
       w[2 * k] = std::cos(-2.0 * pi * k / n);
       w[2 * k + 1] = std::sin(-2.0 * pi * k / n);
     }
-    void** dst = a == 0 ? &p.twx : &p.twy;
+    void* dst = a == 0 ? p.twx : p.twy;
     if (p.L.fp64) {
-      PAT_CUDA(cudaMalloc(dst, w.size() * 8));
-      PAT_CUDA(cudaMemcpy(*dst, w.data(), w.size() * 8, cudaMemcpyHostToDevice));
+      PAT_CUDA(cudaMemcpy(dst, w.data(), w.size() * 8, cudaMemcpyHostToDevice));
     } else {
       std::vector<float> f(w.begin(), w.end());
-      PAT_CUDA(cudaMalloc(dst, f.size() * 4));
-      PAT_CUDA(cudaMemcpy(*dst, f.data(), f.size() * 4, cudaMemcpyHostToDevice));
+      PAT_CUDA(cudaMemcpy(dst, f.data(), f.size() * 4, cudaMemcpyHostToDevice));
     }
   }
   return PAT_OK;
@@ -126,21 +156,15 @@ int64_t spectrum_row_cap(const Layout& L) {
   return std::max<int64_t>(L.Kpad, 4 * ((U + 31) / 32 * 32));
 }
 
-// Device bytes of a plan's workspace, including the host-staging buffers
-// allocated on the first call with host pointers.
-int64_t workspace_bytes(const Layout& L) {
-  const size_t cs = 2 * L.rsize;
-  const int64_t smax = (int64_t)L.max_batch * std::max(L.nz, L.nt);
-  const int64_t xy = smax * spectrum_row_cap(L) * (int64_t)cs;
-  const int64_t tb = smax * L.tslice * (int64_t)cs;
-  const int64_t vol = (int64_t)L.max_batch * L.nz * L.ny * L.nx * (int64_t)L.rsize;
-  const int64_t dat = (int64_t)L.max_batch * L.nt * L.ny * L.nx * (int64_t)L.rsize;
-  const int64_t red = sizeof(double) * (int64_t)std::max(kReduceBlocks, c2r_partials_bound(L));
-  const int64_t twiddles = (int64_t)(L.px + L.py) * (int64_t)cs;
-  return 2 * xy + tb + 5 * vol + 3 * dat + red + twiddles + 6 * 8 * (int64_t)L.max_batch + 1024;
-}
+// FISTA momentum / residual history kept in the workspace: 4096 iterations
+// per solve (a plan that allocates its own memory grows it on demand).
+constexpr int kHistCap = 4097;
+constexpr size_t kWsAlign = 256;
 
-int alloc_workspace(pat_plan* pp) {
+// Walks the workspace regions of a plan in their fixed order, each aligned to
+// 256 bytes; with `base` the plan's pointers are set to their regions.
+// `with_io` adds the host-pointer staging buffers. Returns the bytes spanned.
+size_t ws_walk(pat_plan* pp, unsigned char* base, bool with_io) {
   Plan& p = pp->p;
   PlanExt& x = pp->x;
   const Layout& L = p.L;
@@ -150,30 +174,82 @@ int alloc_workspace(pat_plan* pp) {
   const size_t tb = (size_t)smax * L.tslice * cs;
   const size_t vol = (size_t)L.max_batch * L.nz * L.ny * L.nx * L.rsize;
   const size_t dat = (size_t)L.max_batch * L.nt * L.ny * L.nx * L.rsize;
-  x.c2r_partials = std::max(kReduceBlocks, c2r_partials_bound(L));
-  PAT_CUDA(cudaMalloc(&p.X, xy));
-  PAT_CUDA(cudaMalloc(&p.Y, xy));
-  PAT_CUDA(cudaMalloc(&p.T, tb));
-  PAT_CUDA(cudaMalloc(&p.vol_a, vol));
-  PAT_CUDA(cudaMalloc(&p.vol_b, vol));
-  PAT_CUDA(cudaMalloc(&p.vol_c, vol));
-  PAT_CUDA(cudaMalloc(&p.dat_a, dat));
-  PAT_CUDA(cudaMalloc(&p.dat_b, dat));
-  PAT_CUDA(cudaMalloc(&p.red, sizeof(double) * x.c2r_partials));
-  PAT_CUDA(cudaMalloc(&x.res, sizeof(double) * 8));
-  PAT_CUDA(cudaMalloc(&x.scal, sizeof(double) * 2));
-  PAT_CUDA(cudaMalloc(&p.iter_dev, 3 * sizeof(int)));
-  PAT_CUDA(cudaMemset(p.iter_dev, 0, 3 * sizeof(int)));
+  const int partials = std::max(kReduceBlocks, c2r_partials_bound(L));
   const size_t sb = sizeof(double) * L.max_batch;
-  PAT_CUDA(cudaMalloc(&x.slots.t, sb));
-  PAT_CUDA(cudaMalloc(&x.slots.beta, sb));
-  PAT_CUDA(cudaMalloc(&x.slots.invL, sb));
-  PAT_CUDA(cudaMalloc(&x.slots.lamL, sb));
-  PAT_CUDA(cudaMalloc(&x.slots.r2, sb));
-  PAT_CUDA(cudaMalloc(&x.slots.k, sizeof(int) * L.max_batch));
-  PAT_CUDA(cudaStreamCreateWithFlags(&x.cap, cudaStreamNonBlocking));
-  p.ws_bytes = 2 * xy + tb + 3 * vol + 2 * dat + sizeof(double) * (x.c2r_partials + 10);
-  return PAT_OK;
+  size_t off = 0;
+  auto take = [&](auto** dst, size_t bytes) {
+    if (base) *dst = reinterpret_cast<std::remove_pointer_t<decltype(dst)>>(base + off);
+    off += (bytes + kWsAlign - 1) / kWsAlign * kWsAlign;
+  };
+  take(&p.twx, (size_t)L.px * cs);
+  take(&p.twy, (size_t)L.py * cs);
+  take(&p.X, xy);
+  take(&p.Y, xy);
+  take(&p.T, tb);
+  take(&p.vol_a, vol);
+  take(&p.vol_b, vol);
+  take(&p.vol_c, vol);
+  take(&p.dat_a, dat);
+  take(&p.dat_b, dat);
+  take(&p.red, sizeof(double) * partials);
+  take(&x.res, sizeof(double) * 8);
+  take(&x.scal, sizeof(double) * 2);
+  take(&p.iter_dev, 3 * sizeof(int));
+  take(&x.slots.t, sb);
+  take(&x.slots.beta, sb);
+  take(&x.slots.invL, sb);
+  take(&x.slots.lamL, sb);
+  take(&x.slots.r2, sb);
+  take(&x.slots.k, sizeof(int) * L.max_batch);
+  take(&p.betas, sizeof(double) * kHistCap);
+  take(&p.r2_dev, sizeof(double) * kHistCap);
+  take(&p.tc_err, sizeof(int));
+  if (with_io) {
+    take(&x.io_obj[0], vol);
+    take(&x.io_obj[1], vol);
+    take(&x.io_dat, dat);
+  }
+  if (base) {
+    x.c2r_partials = partials;
+    p.betas_cap = p.r2_cap = kHistCap;
+  }
+  return off;
+}
+
+// Device bytes of a plan's workspace for layout L (with_io: including the
+// host-pointer staging buffers).
+int64_t workspace_bytes(const Layout& L, bool with_io) {
+  pat_plan tmp;
+  tmp.p.L = L;
+  return (int64_t)ws_walk(&tmp, nullptr, with_io);
+}
+
+// Carves the workspace from `user` (caller-owned device memory of ws_bytes)
+// or from one block the plan allocates, and initialises what must start at
+// zero or at fixed values.
+int setup_workspace(pat_plan* pp, void* user, size_t ws_bytes) {
+  Plan& p = pp->p;
+  const bool ext = user != nullptr;
+  const size_t need = ws_walk(pp, nullptr, ext);
+  if (ext) {
+    if (!is_device_ptr(user)) return fail(PAT_ERR_ARG, "workspace is not device memory");
+    if (reinterpret_cast<uintptr_t>(user) % kWsAlign)
+      return fail(PAT_ERR_ARG, "workspace must be 256-byte aligned");
+    if (ws_bytes < need)
+      return fail(PAT_ERR_ARG, "workspace smaller than pat_workspace_size: need " +
+                                   std::to_string(need) + " bytes");
+    p.ws_base = static_cast<unsigned char*>(user);
+    p.ws_external = true;
+  } else {
+    PAT_CUDA(dev_alloc(&p.ws_base, need));
+  }
+  p.ws_cap = ext ? ws_bytes : need;
+  p.ws_used = ws_walk(pp, p.ws_base, ext);
+  p.ws_bytes = p.ws_used;
+  PAT_CUDA(cudaMemset(p.iter_dev, 0, 3 * sizeof(int)));
+  PAT_CUDA(cudaMemset(p.tc_err, 0, sizeof(int)));
+  PAT_CUDA(cudaStreamCreateWithFlags(&pp->x.cap, cudaStreamNonBlocking));
+  return upload_twiddles(p);
 }
 
 int ensure_io(pat_plan* pp) {
@@ -182,13 +258,22 @@ int ensure_io(pat_plan* pp) {
   const Layout& L = pp->p.L;
   const size_t vol = (size_t)L.max_batch * L.nz * L.ny * L.nx * L.rsize;
   const size_t dat = (size_t)L.max_batch * L.nt * L.ny * L.nx * L.rsize;
-  PAT_CUDA(cudaMalloc(&x.io_obj[0], vol));
-  PAT_CUDA(cudaMalloc(&x.io_obj[1], vol));
-  PAT_CUDA(cudaMalloc(&x.io_dat, dat));
+  x.io_heap = true;
+  PAT_CUDA(dev_alloc(&x.io_obj[0], vol));
+  PAT_CUDA(dev_alloc(&x.io_obj[1], vol));
+  PAT_CUDA(dev_alloc(&x.io_dat, dat));
+  pp->p.ws_bytes += 2 * vol + dat;
   return PAT_OK;
 }
 
-int create_common(const pat_geometry* g, pat_plan** out, pat_plan** pp_out) {
+// Arms the allocation fault injector for the duration of a plan creation.
+struct AllocHook {
+  AllocHook() { alloc_hook_arm(); }
+  ~AllocHook() { alloc_hook_disarm(); }
+};
+
+int create_common(const pat_geometry* g, void* ws, size_t ws_bytes, pat_plan** out,
+                  pat_plan** pp_out) {
   if (!out) return fail(PAT_ERR_ARG, "out is NULL");
   *out = nullptr;
   int rc = validate(g);
@@ -196,7 +281,8 @@ int create_common(const pat_geometry* g, pat_plan** out, pat_plan** pp_out) {
   pat_plan* pp = new (std::nothrow) pat_plan();
   if (!pp) return fail(PAT_ERR_OOM, "host allocation of the plan failed");
   pp->p.L = make_layout(g);
-  if ((rc = upload_twiddles(pp->p)) != PAT_OK || (rc = alloc_workspace(pp)) != PAT_OK) {
+  pp->p.tc_spin = kTcSpinDefault;
+  if ((rc = setup_workspace(pp, ws, ws_bytes)) != PAT_OK) {
     free_plan(pp);
     return rc;
   }
@@ -213,10 +299,8 @@ int build_tensor_tables(pat_plan* pp, int flags, cudaStream_t s) {
                 "PAT_FLAG_BF16_SPLIT needs a real single-precision table, nz = 128 and nt a "
                 "multiple of 128 up to 512");
   const size_t one = tc_table_bytes(p.L);
-  PAT_CUDA(cudaMalloc(&p.tc_fwd, one));
-  PAT_CUDA(cudaMalloc(&p.tc_adj, one));
-  PAT_CUDA(cudaMalloc(&p.tc_err, sizeof(int)));
-  PAT_CUDA(cudaMemsetAsync(p.tc_err, 0, sizeof(int), s));
+  PAT_CUDA(dev_alloc(&p.tc_fwd, one));
+  PAT_CUDA(dev_alloc(&p.tc_adj, one));
   PAT_CUDA(tc_build_tables(p, p.tc_fwd, p.tc_adj, s));
   PAT_CUDA(cudaStreamSynchronize(s));
   p.tc_bytes = 2 * one;
@@ -341,8 +425,9 @@ int any_host(std::initializer_list<const void*> ptrs) {
   return 0;
 }
 
-// Fixed-seed start vector of the internal step-size estimate (splitmix64 ->
-// uniform [-1, 1)); any start with a component along the top singular vector works.
+// Seeded start vector of the power iteration (splitmix64 of Steele, Lea &
+// Flood 2014 on the counter seed + (i + 1) * golden gamma -> uniform [-1, 1));
+// any start with a component along the top singular vector works.
 template <typename R>
 __global__ void k_fill_hash(R* v, int64_t n, unsigned long long seed) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -353,6 +438,17 @@ __global__ void k_fill_hash(R* v, int64_t n, unsigned long long seed) {
     z ^= z >> 31;
     v[i] = (R)((double)(z >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0);
   }
+}
+
+int fill_seeded(pat_plan* pp, uint64_t seed, cudaStream_t s) {
+  Plan& p = pp->p;
+  const int64_t n = (int64_t)obj_elems(p.L, 1);
+  if (p.L.fp64)
+    k_fill_hash<double><<<64, 256, 0, s>>>(static_cast<double*>(p.vol_a), n, seed);
+  else
+    k_fill_hash<float><<<64, 256, 0, s>>>(static_cast<float*>(p.vol_a), n, seed);
+  PAT_CUDA(cudaGetLastError());
+  return PAT_OK;
 }
 
 // Power iteration on the plan's buffers: v in vol_a (normalised here first).
@@ -438,14 +534,16 @@ extern "C" {
 
 const char* pat_last_error(void) { return pat::g_err.c_str(); }
 
-int pat_plan_create(const pat_geometry* g, const void* table, pat_table_format fmt,
-                    pat_stream stream, pat_plan** out) {
+int pat_plan_create_with_workspace(const pat_geometry* g, const void* table, pat_table_format fmt,
+                                   void* workspace, size_t ws_bytes, pat_stream stream,
+                                   pat_plan** out) {
   PAT_GUARD_BEGIN
+  AllocHook hook;
   if (!table) return fail(PAT_ERR_ARG, "table is NULL");
   if (fmt < PAT_TABLE_SPATIAL_F64 || fmt > PAT_TABLE_SPECTRAL_C64)
     return fail(PAT_ERR_ARG, "unknown table format");
   pat_plan* pp = nullptr;
-  int rc = create_common(g, out, &pp);
+  int rc = create_common(g, workspace, ws_bytes, out, &pp);
   if (rc != PAT_OK) return rc;
   rc = build_table_from_source(pp->p, table, fmt, (g->flags & PAT_FLAG_FORCE_COMPLEX) != 0,
                                (g->flags & PAT_FLAG_NO_FOLD) == 0, (cudaStream_t)stream);
@@ -459,16 +557,23 @@ int pat_plan_create(const pat_geometry* g, const void* table, pat_table_format f
   PAT_GUARD_END
 }
 
-int pat_plan_create_kspace(const pat_geometry* g, const pat_medium* m, pat_stream stream,
-                           pat_plan** out) {
+int pat_plan_create(const pat_geometry* g, const void* table, pat_table_format fmt,
+                    pat_stream stream, pat_plan** out) {
+  return pat_plan_create_with_workspace(g, table, fmt, nullptr, 0, stream, out);
+}
+
+int pat_plan_create_kspace_with_workspace(const pat_geometry* g, const pat_medium* m,
+                                          void* workspace, size_t ws_bytes, pat_stream stream,
+                                          pat_plan** out) {
   PAT_GUARD_BEGIN
+  AllocHook hook;
   if (!m) return fail(PAT_ERR_ARG, "medium is NULL");
   if (!(m->c > 0 && m->dx > 0 && m->dy > 0 && m->dz > 0 && m->dt > 0))
     return fail(PAT_ERR_ARG, "medium: c, dx, dy, dz, dt must be > 0");
   if (m->z0 < 0 || !pow2_in(m->mz, 2, 1 << 16) || m->mz <= m->z0 + (g ? g->nz : 0))
     return fail(PAT_ERR_ARG, "medium: mz must be a power of two > z0 + nz, z0 >= 0");
   pat_plan* pp = nullptr;
-  int rc = create_common(g, out, &pp);
+  int rc = create_common(g, workspace, ws_bytes, out, &pp);
   if (rc != PAT_OK) return rc;
   rc = build_table_kspace(pp->p, *m, (g->flags & PAT_FLAG_FORCE_COMPLEX) != 0,
                           (g->flags & PAT_FLAG_NO_FOLD) == 0, (cudaStream_t)stream);
@@ -478,6 +583,36 @@ int pat_plan_create_kspace(const pat_geometry* g, const pat_medium* m, pat_strea
     return rc;
   }
   *out = pp;
+  return PAT_OK;
+  PAT_GUARD_END
+}
+
+int pat_plan_create_kspace(const pat_geometry* g, const pat_medium* m, pat_stream stream,
+                           pat_plan** out) {
+  return pat_plan_create_kspace_with_workspace(g, m, nullptr, 0, stream, out);
+}
+
+int64_t pat_workspace_size(const pat_geometry* g) {
+  PAT_GUARD_BEGIN
+  const int rc = validate(g);
+  if (rc != PAT_OK) return rc;
+  return workspace_bytes(make_layout(g), true);
+  PAT_GUARD_END
+}
+
+int64_t pat_debug_live_allocations(void) { return g_live_allocs.load(); }
+
+int pat_plan_set_wait_limit(pat_plan* plan, int64_t polls) {
+  PAT_GUARD_BEGIN
+  if (!plan) return fail(PAT_ERR_ARG, "plan is NULL");
+  if (polls > 0xFFFFFFFFll) return fail(PAT_ERR_ARG, "polls must be < 2^32");
+  const int64_t v = polls < 0 ? kTcSpinDefault : polls;
+  if (v != plan->p.tc_spin) {
+    // the cached graphs hold the old limit in their kernel parameters
+    PAT_CUDA(cudaDeviceSynchronize());
+    drop_graphs(plan->p);
+    plan->p.tc_spin = v;
+  }
   return PAT_OK;
   PAT_GUARD_END
 }
@@ -502,7 +637,7 @@ int pat_plan_estimate(const pat_geometry* g, int real_table, int64_t* table_byte
   *table_bytes = (int64_t)L.table_bytes;
   if ((g->flags & PAT_FLAG_BF16_SPLIT) && tc_supported(L))
     *table_bytes += 2 * (int64_t)tc_table_bytes(L);
-  *workspace = workspace_bytes(L);
+  *workspace = workspace_bytes(L, true);
   return PAT_OK;
   PAT_GUARD_END
 }
@@ -516,6 +651,7 @@ int pat_plan_info(const pat_plan* plan, pat_plan_info_t* info) {
   info->bins_padded = p.L.Kpad;
   info->table_bytes = (int64_t)p.L.table_bytes;
   info->workspace_bytes = (int64_t)p.ws_bytes;
+  info->workspace_external = p.ws_external ? 1 : 0;
   info->table_max_abs = p.table_max_abs;
   info->table_max_imag = p.table_max_imag;
   info->tensor_table_bytes = (int64_t)p.tc_bytes;
@@ -572,7 +708,6 @@ int pat_plan_check(pat_plan* plan) {
   PAT_GUARD_BEGIN
   if (!plan) return fail(PAT_ERR_ARG, "plan is NULL");
   PAT_CUDA(cudaDeviceSynchronize());
-  if (!plan->p.tc_err) return PAT_OK;
   int h = 0;
   PAT_CUDA(cudaMemcpy(&h, plan->p.tc_err, sizeof(int), cudaMemcpyDeviceToHost));
   if (h) {
@@ -674,6 +809,18 @@ int pat_power_norm(pat_plan* plan, const void* v0, int iters, double* L_out, pat
   PAT_GUARD_END
 }
 
+int pat_power_norm_seed(pat_plan* plan, int iters, uint64_t seed, double* L_out,
+                        pat_stream stream) {
+  PAT_GUARD_BEGIN
+  int rc = check_call(plan, 1);
+  if (rc != PAT_OK) return rc;
+  if (!L_out || iters < 1) return fail(PAT_ERR_ARG, "L_out NULL or iters < 1");
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((rc = fill_seeded(plan, seed, s)) != PAT_OK) return rc;
+  return power_dev(plan, iters, L_out, s);
+  PAT_GUARD_END
+}
+
 int pat_fista_solve(pat_plan* plan, const void* y, void* x, int batch,
                     const pat_fista_params* prm, pat_fista_report* report, pat_stream stream) {
   PAT_GUARD_BEGIN
@@ -688,12 +835,7 @@ int pat_fista_solve(pat_plan* plan, const void* y, void* x, int batch,
   cudaStream_t s = (cudaStream_t)stream;
   double Lc = prm->L;
   if (Lc <= 0) {
-    const int64_t n = (int64_t)obj_elems(L, 1);
-    if (L.fp64)
-      k_fill_hash<double><<<64, 256, 0, s>>>(static_cast<double*>(p.vol_a), n, 0x5EEDull);
-    else
-      k_fill_hash<float><<<64, 256, 0, s>>>(static_cast<float*>(p.vol_a), n, 0x5EEDull);
-    PAT_CUDA(cudaGetLastError());
+    if ((rc = fill_seeded(plan, 0x5EEDull, s)) != PAT_OK) return rc;
     if ((rc = power_dev(plan, prm->power_iters, &Lc, s)) != PAT_OK) return rc;
     Lc *= 1.01;
   }
@@ -705,16 +847,24 @@ int pat_fista_solve(pat_plan* plan, const void* y, void* x, int batch,
   // momentum coefficients beta_k = (t_k - 1) / t_{k+1} (FP64 on the host)
   const int iters = prm->iters;
   if (p.betas_cap < iters + 1) {
-    cudaFree(p.betas);
-    cudaFree(p.r2_dev);
+    if (p.ws_external)
+      return fail(PAT_ERR_ARG, "a plan on caller-owned workspace runs at most " +
+                                   std::to_string(p.betas_cap - 1) + " FISTA iterations per call");
+    // grow the history outside the workspace (graphs captured the old pointers)
+    PAT_CUDA(cudaStreamSynchronize(s));
+    drop_graphs(p);
+    if (p.hist_heap) {
+      dev_free(p.betas);
+      dev_free(p.r2_dev);
+    }
     p.betas = nullptr;
     p.r2_dev = nullptr;
     p.betas_cap = p.r2_cap = 0;
-    const int cap = std::max(iters + 1, 128);
-    PAT_CUDA(cudaMalloc(&p.betas, sizeof(double) * cap));
-    PAT_CUDA(cudaMalloc(&p.r2_dev, sizeof(double) * cap));
+    p.hist_heap = true;
+    const int cap = iters + 1;
+    PAT_CUDA(dev_alloc(&p.betas, sizeof(double) * cap));
+    PAT_CUDA(dev_alloc(&p.r2_dev, sizeof(double) * cap));
     p.betas_cap = p.r2_cap = cap;
-    drop_graphs(p);  // graphs captured the old pointers
   }
   std::vector<double> betas(iters + 1, 0.0);
   double t = 1.0;

@@ -105,8 +105,16 @@ extern "C" int pat_spectrum_noalloc(const float* in, int nx, int ny, int px, int
                                    std::to_string(kScratchBytes) + " bytes; use fewer slices per call");
     if (slices == 0) return PAT_OK;
     if (!in || !out) return fail(PAT_ERR_ARG, "in or out is NULL");
-    if (!is_device_ptr(in) || !is_device_ptr(out))
-      return fail(PAT_ERR_ARG, "pat_spectrum_noalloc takes device arrays");
+    // the scratch, the twiddles and the launch belong to the current device,
+    // so both arrays must live there (there is no plan to tie them to)
+    int dev = -1;
+    PAT_CUDA(cudaGetDevice(&dev));
+    const int din = device_of(in), dout = device_of(out);
+    if (din < 0 || dout < 0) return fail(PAT_ERR_ARG, "pat_spectrum_noalloc takes device arrays");
+    if (din != dev || dout != dev)
+      return fail(PAT_ERR_ARG, "pat_spectrum_noalloc: in and out must be on the current device (" +
+                                   std::to_string(dev) + "); they are on " + std::to_string(din) +
+                                   " and " + std::to_string(dout));
     DeviceSetup* s = nullptr;
     int rc = setup_current_device(&s);
     if (rc != PAT_OK) return rc;

@@ -144,6 +144,23 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t s
   return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
 }
 
+// ---- device allocations --------------------------------------------------------
+// Every device allocation of a plan (its table, maps, workspace and the
+// temporaries of table preparation) goes through dev_alloc / dev_free, which
+// keep a count of live allocations (pat_debug_live_allocations). At the start
+// of plan creation the environment variable PAT_DEBUG_FAIL_ALLOC = n (n >= 1)
+// arms a host-side fault injector on the calling thread: the n-th allocation
+// after that returns cudaErrorMemoryAllocation without allocating (testing the
+// PAT_ERR_OOM and clean-up paths; no device fault involved).
+cudaError_t dev_alloc_raw(void** p, size_t bytes);
+template <typename T>
+cudaError_t dev_alloc(T** p, size_t bytes) {
+  return dev_alloc_raw(reinterpret_cast<void**>(p), bytes);
+}
+void dev_free(void* p);  // NULL is a no-op
+void alloc_hook_arm();   // reads PAT_DEBUG_FAIL_ALLOC
+void alloc_hook_disarm();
+
 struct Graph;  // CUDA-graph cache (api.cu)
 
 struct Plan {
@@ -164,12 +181,23 @@ struct Plan {
   double* red = nullptr;  // reduction scratch: partials + results (see kReduce*)
   double* betas = nullptr;  // FISTA momentum coefficients per iteration
   int betas_cap = 0;
+  bool hist_heap = false;   // betas / r2_dev were allocated outside the workspace
   int* iter_dev = nullptr;  // [0] FISTA iteration counter (graph replay), [1] block counter
                             // of the FISTA step pass, [2] block counter of the residual pass
   double* r2_dev = nullptr; // FISTA residual norms per iteration
   int r2_cap = 0;
   Graph* graphs = nullptr;
   size_t ws_bytes = 0;
+  // Workspace arena: every per-call buffer above (twiddles, X, Y, T, the
+  // object / data buffers, reductions, scalars, slot state, FISTA history, the
+  // error flag of the tensor kernels, and the host-pointer staging when the
+  // caller supplied the workspace) is carved from one block, either allocated
+  // by the plan or owned by the caller (never freed by the plan).
+  unsigned char* ws_base = nullptr;
+  size_t ws_cap = 0, ws_used = 0;
+  bool ws_external = false;
+  // Pipeline wait limit of the tensor-core kernels (polls per wait).
+  int64_t tc_spin = 0;
   // D4 folding maps (device): bins of each representative (-1 = none), and
   // the representative of each bin
   int* fold_members = nullptr;  // [Upad][4]
@@ -212,6 +240,7 @@ struct Slots {
 struct PlanExt {
   void* io_obj[2] = {nullptr, nullptr};  // host-pointer staging (objects)
   void* io_dat = nullptr;                // host-pointer staging (data)
+  bool io_heap = false;                  // staging allocated on first use (not in the arena)
   double* res = nullptr;                 // device scalars: [0] dot, [1] r2 current, [2] norm
   double* scal = nullptr;                // device scalars: [0] 1/L, [1] lambda/L
   cudaStream_t cap = nullptr;            // private stream for graph capture
@@ -327,6 +356,9 @@ cudaError_t tc_build_tables(const Plan& p, void* fwd, void* adj, cudaStream_t s)
 cudaError_t tc_contract(const Plan& p, const void* tables_fwd, const void* tables_adj,
                         const void* in, void* out, int batch, bool adjoint, int* err,
                         cudaStream_t s);
+// Default pipeline wait limit of the tensor-core kernels (polls of
+// mbarrier.try_wait per wait; a few seconds).
+constexpr int64_t kTcSpinDefault = int64_t(1) << 22;
 
 // Table construction (table.cu). Both allocate p.table and set the
 // representation (real or complex) of p.L.
@@ -335,6 +367,8 @@ int build_table_from_source(Plan& p, const void* table, pat_table_format fmt, bo
 int build_table_kspace(Plan& p, const pat_medium& m, bool force_complex, bool allow_fold,
                        cudaStream_t s);
 bool is_device_ptr(const void* p);
+// Ordinal of the device holding `p`, or -1 if it is not device memory.
+int device_of(const void* p);
 
 // Representation-dependent parts of the layout.
 inline void set_representation(Layout& L, bool real, bool fold = false) {

@@ -256,7 +256,7 @@ int apply_sensor_response(Plan& p, const double* r, int nr, cudaStream_t s) {
   const int64_t blocks = L.fold ? L.nub : L.nkb;
   const int64_t inner = (int64_t)L.nzg * 32 * 16 / (int64_t)L.rsize;
   double* rd = nullptr;
-  PAT_CUDA(cudaMalloc(&rd, sizeof(double) * nr));
+  PAT_CUDA(dev_alloc(&rd, sizeof(double) * nr));
   cudaError_t e = cudaMemcpyAsync(rd, r, sizeof(double) * nr, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) {
     const int g = grid_for(blocks * inner);
@@ -269,7 +269,7 @@ int apply_sensor_response(Plan& p, const double* r, int nr, cudaStream_t s) {
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  cudaFree(rd);
+  dev_free(rd);
   if (e != cudaSuccess) return cuda_fail(e, "applying the sensor response");
   return PAT_OK;
 }
@@ -308,11 +308,11 @@ int build_fold_maps(Plan& p, std::vector<int>* rep_bins) {
     rep_bins->resize((size_t)L.U);
     for (int64_t u = 0; u < L.U; ++u) (*rep_bins)[u] = members[4 * u];
   }
-  PAT_CUDA(cudaMalloc(&p.fold_slot, slot.size() * sizeof(int)));
+  PAT_CUDA(dev_alloc(&p.fold_slot, slot.size() * sizeof(int)));
   PAT_CUDA(cudaMemcpy(p.fold_slot, slot.data(), slot.size() * sizeof(int),
                       cudaMemcpyHostToDevice));
-  PAT_CUDA(cudaMalloc(&p.fold_members, members.size() * sizeof(int)));
-  PAT_CUDA(cudaMalloc(&p.fold_rep, rep.size() * sizeof(int)));
+  PAT_CUDA(dev_alloc(&p.fold_members, members.size() * sizeof(int)));
+  PAT_CUDA(dev_alloc(&p.fold_rep, rep.size() * sizeof(int)));
   PAT_CUDA(cudaMemcpy(p.fold_members, members.data(), members.size() * sizeof(int),
                       cudaMemcpyHostToDevice));
   PAT_CUDA(cudaMemcpy(p.fold_rep, rep.data(), rep.size() * sizeof(int), cudaMemcpyHostToDevice));
@@ -326,6 +326,15 @@ bool is_device_ptr(const void* p) {
     return false;
   }
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int device_of(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) ? a.device : -1;
 }
 
 int build_table_from_source(Plan& p, const void* table, pat_table_format fmt, bool force_complex,
@@ -347,12 +356,12 @@ int build_table_from_source(Plan& p, const void* table, pat_table_format fmt, bo
   void *stage = nullptr, *spec = nullptr, *Tprep = nullptr, *twx = nullptr, *twy = nullptr;
   unsigned long long* stats = nullptr;
   auto cleanup = [&]() {
-    cudaFree(stage);
-    cudaFree(spec);
-    cudaFree(Tprep);
-    cudaFree(twx);
-    cudaFree(twy);
-    cudaFree(stats);
+    dev_free(stage);
+    dev_free(spec);
+    dev_free(Tprep);
+    dev_free(twx);
+    dev_free(twy);
+    dev_free(stats);
   };
 #define PREP_CUDA(call)               \
   do {                                \
@@ -364,8 +373,8 @@ int build_table_from_source(Plan& p, const void* table, pat_table_format fmt, bo
     }                                 \
   } while (0)
 
-  if (!on_dev) PREP_CUDA(cudaMalloc(&stage, (size_t)ntc * plane_src * esz_src));
-  PREP_CUDA(cudaMalloc(&stats, 2 * sizeof(unsigned long long)));
+  if (!on_dev) PREP_CUDA(dev_alloc(&stage, (size_t)ntc * plane_src * esz_src));
+  PREP_CUDA(dev_alloc(&stats, 2 * sizeof(unsigned long long)));
   PREP_CUDA(cudaMemsetAsync(stats, 0, 2 * sizeof(unsigned long long), s));
 
   // A transform-only view of the plan in the source precision: the same
@@ -374,18 +383,18 @@ int build_table_from_source(Plan& p, const void* table, pat_table_format fmt, bo
   prep.L = L;
   prep.L.fp64 = src64;
   if (spatial) {
-    PREP_CUDA(cudaMalloc(&spec, (size_t)ntc * Kfull * csz));
-    PREP_CUDA(cudaMalloc(&Tprep, (size_t)ntc * (L.px / 2 + 1) * L.py * csz));
+    PREP_CUDA(dev_alloc(&spec, (size_t)ntc * Kfull * csz));
+    PREP_CUDA(dev_alloc(&Tprep, (size_t)ntc * (L.px / 2 + 1) * L.py * csz));
     std::vector<double> wx = twiddles(L.px), wy = twiddles(L.py);
     if (src64) {
-      PREP_CUDA(cudaMalloc(&twx, wx.size() * 8));
-      PREP_CUDA(cudaMalloc(&twy, wy.size() * 8));
+      PREP_CUDA(dev_alloc(&twx, wx.size() * 8));
+      PREP_CUDA(dev_alloc(&twy, wy.size() * 8));
       PREP_CUDA(cudaMemcpy(twx, wx.data(), wx.size() * 8, cudaMemcpyHostToDevice));
       PREP_CUDA(cudaMemcpy(twy, wy.data(), wy.size() * 8, cudaMemcpyHostToDevice));
     } else {
       std::vector<float> fx(wx.begin(), wx.end()), fy(wy.begin(), wy.end());
-      PREP_CUDA(cudaMalloc(&twx, fx.size() * 4));
-      PREP_CUDA(cudaMalloc(&twy, fy.size() * 4));
+      PREP_CUDA(dev_alloc(&twx, fx.size() * 4));
+      PREP_CUDA(dev_alloc(&twy, fy.size() * 4));
       PREP_CUDA(cudaMemcpy(twx, fx.data(), fx.size() * 4, cudaMemcpyHostToDevice));
       PREP_CUDA(cudaMemcpy(twy, fy.data(), fy.size() * 4, cudaMemcpyHostToDevice));
     }
@@ -445,7 +454,7 @@ int build_table_from_source(Plan& p, const void* table, pat_table_format fmt, bo
   set_representation(L, !force_complex && mi <= 1e-6 * p.table_max_abs);
 
   // Pass 2: fill the resident table.
-  PREP_CUDA(cudaMalloc(&p.table, L.table_bytes));
+  PREP_CUDA(dev_alloc(&p.table, L.table_bytes));
   PREP_CUDA(cudaMemsetAsync(p.table, 0, L.table_bytes, s));
   const double scale = 1.0 / ((double)L.px * (double)L.py);
   for (int z = 0; z < L.nz; ++z)
@@ -465,7 +474,7 @@ int build_table_from_source(Plan& p, const void* table, pat_table_format fmt, bo
     int rc = build_fold_maps(p, nullptr);
     if (rc != PAT_OK) return rc;
     unsigned long long* dev_max = nullptr;
-    PAT_CUDA(cudaMalloc(&dev_max, sizeof(unsigned long long)));
+    PAT_CUDA(dev_alloc(&dev_max, sizeof(unsigned long long)));
     cudaError_t e = cudaMemsetAsync(dev_max, 0, sizeof(unsigned long long), s);
     if (e == cudaSuccess) {
       k_fold_check<<<grid_for(L.K * L.nt * L.nzg * 4), 256, 0, s>>>(
@@ -476,7 +485,7 @@ int build_table_from_source(Plan& p, const void* table, pat_table_format fmt, bo
     unsigned long long hm = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&hm, dev_max, sizeof(hm), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    cudaFree(dev_max);
+    dev_free(dev_max);
     if (e != cudaSuccess) return cuda_fail(e, "checking the D4 symmetry of the table");
     double dmax;
     memcpy(&dmax, &hm, 8);
@@ -485,22 +494,22 @@ int build_table_from_source(Plan& p, const void* table, pat_table_format fmt, bo
       Layout F = L;
       set_representation(F, true, true);
       void* folded = nullptr;
-      PAT_CUDA(cudaMalloc(&folded, F.table_bytes));
+      PAT_CUDA(dev_alloc(&folded, F.table_bytes));
       k_fold_gather<<<grid_for(F.Upad * F.nt * F.nzg), 256, 0, s>>>(
           static_cast<const float4*>(p.table), static_cast<float4*>(folded), p.fold_members, F.U,
           F.Upad, F.nt, F.nzg);
       e = cudaGetLastError();
       if (e == cudaSuccess) e = cudaStreamSynchronize(s);
       if (e != cudaSuccess) {
-        cudaFree(folded);
+        dev_free(folded);
         return cuda_fail(e, "folding the table");
       }
-      cudaFree(p.table);
+      dev_free(p.table);
       p.table = folded;
       L = F;
     } else {
-      cudaFree(p.fold_members);
-      cudaFree(p.fold_rep);
+      dev_free(p.fold_members);
+      dev_free(p.fold_rep);
       p.fold_members = p.fold_rep = nullptr;
     }
   }
@@ -553,8 +562,8 @@ int build_table_kspace(Plan& p, const pat_medium& m, bool force_complex, bool al
   unsigned long long* u_d = nullptr;
   float* W_d = nullptr;
   auto cleanup = [&]() {
-    cudaFree(u_d);
-    cudaFree(W_d);
+    dev_free(u_d);
+    dev_free(W_d);
   };
 #define GEN_CUDA(call)                \
   do {                                \
@@ -565,11 +574,11 @@ int build_table_kspace(Plan& p, const pat_medium& m, bool force_complex, bool al
       return rc_;                     \
     }                                 \
   } while (0)
-  GEN_CUDA(cudaMalloc(&u_d, u.size() * sizeof(unsigned long long)));
-  GEN_CUDA(cudaMalloc(&W_d, W.size() * sizeof(float)));
+  GEN_CUDA(dev_alloc(&u_d, u.size() * sizeof(unsigned long long)));
+  GEN_CUDA(dev_alloc(&W_d, W.size() * sizeof(float)));
   GEN_CUDA(cudaMemcpy(u_d, u.data(), u.size() * sizeof(unsigned long long), cudaMemcpyHostToDevice));
   GEN_CUDA(cudaMemcpy(W_d, W.data(), W.size() * sizeof(float), cudaMemcpyHostToDevice));
-  GEN_CUDA(cudaMalloc(&p.table, L.table_bytes));
+  GEN_CUDA(dev_alloc(&p.table, L.table_bytes));
   GEN_CUDA(cudaMemsetAsync(p.table, 0, L.table_bytes, s));
   const size_t smem = sizeof(float) * ((size_t)M * L.nz + (size_t)M * 32);
   if (smem > 227 * 1024) {

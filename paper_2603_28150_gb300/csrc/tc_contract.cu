@@ -45,7 +45,9 @@ constexpr int kTileBytes = kTile * kTile * 2;  // 32 KB of BF16
 constexpr int kLBO = 128;                // bytes between K-adjacent core matrices
 constexpr int kSBO = (kTile / 8) * 128;  // bytes between M/N-adjacent core matrices (2048)
 constexpr int kBBytes = kN * kTile * 2;  // one 32 x 128 B-operand chunk (8 KB)
-constexpr uint32_t kSpinLimit = 1u << 26;
+// Teardown drains (copies and MMAs still in flight after an abort) wait at
+// most this long in total, measured on the global timer.
+constexpr uint64_t kDrainNs = 2000000000ull;
 
 // -------------------------------------------------------------------- PTX helpers
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -69,13 +71,27 @@ __device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait for the phase with the given parity; false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  for (uint32_t i = 0; i < kSpinLimit; ++i) {
+// Bounded pipeline wait for the phase with the given parity: at most `limit`
+// tests (mbarrier.try_wait itself suspends the thread for a bounded time, so
+// the loop polls without sleeping); false on timeout. limit = 0 gives up at
+// once (the plan's wait limit set to 0 exercises the abort path).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t limit) {
+  for (uint32_t i = 0; i < limit; ++i)
     if (mbar_test(bar, parity)) return true;
-    if (i > 64) __nanosleep(64);
-  }
   return false;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+// Teardown wait: until the phase completes or the global timer passes
+// `deadline` (shared by all drain waits of a thread, so once it has passed the
+// remaining drains return at once).
+__device__ __forceinline__ bool drain_wait(uint64_t* bar, uint32_t parity, uint64_t deadline) {
+  while (!mbar_test(bar, parity))
+    if (global_ns() > deadline) return false;
+  return true;
 }
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
   asm volatile(
@@ -169,6 +185,7 @@ struct Params {
   int mtiles;        // output row tiles: nt/128 (fwd) or 1 (adj)
   int kchunks;       // K chunks of 128: 1 (fwd) or nt/128 (adj)
   int* err;          // set to 1 on a timed-out wait
+  uint32_t spin;     // pipeline wait limit (tests per wait)
 };
 
 // G bins per group, S pipeline slots.
@@ -232,7 +249,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_contract(Params p) {
   int64_t issued = 0, consumed = 0;
   auto issue = [&](int64_t j) -> bool {
     const int s = (int)(j % S);
-    if (j >= S && !mbar_wait(&empty[s], (uint32_t)(((j / S) - 1) & 1))) return false;
+    if (j >= S && !mbar_wait(&empty[s], (uint32_t)(((j / S) - 1) & 1), p.spin)) return false;
     mbar_arrive_expect_tx(&full[s], kTileBytes);
     bulk_g2s(slots + (size_t)s * kTileBytes, tile_src(j), kTileBytes, &full[s]);
     return true;
@@ -290,7 +307,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_contract(Params p) {
       for (int r = 0; r < tiles_per_group; ++r) {
         const int64_t j = gi * tiles_per_group + r;
         const int s = (int)(j % S);
-        if (!mbar_wait(&full[s], (uint32_t)((j / S) & 1))) {
+        if (!mbar_wait(&full[s], (uint32_t)((j / S) & 1), p.spin)) {
           *abort_s = 1;
           break;
         }
@@ -324,7 +341,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_contract(Params p) {
     }
     // ---- epilogue: accumulators -> Y / Z rows of this warp's TMEM lanes
     // warp-uniform, since tcgen05.ld below is a warp-collective instruction
-    const bool ok = __all_sync(0xffffffffu, mbar_wait(accb, (uint32_t)(gi & 1)));
+    const bool ok = __all_sync(0xffffffffu, mbar_wait(accb, (uint32_t)(gi & 1), p.spin));
     if (!ok) *abort_s = 1;
     tc_fence_after();
     __syncwarp();
@@ -353,9 +370,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_contract(Params p) {
   // ---- teardown (also after a timeout): drain our copies, free tensor memory
   if (tid == 0 && *abort_s) {
     atomicExch(p.err, 1);
-    for (int64_t j = consumed; j < issued; ++j) mbar_wait(&full[j % S], (uint32_t)((j / S) & 1));
+    const uint64_t deadline = global_ns() + kDrainNs;
+    for (int64_t j = consumed; j < issued; ++j)
+      drain_wait(&full[j % S], (uint32_t)((j / S) & 1), deadline);
     mma_commit(drainb);  // arrives once every MMA issued so far has completed
-    mbar_wait(drainb, 0);
+    drain_wait(drainb, 0, deadline);
   }
   tc_fence_before();
   __syncthreads();
@@ -401,13 +420,14 @@ struct FoldParams {
   int rows_in, rows_out;  // nz, nt (fwd) or nt, nz (adj)
   int R;                  // tile rows per representative: mtiles (fwd) or kchunks (adj)
   int* err;
+  uint32_t spin;          // pipeline wait limit (tests per wait)
 };
 
-// Bounded wait that also gives up once another role has aborted.
-// (try_wait itself suspends the thread for a bounded time, so the loop polls
-// without sleeping; 2^22 polls bound the wait to a few seconds.)
-__device__ __forceinline__ bool fwait(uint64_t* bar, uint32_t parity, volatile int* abort_s) {
-  for (uint32_t i = 0; i < (1u << 22); ++i) {
+// Bounded pipeline wait (at most `limit` tests, see mbar_wait) that also gives
+// up once another role has aborted; a wait that runs out sets the abort flag.
+__device__ __forceinline__ bool fwait(uint64_t* bar, uint32_t parity, volatile int* abort_s,
+                                      uint32_t limit) {
+  for (uint32_t i = 0; i < limit; ++i) {
     if (mbar_test(bar, parity)) return true;
     if (*abort_s) return false;
   }
@@ -415,8 +435,9 @@ __device__ __forceinline__ bool fwait(uint64_t* bar, uint32_t parity, volatile i
   return false;
 }
 // Warp-uniform form: every lane polls, all lanes get the same answer.
-__device__ __forceinline__ bool fwait_warp(uint64_t* bar, uint32_t parity, volatile int* abort_s) {
-  return __all_sync(0xffffffffu, fwait(bar, parity, abort_s));
+__device__ __forceinline__ bool fwait_warp(uint64_t* bar, uint32_t parity, volatile int* abort_s,
+                                           uint32_t limit) {
+  return __all_sync(0xffffffffu, fwait(bar, parity, abort_s, limit));
 }
 __device__ __forceinline__ int member(int4 v, int m) {
   return m == 0 ? v.x : (m == 1 ? v.y : (m == 2 ? v.z : v.w));
@@ -517,7 +538,9 @@ __global__ void __launch_bounds__(kFThreads, 1)
     const int64_t total = nmine * 2 * R;
     for (int64_t j = 0; j < total && !*abort_s; ++j) {
       const int s = (int)(j % kFS);
-      if (j >= kFS && !fwait_warp(&empty[s], (uint32_t)(((j / kFS) - 1) & 1), abort_s)) break;
+      if (j >= kFS &&
+          !fwait_warp(&empty[s], (uint32_t)(((j / kFS) - 1) & 1), abort_s, p.spin))
+        break;
       if (lane == 0) {
         const int64_t u = blockIdx.x + (j / (2 * R)) * gridDim.x;
         const int64_t tile = u * 2 * R + j % (2 * R);
@@ -556,14 +579,14 @@ __global__ void __launch_bounds__(kFThreads, 1)
         const int64_t c = ADJ ? i * NB + r : i;  // B chunk
         if (ADJ) {
           // chunk c read out of the staging buffer: stage chunk c + 1
-          ok = fwait_warp(sfree, (uint32_t)(c & 1), abort_s);
+          ok = fwait_warp(sfree, (uint32_t)(c & 1), abort_s, p.spin);
           if (ok && c + 1 < nchunks) stage_chunk(c + 1);
         }
-        if (ok && (ADJ || r == 0)) ok = fwait_warp(bready, (uint32_t)(c & 1), abort_s);
+        if (ok && (ADJ || r == 0)) ok = fwait_warp(bready, (uint32_t)(c & 1), abort_s, p.spin);
         const int64_t q = ADJ ? i : i * NA + r / 2;  // accumulator unit
         const bool unit_start = ADJ ? r == 0 : (r % 2 == 0);
         if (ok && unit_start && q >= 2)
-          ok = fwait_warp(&aempty[q & 1], (uint32_t)(((q >> 1) - 1) & 1), abort_s);
+          ok = fwait_warp(&aempty[q & 1], (uint32_t)(((q >> 1) - 1) & 1), abort_s, p.spin);
         if (!ok) break;
         tc_fence_after();
         const unsigned char* bh = bbuf;
@@ -571,7 +594,7 @@ __global__ void __launch_bounds__(kFThreads, 1)
         const uint32_t d = tmem + (uint32_t)((q & 1) * 256 + (ADJ ? 0 : (r % 2) * 128));
         for (int part = 0; part < 2 && ok; ++part, ++j) {
           const int s = (int)(j % kFS);
-          ok = fwait_warp(&full[s], (uint32_t)((j / kFS) & 1), abort_s);
+          ok = fwait_warp(&full[s], (uint32_t)((j / kFS) & 1), abort_s, p.spin);
           if (!ok) break;
           tc_fence_after();
           if (lane == 0) {
@@ -606,7 +629,7 @@ __global__ void __launch_bounds__(kFThreads, 1)
     // representative u at [4u, 4u + 4) of its srow complex values (32 bytes).
     auto gather = [&](int64_t i, int kc, int64_t c) -> bool {
       (void)kc;
-      if (!fwait_warp(sfull, (uint32_t)(c & 1), abort_s)) return false;
+      if (!fwait_warp(sfull, (uint32_t)(c & 1), abort_s, p.spin)) return false;
       tc_fence_after();
       const int64_t u = blockIdx.x + i * gridDim.x;
       const int4 mem = p.members[u];
@@ -633,7 +656,7 @@ __global__ void __launch_bounds__(kFThreads, 1)
         mbar_arrive(sfree);
       }
       // the B buffer is free once the MMAs of chunk c - 1 are done
-      if (c >= 1 && !fwait_warp(bfree, (uint32_t)((c - 1) & 1), abort_s)) return false;
+      if (c >= 1 && !fwait_warp(bfree, (uint32_t)((c - 1) & 1), abort_s, p.spin)) return false;
 #pragma unroll
       for (int k = 0; k < 2; ++k) {
         const int it = ct + k * 128;
@@ -666,7 +689,7 @@ __global__ void __launch_bounds__(kFThreads, 1)
     // Adjoint drain of representative i in `parts` shares of the volumes:
     // share `part` stores volumes [part * 16 / parts, (part + 1) * 16 / parts).
     auto epilogue_adj = [&](int64_t i, int part, int parts) -> bool {
-      if (part == 0 && !fwait_warp(&afull[i & 1], (uint32_t)((i >> 1) & 1), abort_s))
+      if (part == 0 && !fwait_warp(&afull[i & 1], (uint32_t)((i >> 1) & 1), abort_s, p.spin))
         return false;
       tc_fence_after();
       const int64_t u = blockIdx.x + i * gridDim.x;
@@ -698,7 +721,7 @@ __global__ void __launch_bounds__(kFThreads, 1)
     uint32_t gph = 0;  // phase of the gather-warp barrier
     auto gsync = [&]() -> bool {
       mbar_arrive(gbar);
-      const bool ok = fwait_warp(gbar, gph & 1, abort_s);
+      const bool ok = fwait_warp(gbar, gph & 1, abort_s, p.spin);
       ++gph;
       return ok;
     };
@@ -712,7 +735,7 @@ __global__ void __launch_bounds__(kFThreads, 1)
       }
     };
     auto epilogue_fwd = [&](int64_t i, int a, int64_t q) -> bool {
-      if (!fwait_warp(&afull[q & 1], (uint32_t)((q >> 1) & 1), abort_s)) return false;
+      if (!fwait_warp(&afull[q & 1], (uint32_t)((q >> 1) & 1), abort_s, p.spin)) return false;
       tc_fence_after();
       const int64_t u = blockIdx.x + i * gridDim.x;
       const int nmt = min(2, R - 2 * a);
@@ -765,7 +788,8 @@ __global__ void __launch_bounds__(kFThreads, 1)
       // after an abort: the staging copy still in flight lands before the
       // shared memory is released, and every store has read its tile
       if (ct == 0) {
-        if (*abort_s && fstaged > 0) mbar_wait(sfull, (uint32_t)((fstaged - 1) & 1));
+        if (*abort_s && fstaged > 0)
+          drain_wait(sfull, (uint32_t)((fstaged - 1) & 1), global_ns() + kDrainNs);
         asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
       }
     } else {
@@ -788,14 +812,16 @@ __global__ void __launch_bounds__(kFThreads, 1)
   if (warp == 0 && lane == 0 && *abort_s) {
     atomicExch(p.err, 1);
     // every copy issued lands before the shared memory is released
+    const uint64_t deadline = global_ns() + kDrainNs;
     for (int64_t j = issued - kFS < 0 ? 0 : issued - kFS; j < issued; ++j)
-      mbar_wait(&full[j % kFS], (uint32_t)((j / kFS) & 1));
+      drain_wait(&full[j % kFS], (uint32_t)((j / kFS) & 1), deadline);
   }
   if (warp == 1 && lane == 0 && *abort_s) {
+    const uint64_t deadline = global_ns() + kDrainNs;
     mma_commit(drainb);  // arrives once every MMA issued so far has completed
-    mbar_wait(drainb, 0);
+    drain_wait(drainb, 0, deadline);
     // the last staging copy issued lands before the shared memory is released
-    if (staged > 0) mbar_wait(sfull, (uint32_t)((staged - 1) & 1));
+    if (staged > 0) drain_wait(sfull, (uint32_t)((staged - 1) & 1), deadline);
   }
   tc_fence_before();
   __syncthreads();
@@ -953,6 +979,7 @@ cudaError_t tc_contract(const Plan& p, const void* tables_fwd, const void* table
       q.rows_out = rows_out;
       q.R = L.nt / tc::kTile;
       q.err = err;
+      q.spin = (uint32_t)p.tc_spin;
       CUtensorMap map_in, map_out;
       if ((e = encode_operand_map(&map_in, q.in, q.srow, rows_in, q.batch, true)) != cudaSuccess ||
           (e = encode_operand_map(&map_out, q.out, q.srow, rows_out, q.batch)) != cudaSuccess)
@@ -971,6 +998,7 @@ cudaError_t tc_contract(const Plan& p, const void* tables_fwd, const void* table
     q.nt = L.nt;
     q.batch = std::min(tc::kVB, batch - b0);
     q.err = err;
+    q.spin = (uint32_t)p.tc_spin;
     if (!adjoint) {
       q.table = static_cast<const unsigned char*>(tables_fwd);
       q.in = static_cast<const float2*>(in) + (int64_t)b0 * L.nz * L.Kpad;

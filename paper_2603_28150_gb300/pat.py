@@ -44,7 +44,11 @@ EXPORTS = (
     "pat_stage_contract", "pat_spectrum_noalloc", "pat_plan_estimate", "pat_slot_load",
     "pat_slot_move", "pat_slots_step", "pat_slot_read", "pat_plan_set_tensor_batch",
     "pat_plan_check", "pat_plan_set_sampling", "pat_plan_set_sensor_response",
+    "pat_workspace_size", "pat_plan_create_with_workspace", "pat_plan_create_kspace_with_workspace",
+    "pat_plan_set_wait_limit", "pat_debug_live_allocations", "pat_power_norm_seed",
 )
+
+WAIT_LIMIT_DEFAULT = 4194304
 
 
 class PatError(RuntimeError):
@@ -72,7 +76,7 @@ class PlanInfo(ctypes.Structure):
                 ("workspace_bytes", ctypes.c_int64), ("table_max_abs", ctypes.c_double),
                 ("table_max_imag", ctypes.c_double), ("tensor_table_bytes", ctypes.c_int64),
                 ("tensor_min_batch", ctypes.c_int32), ("folded", ctypes.c_int32),
-                ("table_rows", ctypes.c_int64)]
+                ("table_rows", ctypes.c_int64), ("workspace_external", ctypes.c_int32)]
 
 
 class FistaParams(ctypes.Structure):
@@ -130,6 +134,14 @@ def lib(build_if_missing: bool = True):
         "pat_plan_check": ([P], I),
         "pat_plan_set_sampling": ([P, I, I, I, I], I),
         "pat_plan_set_sensor_response": ([P, D, I, P], I),
+        "pat_workspace_size": ([ctypes.POINTER(Geometry)], ctypes.c_int64),
+        "pat_plan_create_with_workspace": ([ctypes.POINTER(Geometry), V, I, V, ctypes.c_size_t, P,
+                                            ctypes.POINTER(P)], I),
+        "pat_plan_create_kspace_with_workspace": ([ctypes.POINTER(Geometry), ctypes.POINTER(MediumC),
+                                                   V, ctypes.c_size_t, P, ctypes.POINTER(P)], I),
+        "pat_plan_set_wait_limit": ([P, ctypes.c_int64], I),
+        "pat_debug_live_allocations": ([], ctypes.c_int64),
+        "pat_power_norm_seed": ([P, I, ctypes.c_uint64, D, P], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -187,12 +199,16 @@ class Plan:
 
     Build from a table (`table` = spatial h[nz][nt][py][px] real or spectral
     Hh[nz][nt][py][px//2+1] complex; numpy / torch, host or device) or from a
-    `medium` (library generated on the device from the k-space solution)."""
+    `medium` (library generated on the device from the k-space solution).
+    `workspace`: optional caller-owned CUDA tensor of at least
+    workspace_size(...) bytes (e.g. torch.empty(n, dtype=torch.uint8,
+    device="cuda")) that holds every per-call buffer of the plan; the plan keeps
+    a reference to it and never frees it."""
 
     def __init__(self, nx: int, ny: int, nz: int, nt: int, px: int | None = None,
                  py: int | None = None, max_batch: int = 1, fp64: bool = False,
                  force_complex: bool = False, table=None, medium: Medium | None = None,
-                 bf16_split: bool = False, fold: bool = True, stream=None):
+                 bf16_split: bool = False, fold: bool = True, stream=None, workspace=None):
         L = lib()
         self.nx, self.ny, self.nz, self.nt = nx, ny, nz, nt
         self.mx, self.my = nx, ny          # scan grid of the data (see set_sampling)
@@ -208,13 +224,19 @@ class Plan:
         s = _stream(stream)
         if (table is None) == (medium is None):
             raise ValueError("give exactly one of table= or medium=")
+        self._ws = workspace
+        ws_ptr, ws_bytes = (None, 0) if workspace is None else (
+            workspace.data_ptr(), workspace.numel() * workspace.element_size())
+        if workspace is not None and not workspace.is_cuda:
+            raise ValueError("workspace must be a CUDA tensor")
         if medium is not None:
-            _check(L.pat_plan_create_kspace(ctypes.byref(self._geom), ctypes.byref(medium.c_struct()),
-                                            s, ctypes.byref(self._h)))
+            _check(L.pat_plan_create_kspace_with_workspace(
+                ctypes.byref(self._geom), ctypes.byref(medium.c_struct()), ws_ptr, ws_bytes, s,
+                ctypes.byref(self._h)))
         else:
             fmt, keep = _table_format(table, self)
-            _check(L.pat_plan_create(ctypes.byref(self._geom), _ptr(keep), fmt, s,
-                                     ctypes.byref(self._h)))
+            _check(L.pat_plan_create_with_workspace(ctypes.byref(self._geom), _ptr(keep), fmt,
+                                                    ws_ptr, ws_bytes, s, ctypes.byref(self._h)))
         self.dtype_name = "float64" if fp64 else "float32"
 
     # ------------------------------------------------------------------ helpers
@@ -253,10 +275,16 @@ class Plan:
         """Raises PatError(PAT_ERR_TIMEOUT) if a bounded device wait gave up."""
         _check(lib().pat_plan_check(self._h))
 
+    def set_wait_limit(self, polls: int) -> None:
+        """Pipeline wait limit of the tensor-core kernels (tests per wait;
+        < 0 restores the default, 0 makes every such wait give up)."""
+        _check(lib().pat_plan_set_wait_limit(self._h, int(polls)))
+
     def close(self) -> None:
         if self._h and self._h.value:
             lib().pat_plan_destroy(self._h)
             self._h = ctypes.c_void_p(0)
+        self._ws = None
 
     def __del__(self):
         try:
@@ -329,6 +357,13 @@ class Plan:
         self._check_dtype(v0)
         Lout = ctypes.c_double(0.0)
         _check(lib().pat_power_norm(self._h, _ptr(v0), iters, ctypes.byref(Lout), _stream(stream)))
+        return Lout.value
+
+    def power_norm_seed(self, iters: int, seed: int, stream=None) -> float:
+        """L = ||H*H|| by power iteration from the seeded splitmix64 start vector."""
+        Lout = ctypes.c_double(0.0)
+        _check(lib().pat_power_norm_seed(self._h, iters, ctypes.c_uint64(seed), ctypes.byref(Lout),
+                                         _stream(stream)))
         return Lout.value
 
     def fista(self, y, x=None, iters: int = 100, lam: float = 0.0, L: float = 0.0,
@@ -428,14 +463,42 @@ def spectrum_noalloc(x, px: int, py: int, out=None, stream=None):
     """pat_spectrum_noalloc: stage-i spectrum of float32 [S][ny][nx] CUDA slices
     without a plan and without any device allocation inside the call (the
     library's static scratch holds the intermediate). `out`, if given, must be a
-    complex64 CUDA tensor [S][px//2+1][py]; allocate it before calling when the
-    caller itself cannot allocate."""
+    complex64 CUDA tensor [S][px//2+1][py] on x's device; allocate it before
+    calling when the caller itself cannot allocate. Runs on x's device (on
+    `stream`, else that device's current stream)."""
     torch = _torch()
+    if not (isinstance(x, torch.Tensor) and x.is_cuda and x.dtype == torch.float32
+            and x.is_contiguous() and x.dim() == 3):
+        raise TypeError("x must be a contiguous float32 CUDA tensor [S][ny][nx]")
     S, ny, nx = int(x.shape[0]), int(x.shape[-2]), int(x.shape[-1])
+    shape = (S, px // 2 + 1, py)
     if out is None:
-        out = torch.empty((S, px // 2 + 1, py), dtype=torch.complex64, device=x.device)
-    _check(lib().pat_spectrum_noalloc(_ptr(x), nx, ny, px, py, S, _ptr(out), _stream(stream)))
+        out = torch.empty(shape, dtype=torch.complex64, device=x.device)
+    elif not (isinstance(out, torch.Tensor) and out.dtype == torch.complex64
+              and tuple(out.shape) == shape and out.device == x.device and out.is_contiguous()):
+        raise TypeError(f"out must be a contiguous complex64 tensor {shape} on {x.device}")
+    with torch.cuda.device(x.device):
+        s = _stream(stream) if stream is not None else int(
+            torch.cuda.current_stream(x.device).cuda_stream)
+        _check(lib().pat_spectrum_noalloc(_ptr(x), nx, ny, px, py, S, _ptr(out), s))
     return out
+
+
+def workspace_size(nx: int, ny: int, nz: int, nt: int, px: int | None = None,
+                   py: int | None = None, max_batch: int = 1, fp64: bool = False) -> int:
+    """Bytes of caller-owned workspace a plan for this grid needs (pat_workspace_size)."""
+    px = px if px is not None else _pow2_at_least(2 * nx)
+    py = py if py is not None else _pow2_at_least(2 * ny)
+    g = Geometry(nx, ny, nz, nt, px, py, max_batch, FLAG_FP64 if fp64 else 0)
+    n = lib().pat_workspace_size(ctypes.byref(g))
+    if n < 0:
+        _check(int(n))
+    return int(n)
+
+
+def debug_live_allocations() -> int:
+    """Device allocations the library currently holds (all plans)."""
+    return int(lib().pat_debug_live_allocations())
 
 
 def _pow2_at_least(n: int) -> int:

@@ -131,3 +131,19 @@ def timing_spectra(nz: int, nt: int, py: int, px: int, seed: int = 0) -> np.ndar
     for j in range(nz):
         np.multiply(scale[j][:, None, None], base[None], out=out[j])
     return out
+
+
+def splitmix_uniform(n: int, seed: int) -> np.ndarray:
+    """n values 2 u_i - 1 in [-1, 1), u_i = (splitmix64(seed + (i + 1) * gamma) >> 11) * 2^-53,
+    gamma = 0x9E3779B97F4A7C15: the counter-based generator of Steele, Lea &
+    Flood ("Fast splittable pseudorandom number generators", 2014), written
+    from its published definition (the device fills the power iteration's
+    seeded start vector with the same sequence)."""
+    m64 = np.uint64(0xFFFFFFFFFFFFFFFF)
+    with np.errstate(over="ignore"):
+        z = (np.uint64(seed & 0xFFFFFFFFFFFFFFFF)
+             + np.uint64(0x9E3779B97F4A7C15) * np.arange(1, n + 1, dtype=np.uint64)) & m64
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        z = z ^ (z >> np.uint64(31))
+    return (z >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0) * 2.0 - 1.0

@@ -94,3 +94,48 @@ def test_product_has_no_cpu_fallback():
             src = open(os.path.join(os.path.dirname(pkg.__file__), f)).read()
             assert "import oracle" not in src and "from oracle" not in src, f
             assert "np.fft" not in src and "torch.fft" not in src, f
+
+
+def test_workspace_size_without_gpu():
+    """pat_workspace_size needs no device; it equals the workspace part of
+    pat_plan_estimate, grows with max_batch and rejects invalid grids."""
+    L = pat.lib()
+    sizes = []
+    for mb in (1, 2, 4):
+        g = pat.Geometry(128, 128, 64, 256, 256, 256, mb, 0)
+        n = L.pat_workspace_size(ctypes.byref(g))
+        tb, ws = ctypes.c_int64(0), ctypes.c_int64(0)
+        assert L.pat_plan_estimate(ctypes.byref(g), 1, ctypes.byref(tb), ctypes.byref(ws)) == pat.PAT_OK
+        assert n == ws.value > 0
+        sizes.append(n)
+    assert sizes[0] < sizes[1] < sizes[2]
+    # spectra X, Y (>= max(nz, nt) rows of K bins each) dominate
+    assert sizes[0] > 2 * 256 * (129 * 256) * 8
+    assert pat.workspace_size(128, 128, 64, 256) == sizes[0]
+    bad = pat.Geometry(40, 32, 4, 8, 64, 64, 1, 0)
+    assert L.pat_workspace_size(ctypes.byref(bad)) == pat.PAT_ERR_ARG
+    assert L.pat_workspace_size(None) == pat.PAT_ERR_ARG
+
+
+def test_allocation_fault_injection_without_gpu(monkeypatch):
+    """PAT_DEBUG_FAIL_ALLOC = 1 fails the plan's first device allocation on the
+    host (before any CUDA call): PAT_ERR_OOM, nothing left allocated."""
+    L = pat.lib()
+    g = pat.Geometry(16, 16, 4, 8, 32, 32, 1, 0)
+    med = pat.MediumC(1500.0, 1e-4, 1e-4, 1e-4, 2e-8, 64, 1)
+    out = ctypes.c_void_p(0)
+    before = L.pat_debug_live_allocations()
+    monkeypatch.setenv("PAT_DEBUG_FAIL_ALLOC", "1")
+    assert L.pat_plan_create_kspace(ctypes.byref(g), ctypes.byref(med), None,
+                                    ctypes.byref(out)) == pat.PAT_ERR_OOM
+    assert out.value is None
+    assert b"memory" in L.pat_last_error().lower()
+    assert L.pat_debug_live_allocations() == before
+
+
+def test_wait_limit_and_seed_arguments_without_gpu():
+    L = pat.lib()
+    assert L.pat_plan_set_wait_limit(None, 10) == pat.PAT_ERR_ARG
+    d = ctypes.c_double(0.0)
+    assert L.pat_power_norm_seed(None, 5, 1, ctypes.byref(d), None) == pat.PAT_ERR_ARG
+    assert pat.WAIT_LIMIT_DEFAULT == 1 << 22
