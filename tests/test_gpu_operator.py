@@ -380,3 +380,30 @@ def test_fista_100_cfg2_matches_oracle():
     assert err < 1e-5, err
     assert abs(rep["resid2_first"] - ref.resid2[0]) < 1e-5 * ref.resid2[0]
     assert abs(rep["resid2_last"] - ref.resid2[-1]) < 1e-4 * ref.resid2[-1]
+
+
+@pytest.mark.parametrize("nz,nt", [(72, 40), (64, 256), (16, 33), (128, 64)],
+                         ids=["z72_t40", "z64_t256", "z16_t33", "z128_t64"])
+@pytest.mark.parametrize("B", [1, 3])
+def test_folded_table_stream_shapes(nz, nt, B):
+    """The folded contractions at depth / time counts beyond the small test
+    grids: a ragged last z-group (72 depths = 18 groups of 4, more than the 16
+    groups one adjoint z-chunk holds), ragged last time blocks (40 and 33
+    samples), the benchmark's counts, and a 128-depth table: folded ==
+    unfolded, and both equal the FP64 oracle."""
+    g = oracle.Grid.square(24, nz, nt, pad=64)
+    h = _tables(g, "d4", seed=nz + nt)
+    pf = Plan(g.nx, g.ny, g.nz, g.nt, g.px, g.py, table=h, max_batch=B)
+    pu = Plan(g.nx, g.ny, g.nz, g.nt, g.px, g.py, table=h, max_batch=B, fold=False)
+    assert pf.info()["folded"] == 1
+    xs = np.stack([synth.blobs(g.nx, g.ny, g.nz, count=4, seed=60 + s) for s in range(B)])
+    ys = np.stack([synth.gaussian_field((g.nt, g.ny, g.nx), 70 + s) for s in range(B)])
+    A, AT = _ref_ops(h, g)
+    df, du = host(pf.forward(cuda(xs))), host(pu.forward(cuda(xs)))
+    af, au = host(pf.adjoint(cuda(ys))), host(pu.adjoint(cuda(ys)))
+    pf.check()
+    assert np.abs(df - du).max() <= 1e-6 * np.abs(du).max()
+    assert np.abs(af - au).max() <= 1e-6 * np.abs(au).max()
+    for b in range(B):
+        assert oracle.rel_l2(df[b], A(xs[b])) < 1e-5
+        assert oracle.rel_l2(af[b], AT(ys[b])) < 1e-5
