@@ -14,9 +14,13 @@ Also reported: the bare A+A^T pair rate, the plain single-precision path
 dominant kernel (the depth contraction), an end-to-end rate through the C ABI
 with host buffers, the clocks seen while timing, and the CPU oracle's rate.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--mode freq-shard]
 Under torchrun every rank reconstructs its own volume (independent problems,
 weak scaling, no collective on the data path); rank 0 prints one JSON line.
+With --mode freq-shard the ranks instead share one reconstruction: each holds
+1/N of the table's rows, 1/N of the depth slices and 1/N of the time samples,
+with an all-to-all of slice spectra (NCCL) at each stage boundary (strong
+scaling).
 """
 from __future__ import annotations
 
@@ -67,6 +71,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="wall time of the CPU-oracle sample")
+    ap.add_argument("--mode", default="volumes", choices=["volumes", "freq-shard"],
+                    help="volumes: one independent volume per rank; freq-shard: one volume "
+                         "with the operator split over the ranks by frequency rows")
     ap.add_argument("--serve-seconds", type=float, default=60.0,
                     help="arrival window of the serving measurement (0 = skip)")
     return ap.parse_args()
@@ -622,6 +629,75 @@ def cpu_baseline(seconds: float):
             "spatial_form_cfg1_one_core": spatial}
 
 
+# ----------------------------------------------------------------------------- sharded
+class _SelfExchange:
+    """The exchange of a single rank: every chunk stays where it is."""
+
+    def all_to_all(self, send):
+        return send
+
+    def sum(self, value, device):
+        return value
+
+
+def run_shard(args, world, rank, local):
+    """FISTA-100 of one volume with the operator split over the ranks: each
+    rank keeps 1/N of the folded table's rows (the stored operator scales as
+    1/N per GPU), 1/N of the depth slices and 1/N of the time samples; the
+    slice spectra cross ranks in one all-to-all per stage boundary."""
+    import numpy as np
+    import torch
+
+    from paper_2603_28150_gb300 import Medium, Plan
+    from paper_2603_28150_gb300.shard import DistExchange, ShardedOperator
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist_init(world, "nccl")
+    if NZ % world or NT % world:
+        raise SystemExit(f"--mode freq-shard needs N dividing {NZ} and {NT}")
+    plan = Plan(N, N, NZ, NT, P, P, medium=Medium(C0, DX, DX, DX, DT, MZ, Z0), shard=(rank, world))
+    info = plan.shard_info()
+    sop = ShardedOperator(plan, DistExchange() if world > 1 else _SelfExchange())
+    zr, tr = NZ // world, NT // world
+    p0, noise = make_inputs(seed=0)
+    clean = sop.forward(torch.tensor(p0[rank * zr:(rank + 1) * zr], dtype=torch.float32, device=dev))
+    sigma = 0.05 * float(np.sqrt(sop.ex.sum(plan.dot(clean, clean), dev) / (NT * N * N)))
+    y = clean.clone()
+    plan.axpby(y, torch.tensor(noise[rank * tr:(rank + 1) * tr], dtype=torch.float32, device=dev),
+               sigma, 1.0)
+    L = 1.01 * sop.power_norm(torch.ones((zr, N, N), dtype=torch.float32, device=dev), 50)
+    for _ in range(args.warmup):
+        sop.fista(y, L, ITERS)
+    torch.cuda.synchronize()
+    barrier(world)
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(s)
+        for _ in range(args.steps):
+            _, hist = sop.fista(y, L, ITERS)
+        e1.record(s)
+        torch.cuda.synchronize()
+    barrier(world)
+    t_ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
+    value = args.steps * ITERS / (t_ms / 1e3)
+    return {
+        "metric": METRIC, "value": value, "unit": "FISTA it/s (= A+Aᵀ pairs/s)",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "strong",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": dict(bench_config(), per_rank="1/N of one volume's table rows, depth slices and "
+                                                "time samples (frequency shards)"),
+        "mode": "freq-shard",
+        "shard": {"rows_per_rank": info["rows_per_rank"], "slot_width": info["slot_width"],
+                  "table_bytes_per_rank": plan.info()["table_bytes"]},
+        # per iteration: stage i (2 kernels), stage ii (1), stage iii with the
+        # residual (3), stage i (2), stage ii (1), stage iii (2), FISTA step (1)
+        "gpu_launches": 12 * ITERS * args.steps,
+        "clocks": clk.summary(), "L": L, "resid2_last": hist[-1],
+    }
+
+
 def run_reference(args, world, rank):
     """The CPU oracle as the reference arm: each step one FP64 FISTA iteration."""
     if rank != 0:
@@ -661,6 +737,8 @@ def main():
     world, rank, local = dist_env()
     if args.impl == "reference":
         out = run_reference(args, world, rank)
+    elif args.mode == "freq-shard":
+        out = run_shard(args, world, rank, local)
     else:
         out = run_ours(args, world, rank, local)
     if rank == 0 and out is not None:

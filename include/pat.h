@@ -394,6 +394,81 @@ int pat_stage_image(pat_plan* plan, const void* in, void* out, int slices,
 int pat_stage_contract(pat_plan* plan, const void* in, void* out, int batch, int adjoint,
                        pat_stream stream);
 
+/* --- frequency shards: the operator split over ranks --------------------------------- */
+
+/* Stage ii (Eq. 16 term (ii), the per-frequency contraction) is independent
+ * per frequency bin, so `world` ranks (one per GPU) can each keep an equal
+ * share of the table's rows (D4 representatives of a folded library, else
+ * bins): the stored operator, whose size is the limitation discussed in
+ * Sec. 4, then scales as 1 / world per GPU. Stages i and iii are split by
+ * slices: rank r holds depth slices [r nz/world, (r+1) nz/world) of objects
+ * and time samples [r nt/world, (r+1) nt/world) of data. One all-to-all of
+ * slice spectra sits at each stage boundary (the caller runs it, e.g.
+ * NCCL all_to_all_single on equal chunks):
+ *   H:  pat_shard_spectrum(side 0, rho_r) -> send[world][nz/world][W]
+ *       all-to-all                         -> X[nz][W]  (this rank's slots of every depth)
+ *       pat_shard_contract(0, X)           -> Y[nt][W]  = [world][nt/world][W]
+ *       all-to-all                         -> recv[world][nt/world][W]
+ *       pat_shard_image(side 1, recv)      -> d_r [nt/world][ny][nx]
+ *   H*: the same with sides and directions swapped.
+ * Spectra are complex float; W = slot_width: the rank's rows times 4 slots
+ * per representative (folded) or 1 per bin. Slots no bin uses are never read.
+ * Requires world | nz and world | nt. */
+typedef struct {
+  int32_t world, rank;
+  int32_t nz_local, nt_local; /* slices of this rank: nz / world, nt / world */
+  int32_t folded;             /* 1: rows are D4 representatives */
+  int32_t reserved;
+  int64_t rows_total;         /* table rows of the whole operator */
+  int64_t rows_per_rank;      /* equal range per rank, a multiple of 32 */
+  int64_t row0, rows;         /* this rank's rows [row0, row0 + rows) */
+  int64_t slot_width;         /* W: complex values per exchange row */
+  int64_t bins;               /* frequency bins (px/2 + 1) py */
+} pat_shard_info;
+
+/* Host only (no device call): the partition of rank `rank` of `world` for a
+ * library stored folded (`fold` = 1) or per bin. Optional outputs (host
+ * arrays): zmap[bins] / tmap[bins], the position of every bin k of one slice
+ * in the depth-side / time-side exchange buffer (owner q of k's row:
+ * q * (slices per rank) * W + slot of k), and members_local[rows_per_rank * 4]
+ * (folded: slot of member i of this rank's j-th representative, -1 = none). */
+int pat_shard_layout(const pat_geometry* g, int fold, int rank, int world, pat_shard_info* info,
+                     int32_t* zmap, int32_t* tmap, int32_t* members_local);
+
+/* A plan holding only this rank's rows of the library generated from `m`
+ * (as pat_plan_create_kspace; single precision, max_batch = 1). It runs only
+ * the pat_shard_* stages (other operator entry points return PAT_ERR_ARG). */
+int pat_plan_create_kspace_shard(const pat_geometry* g, const pat_medium* m, int rank, int world,
+                                 pat_stream stream, pat_plan** out);
+int pat_plan_shard_info(const pat_plan* plan, pat_shard_info* info);
+
+/* Stage i of this rank's slices (side 0: depth slices of an object, side 1:
+ * time samples of data; in float[n][ny][nx], n = nz_local or nt_local) into
+ * the send buffer complex[world][n][W] (Eq. 16 term (i)). Device arrays. */
+int pat_shard_spectrum(pat_plan* plan, int side, const float* in, void* send, pat_stream stream);
+
+/* Stage ii on this rank's rows: adjoint = 0: in X[nz][W] -> out Y[nt][W]
+ * (Eq. 7); adjoint = 1: in D[nt][W] -> out Z[nz][W] (Eq. 11). */
+int pat_shard_contract(pat_plan* plan, int adjoint, const void* in, void* out, pat_stream stream);
+
+/* Stage iii of this rank's slices from the received spectra
+ * recv[world][n][W] into out float[n][ny][nx] (Eq. 16 term (iii)). With
+ * `sub` (same shape as out): out = image - sub, and if r2 is not NULL *r2
+ * (host) = sum of out^2 in FP64 over this rank's slices (the call then
+ * synchronises `stream`). */
+int pat_shard_image(pat_plan* plan, int side, const void* recv, float* out, const float* sub,
+                    double* r2, pat_stream stream);
+
+/* The FISTA update of Eq. 14-15 on n device floats (a distributed solve keeps
+ * each rank's depth slices): x = max(y - grad invL - lamL, 0),
+ * y <- x + beta (x - xprev), xprev <- x. */
+int pat_fista_step(float* y, float* xprev, const float* grad, int64_t n, double invL, double lamL,
+                   double beta, pat_stream stream);
+
+/* y = a x + b y on n device floats (x may equal y): the scaling and
+ * combination steps of a distributed power iteration or data synthesis. */
+int pat_axpby(float* y, const float* x, int64_t n, double a, double b, pat_stream stream);
+
 /* --- for callers that cannot allocate device memory ----------------------------- */
 
 /* The paper has no counterpart to this entry point; it exists for callers that

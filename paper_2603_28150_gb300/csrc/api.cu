@@ -104,7 +104,8 @@ void free_plan(pat_plan* pp) {
   }
   // the plan's own memory: the table side, buffers allocated on first use,
   // and the workspace arena unless the caller owns it
-  void* owned[] = {p.table, p.tc_fwd, p.tc_adj, p.fold_members, p.fold_rep, p.fold_slot};
+  void* owned[] = {p.table,         p.tc_fwd,        p.tc_adj,    p.fold_members, p.fold_rep,
+                   p.fold_slot,     p.shard_zmap,    p.shard_tmap, p.shard_members};
   for (void* b : owned) dev_free(b);
   if (x.io_heap) {
     dev_free(x.io_obj[0]);
@@ -399,6 +400,8 @@ namespace {
 
 int check_call(pat_plan* plan, int batch) {
   if (!plan) return fail(PAT_ERR_ARG, "plan is NULL");
+  if (plan->p.shard_world)
+    return fail(PAT_ERR_ARG, "a frequency-shard plan runs only the pat_shard_* stages");
   if (batch < 0 || batch > plan->p.L.max_batch)
     return fail(PAT_ERR_ARG, "batch must be in [0, max_batch]");
   return PAT_OK;
@@ -518,6 +521,13 @@ Graph* graph_for(pat_plan* pp, int batch, int* rc) {
 }
 
 }  // namespace
+
+namespace pat {
+int plan_create_common(const pat_geometry* g, pat_plan** out, pat_plan** pp) {
+  return create_common(g, nullptr, 0, out, pp);
+}
+void plan_free(pat_plan* pp) { free_plan(pp); }
+}  // namespace pat
 
 
 #define PAT_GUARD_BEGIN try {
@@ -932,6 +942,7 @@ int pat_dot_f64(pat_plan* plan, const void* a, const void* b, int64_t n, double*
 int pat_stage_spectrum(pat_plan* plan, const void* in, void* out, int slices, pat_stream stream) {
   PAT_GUARD_BEGIN
   if (!plan || !in || !out) return fail(PAT_ERR_ARG, "bad arguments");
+  if (plan->p.shard_world) return fail(PAT_ERR_ARG, "a frequency-shard plan runs only the pat_shard_* stages");
   const Layout& L = plan->p.L;
   if (slices < 0 || slices > L.max_batch * std::max(L.nz, L.nt))
     return fail(PAT_ERR_ARG, "slices must be in [0, max_batch * max(nz, nt)]");
@@ -944,6 +955,7 @@ int pat_stage_spectrum(pat_plan* plan, const void* in, void* out, int slices, pa
 int pat_stage_image(pat_plan* plan, const void* in, void* out, int slices, pat_stream stream) {
   PAT_GUARD_BEGIN
   if (!plan || !in || !out) return fail(PAT_ERR_ARG, "bad arguments");
+  if (plan->p.shard_world) return fail(PAT_ERR_ARG, "a frequency-shard plan runs only the pat_shard_* stages");
   const Layout& L = plan->p.L;
   if (slices < 0 || slices > L.max_batch * std::max(L.nz, L.nt))
     return fail(PAT_ERR_ARG, "slices must be in [0, max_batch * max(nz, nt)]");

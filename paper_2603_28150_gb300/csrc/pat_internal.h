@@ -213,6 +213,15 @@ struct Plan {
   size_t tc_bytes = 0;   // both directions
   int* tc_err = nullptr; // device flag of timed-out waits
   int tc_min_batch = 0;
+  // Frequency shard (pat_plan_create_kspace_shard): this plan holds table rows
+  // [shard_row0, shard_row0 + shard_rows) of shard_world equal ranges of
+  // shard_Wr rows; its spectra live in exchange buffers of rows of shard_W
+  // complex values (4 slots per representative when folded, 1 per bin else).
+  int shard_world = 0, shard_rank = 0;
+  int64_t shard_row0 = 0, shard_rows = 0, shard_Wr = 0, shard_W = 0;
+  int* shard_zmap = nullptr;     // [K] bin -> position in the depth-side exchange buffer
+  int* shard_tmap = nullptr;     // [K] bin -> position in the time-side exchange buffer
+  int* shard_members = nullptr;  // [Wr][4] local slots of this shard's representatives
 };
 
 constexpr int kReduceBlocks = 1024;  // max blocks of the FP64 reductions
@@ -262,6 +271,9 @@ cudaError_t adjoint_dev(const Plan& p, const void* d, void* rho, int batch, cuda
 cudaError_t gradient_dev(const Plan& p, const void* x, const void* y, void* grad, int batch,
                          cudaStream_t s, double* sumsq, int groups = 0,
                          double* group_sums = nullptr, const FistaStep* step = nullptr);
+// Plan shell with its workspace (api.cu) and its release.
+int plan_create_common(const pat_geometry* g, pat_plan** out, pat_plan** pp);
+void plan_free(pat_plan* pp);
 // Records the kernel nodes of `graph`; instantiates it.
 cudaError_t instantiate_counted(cudaGraph_t graph, cudaGraphExec_t* exec, int* kernels);
 
@@ -366,6 +378,18 @@ int build_table_from_source(Plan& p, const void* table, pat_table_format fmt, bo
                             bool allow_fold, cudaStream_t s);
 int build_table_kspace(Plan& p, const pat_medium& m, bool force_complex, bool allow_fold,
                        cudaStream_t s);
+// Whether a k-space library of this layout is stored folded (real table on a
+// square grid, dx = dy, single precision, folding allowed).
+bool kspace_folds(const Layout& L, const pat_medium& m, bool allow_fold);
+// Generates the k-space library rows at the given bins (one bin per table row,
+// the row's representative when folded) into a newly allocated p.table of
+// p.L.table_bytes in p.L's representation.
+int kspace_generate(Plan& p, const pat_medium& m, const std::vector<int>& bins, cudaStream_t s);
+// Host enumeration of the D4 representatives of a P x P half spectrum:
+// members[4 u + i] (the up to 4 bins of representative u, -1 = none),
+// rep[k] and slot[k] = 4 u + i for every bin k.
+void fold_enumerate(int P, std::vector<int>& members, std::vector<int>& rep,
+                    std::vector<int>& slot);
 bool is_device_ptr(const void* p);
 // Ordinal of the device holding `p`, or -1 if it is not device memory.
 int device_of(const void* p);

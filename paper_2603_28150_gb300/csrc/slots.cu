@@ -129,6 +129,8 @@ Graph* step_graph(pat_plan* pp, int n, int* rc) {
 
 int check_slot(pat_plan* plan, int slot) {
   if (!plan) return fail(PAT_ERR_ARG, "plan is NULL");
+  if (plan->p.shard_world)
+    return fail(PAT_ERR_ARG, "a frequency-shard plan runs only the pat_shard_* stages");
   if (slot < 0 || slot >= plan->p.L.max_batch) return fail(PAT_ERR_ARG, "slot out of range");
   return PAT_OK;
 }
@@ -190,6 +192,8 @@ int pat_slot_move(pat_plan* plan, int dst, int src, pat_stream stream) {
 int pat_slots_step(pat_plan* plan, int n, int* kernels, pat_stream stream) {
   try {
     if (!plan) return fail(PAT_ERR_ARG, "plan is NULL");
+    if (plan->p.shard_world)
+      return fail(PAT_ERR_ARG, "a frequency-shard plan runs only the pat_shard_* stages");
     if (n < 0 || n > plan->p.L.max_batch) return fail(PAT_ERR_ARG, "n must be in [0, max_batch]");
     if (kernels) *kernels = 0;
     if (n == 0) return PAT_OK;

@@ -274,10 +274,13 @@ int apply_sensor_response(Plan& p, const double* r, int nr, cudaStream_t s) {
   return PAT_OK;
 }
 
-int build_fold_maps(Plan& p, std::vector<int>* rep_bins) {
-  Layout& L = p.L;
-  const int P = L.px, half = P / 2;
-  std::vector<int> members, rep((size_t)L.K, -1), slot((size_t)L.K, -1);
+void fold_enumerate(int P, std::vector<int>& members, std::vector<int>& rep,
+                    std::vector<int>& slot) {
+  const int half = P / 2;
+  const int64_t K = (int64_t)(half + 1) * P;
+  members.clear();
+  rep.assign((size_t)K, -1);
+  slot.assign((size_t)K, -1);
   for (int a = 0; a <= half; ++a)
     for (int b = a; b <= half; ++b) {
       // bins (kx, ky) of the half spectrum with {kx, |ky|} = {a, b}
@@ -298,6 +301,12 @@ int build_fold_maps(Plan& p, std::vector<int>* rep_bins) {
         }
       }
     }
+}
+
+int build_fold_maps(Plan& p, std::vector<int>* rep_bins) {
+  Layout& L = p.L;
+  std::vector<int> members, rep, slot;
+  fold_enumerate(L.px, members, rep, slot);
   L.U = (int64_t)members.size() / 4;
   L.Upad = (L.U + 31) / 32 * 32;
   L.nub = L.Upad / 32;
@@ -525,8 +534,7 @@ int build_table_kspace(Plan& p, const pat_medium& m, bool force_complex, bool al
   // |k| depends on kx^2 + ky^2 only, so with dx = dy on a square grid the
   // library is exactly D4-symmetric: generate one row per representative.
   std::vector<int> bins;
-  const bool fold = allow_fold && fold_possible(L) && m.dx == m.dy;
-  if (fold) {
+  if (kspace_folds(L, m, allow_fold)) {
     int rc = build_fold_maps(p, &bins);
     if (rc != PAT_OK) return rc;
     set_representation(L, true, true);
@@ -534,6 +542,15 @@ int build_table_kspace(Plan& p, const pat_medium& m, bool force_complex, bool al
     bins.resize((size_t)L.K);
     for (int64_t k = 0; k < L.K; ++k) bins[k] = (int)k;
   }
+  return kspace_generate(p, m, bins, s);
+}
+
+bool kspace_folds(const Layout& L, const pat_medium& m, bool allow_fold) {
+  return allow_fold && fold_possible(L) && m.dx == m.dy;
+}
+
+int kspace_generate(Plan& p, const pat_medium& m, const std::vector<int>& bins, cudaStream_t s) {
+  const Layout& L = p.L;
   const int64_t npos = (int64_t)bins.size();
   const int M = m.mz / 2 + 1;
   const double pi = 3.14159265358979323846;
@@ -587,10 +604,12 @@ int build_table_kspace(Plan& p, const pat_medium& m, bool force_complex, bool al
   }
   GEN_CUDA(cudaFuncSetAttribute((const void*)k_kspace, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)smem));
-  k_kspace<<<(unsigned)((npos + 31) / 32), 256, smem, s>>>(L.px, L.py, m.mz, L.nz, L.nt, L.nzg,
-                                                            L.zg, L.real ? 0 : 1, u_d, W_d,
-                                                            p.table, npos);
-  GEN_CUDA(cudaGetLastError());
+  if (npos > 0) {  // a frequency shard may hold no rows
+    k_kspace<<<(unsigned)((npos + 31) / 32), 256, smem, s>>>(L.px, L.py, m.mz, L.nz, L.nt, L.nzg,
+                                                              L.zg, L.real ? 0 : 1, u_d, W_d,
+                                                              p.table, npos);
+    GEN_CUDA(cudaGetLastError());
+  }
   GEN_CUDA(cudaStreamSynchronize(s));
   cleanup();
   p.table_max_abs = 0;

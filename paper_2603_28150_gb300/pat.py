@@ -46,6 +46,9 @@ EXPORTS = (
     "pat_plan_check", "pat_plan_set_sampling", "pat_plan_set_sensor_response",
     "pat_workspace_size", "pat_plan_create_with_workspace", "pat_plan_create_kspace_with_workspace",
     "pat_plan_set_wait_limit", "pat_debug_live_allocations", "pat_power_norm_seed",
+    "pat_shard_layout", "pat_plan_create_kspace_shard", "pat_plan_shard_info",
+    "pat_shard_spectrum", "pat_shard_contract", "pat_shard_image", "pat_fista_step",
+    "pat_axpby",
 )
 
 WAIT_LIMIT_DEFAULT = 4194304
@@ -77,6 +80,18 @@ class PlanInfo(ctypes.Structure):
                 ("table_max_imag", ctypes.c_double), ("tensor_table_bytes", ctypes.c_int64),
                 ("tensor_min_batch", ctypes.c_int32), ("folded", ctypes.c_int32),
                 ("table_rows", ctypes.c_int64), ("workspace_external", ctypes.c_int32)]
+
+
+class ShardInfo(ctypes.Structure):
+    _fields_ = [("world", ctypes.c_int32), ("rank", ctypes.c_int32),
+                ("nz_local", ctypes.c_int32), ("nt_local", ctypes.c_int32),
+                ("folded", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("rows_total", ctypes.c_int64), ("rows_per_rank", ctypes.c_int64),
+                ("row0", ctypes.c_int64), ("rows", ctypes.c_int64),
+                ("slot_width", ctypes.c_int64), ("bins", ctypes.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
 
 
 class FistaParams(ctypes.Structure):
@@ -142,6 +157,16 @@ def lib(build_if_missing: bool = True):
         "pat_plan_set_wait_limit": ([P, ctypes.c_int64], I),
         "pat_debug_live_allocations": ([], ctypes.c_int64),
         "pat_power_norm_seed": ([P, I, ctypes.c_uint64, D, P], I),
+        "pat_shard_layout": ([ctypes.POINTER(Geometry), I, I, I, ctypes.POINTER(ShardInfo), V, V, V], I),
+        "pat_plan_create_kspace_shard": ([ctypes.POINTER(Geometry), ctypes.POINTER(MediumC), I, I, P,
+                                          ctypes.POINTER(P)], I),
+        "pat_plan_shard_info": ([P, ctypes.POINTER(ShardInfo)], I),
+        "pat_shard_spectrum": ([P, I, V, V, P], I),
+        "pat_shard_contract": ([P, I, V, V, P], I),
+        "pat_shard_image": ([P, I, V, V, V, D, P], I),
+        "pat_fista_step": ([V, V, V, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
+                            ctypes.c_double, P], I),
+        "pat_axpby": ([V, V, ctypes.c_int64, ctypes.c_double, ctypes.c_double, P], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -208,7 +233,8 @@ class Plan:
     def __init__(self, nx: int, ny: int, nz: int, nt: int, px: int | None = None,
                  py: int | None = None, max_batch: int = 1, fp64: bool = False,
                  force_complex: bool = False, table=None, medium: Medium | None = None,
-                 bf16_split: bool = False, fold: bool = True, stream=None, workspace=None):
+                 bf16_split: bool = False, fold: bool = True, stream=None, workspace=None,
+                 shard: tuple | None = None):
         L = lib()
         self.nx, self.ny, self.nz, self.nt = nx, ny, nz, nt
         self.mx, self.my = nx, ny          # scan grid of the data (see set_sampling)
@@ -229,7 +255,15 @@ class Plan:
             workspace.data_ptr(), workspace.numel() * workspace.element_size())
         if workspace is not None and not workspace.is_cuda:
             raise ValueError("workspace must be a CUDA tensor")
-        if medium is not None:
+        self.shard = shard
+        if shard is not None:
+            if medium is None or workspace is not None:
+                raise ValueError("a frequency shard is built from a medium, on its own workspace")
+            rank, world = shard
+            _check(L.pat_plan_create_kspace_shard(ctypes.byref(self._geom),
+                                                  ctypes.byref(medium.c_struct()), rank, world, s,
+                                                  ctypes.byref(self._h)))
+        elif medium is not None:
             _check(L.pat_plan_create_kspace_with_workspace(
                 ctypes.byref(self._geom), ctypes.byref(medium.c_struct()), ws_ptr, ws_bytes, s,
                 ctypes.byref(self._h)))
@@ -417,6 +451,59 @@ class Plan:
                                    _stream(stream)))
         return out, (r2.value if resid else None)
 
+    # ------------------------------------------------------------------ frequency shards
+    def shard_info(self) -> dict:
+        inf = ShardInfo()
+        _check(lib().pat_plan_shard_info(self._h, ctypes.byref(inf)))
+        return inf.as_dict()
+
+    def shard_spectrum(self, side: int, x, send=None, stream=None):
+        """Stage i of this rank's slices (side 0: depth slices of an object,
+        1: time samples of data) into the all-to-all send buffer
+        complex64 [world][slices][W]."""
+        torch = _torch()
+        inf = self.shard_info()
+        n = inf["nt_local"] if side else inf["nz_local"]
+        if send is None:
+            send = torch.empty((inf["world"], n, inf["slot_width"]), dtype=torch.complex64,
+                               device=x.device)
+        _check(lib().pat_shard_spectrum(self._h, side, _ptr(x), _ptr(send), _stream(stream)))
+        return send
+
+    def shard_contract(self, inp, out=None, adjoint: bool = False, stream=None):
+        """Stage ii on this rank's rows: [nz][W] -> [nt][W] (or the adjoint)."""
+        torch = _torch()
+        if out is None:
+            inf = self.shard_info()
+            rows = self.nz if adjoint else self.nt
+            out = torch.empty((rows, inf["slot_width"]), dtype=torch.complex64, device=inp.device)
+        _check(lib().pat_shard_contract(self._h, 1 if adjoint else 0, _ptr(inp), _ptr(out),
+                                        _stream(stream)))
+        return out
+
+    def shard_image(self, side: int, recv, out=None, sub=None, resid: bool = False, stream=None):
+        """Stage iii of this rank's slices from the received spectra
+        [world][slices][W]; with `sub`, image - sub (and its FP64 sum of squares
+        over this rank when resid). Returns (out, r2 or None)."""
+        torch = _torch()
+        inf = self.shard_info()
+        n = inf["nt_local"] if side else inf["nz_local"]
+        if out is None:
+            out = torch.empty((n, self.ny, self.nx), dtype=torch.float32, device=recv.device)
+        r2 = ctypes.c_double(0.0)
+        _check(lib().pat_shard_image(self._h, side, _ptr(recv), _ptr(out),
+                                     _ptr(sub) if sub is not None else None,
+                                     ctypes.byref(r2) if resid else None, _stream(stream)))
+        return out, (r2.value if resid else None)
+
+    def fista_step(self, y, xprev, grad, invL: float, lamL: float, beta: float, stream=None):
+        """The FISTA update of Eq. 14-15 in place (pat_fista_step)."""
+        fista_step(y, xprev, grad, invL, lamL, beta, stream)
+
+    def axpby(self, y, x, a: float, b: float, stream=None) -> None:
+        """y = a x + b y in place (pat_axpby)."""
+        axpby(y, x, a, b, stream)
+
     # ------------------------------------------------------------------ stages
     def stage_spectrum(self, x, out=None, stream=None):
         """Zero-padded 2D real DFT of real [S][ny][nx] slices -> complex [S][px//2+1][py]."""
@@ -482,6 +569,38 @@ def spectrum_noalloc(x, px: int, py: int, out=None, stream=None):
             torch.cuda.current_stream(x.device).cuda_stream)
         _check(lib().pat_spectrum_noalloc(_ptr(x), nx, ny, px, py, S, _ptr(out), s))
     return out
+
+
+def fista_step(y, xprev, grad, invL: float, lamL: float, beta: float, stream=None) -> None:
+    """pat_fista_step: the FISTA update of Eq. 14-15 in place on float32 CUDA arrays."""
+    n = int(np.prod(y.shape))
+    assert int(np.prod(xprev.shape)) == n and int(np.prod(grad.shape)) == n
+    _check(lib().pat_fista_step(_ptr(y), _ptr(xprev), _ptr(grad), n, invL, lamL, beta,
+                                _stream(stream)))
+
+
+def axpby(y, x, a: float, b: float, stream=None) -> None:
+    """y = a x + b y in place on float32 CUDA arrays (pat_axpby)."""
+    n = int(np.prod(y.shape))
+    assert int(np.prod(x.shape)) == n
+    _check(lib().pat_axpby(_ptr(y), _ptr(x), n, a, b, _stream(stream)))
+
+
+def shard_layout(nx: int, ny: int, nz: int, nt: int, px: int, py: int, fold: bool, rank: int,
+                 world: int):
+    """pat_shard_layout (host only): the partition of one rank and its slot maps
+    (zmap, tmap: int32 [bins]; members_local: int32 [rows_per_rank][4] when folded)."""
+    g = Geometry(nx, ny, nz, nt, px, py, 1, 0)
+    inf = ShardInfo()
+    _check(lib().pat_shard_layout(ctypes.byref(g), 1 if fold else 0, rank, world, ctypes.byref(inf),
+                                  None, None, None))
+    K = inf.bins
+    zmap = np.empty(K, np.int32)
+    tmap = np.empty(K, np.int32)
+    mem = np.empty((inf.rows_per_rank, 4), np.int32)
+    _check(lib().pat_shard_layout(ctypes.byref(g), 1 if fold else 0, rank, world, ctypes.byref(inf),
+                                  zmap.ctypes.data, tmap.ctypes.data, mem.ctypes.data))
+    return inf.as_dict(), zmap, tmap, (mem if fold else None)
 
 
 def workspace_size(nx: int, ny: int, nz: int, nt: int, px: int | None = None,

@@ -139,3 +139,20 @@ def test_wait_limit_and_seed_arguments_without_gpu():
     d = ctypes.c_double(0.0)
     assert L.pat_power_norm_seed(None, 5, 1, ctypes.byref(d), None) == pat.PAT_ERR_ARG
     assert pat.WAIT_LIMIT_DEFAULT == 1 << 22
+
+
+def test_shard_arguments_without_gpu():
+    L = pat.lib()
+    out = ctypes.c_void_p(0)
+    g = pat.Geometry(16, 16, 6, 8, 32, 32, 1, 0)
+    med = pat.MediumC(1500.0, 1e-4, 1e-4, 1e-4, 2e-8, 64, 1)
+    # world must divide nz and nt
+    assert L.pat_plan_create_kspace_shard(ctypes.byref(g), ctypes.byref(med), 0, 4, None,
+                                          ctypes.byref(out)) == pat.PAT_ERR_UNSUPPORTED
+    assert L.pat_plan_create_kspace_shard(ctypes.byref(g), ctypes.byref(med), 2, 2, None,
+                                          ctypes.byref(out)) == pat.PAT_ERR_ARG
+    g2 = pat.Geometry(16, 16, 6, 8, 32, 32, 2, 0)
+    assert L.pat_plan_create_kspace_shard(ctypes.byref(g2), ctypes.byref(med), 0, 2, None,
+                                          ctypes.byref(out)) == pat.PAT_ERR_UNSUPPORTED
+    assert L.pat_shard_spectrum(None, 0, None, None, None) == pat.PAT_ERR_ARG
+    assert L.pat_fista_step(None, None, None, 5, 1.0, 0.0, 0.0, None) == pat.PAT_ERR_ARG
