@@ -469,6 +469,16 @@ int pat_fista_step(float* y, float* xprev, const float* grad, int64_t n, double 
  * combination steps of a distributed power iteration or data synthesis. */
 int pat_axpby(float* y, const float* x, int64_t n, double a, double b, pat_stream stream);
 
+/* Stage ii of the folded split-BF16 path as the operator runs it, on spectra
+ * already in its representative-slot layout (no conversion): rows of
+ * 4 * ceil(U / 32) * 32 complex float, bin k at slot 4 u + i (member i of its
+ * D4 representative u), in[b][nz or nt][row], out likewise. Only for plans
+ * built with PAT_FLAG_BF16_SPLIT, folded, and batch >= the tensor batch
+ * (PAT_ERR_ARG otherwise). Eq. 16 term (ii); a timing aid for the tensor-core
+ * contraction alone. */
+int pat_stage_contract_slots(pat_plan* plan, const void* in, void* out, int batch, int adjoint,
+                             pat_stream stream);
+
 /* --- for callers that cannot allocate device memory ----------------------------- */
 
 /* The paper has no counterpart to this entry point; it exists for callers that

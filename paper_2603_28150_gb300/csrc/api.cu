@@ -993,4 +993,24 @@ int pat_stage_contract(pat_plan* plan, const void* in, void* out, int batch, int
   PAT_GUARD_END
 }
 
+int pat_stage_contract_slots(pat_plan* plan, const void* in, void* out, int batch, int adjoint,
+                             pat_stream stream) {
+  PAT_GUARD_BEGIN
+  int rc = check_call(plan, batch);
+  if (rc != PAT_OK) return rc;
+  if (batch == 0) return PAT_OK;
+  if (!in || !out) return fail(PAT_ERR_ARG, "in or out is NULL");
+  const Plan& p = plan->p;
+  if (!tc_slots(p, batch))
+    return fail(PAT_ERR_ARG, "the representative-slot layout belongs to the folded split-BF16 "
+                             "path at batch >= its tensor batch");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (adjoint)
+    PAT_CUDA(launch_contract_adj(p, in, out, batch, s));
+  else
+    PAT_CUDA(launch_contract_fwd(p, in, out, batch, s));
+  return PAT_OK;
+  PAT_GUARD_END
+}
+
 }  // extern "C"

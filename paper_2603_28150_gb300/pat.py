@@ -48,7 +48,7 @@ EXPORTS = (
     "pat_plan_set_wait_limit", "pat_debug_live_allocations", "pat_power_norm_seed",
     "pat_shard_layout", "pat_plan_create_kspace_shard", "pat_plan_shard_info",
     "pat_shard_spectrum", "pat_shard_contract", "pat_shard_image", "pat_fista_step",
-    "pat_axpby",
+    "pat_axpby", "pat_stage_contract_slots",
 )
 
 WAIT_LIMIT_DEFAULT = 4194304
@@ -167,6 +167,7 @@ def lib(build_if_missing: bool = True):
         "pat_fista_step": ([V, V, V, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
                             ctypes.c_double, P], I),
         "pat_axpby": ([V, V, ctypes.c_int64, ctypes.c_double, ctypes.c_double, P], I),
+        "pat_stage_contract_slots": ([P, V, V, I, I, P], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -520,6 +521,13 @@ class Plan:
         """Stage ii alone on complex [batch][rows][bins_padded] device arrays."""
         _check(lib().pat_stage_contract(self._h, _ptr(X), _ptr(out), batch, 1 if adjoint else 0,
                                         _stream(stream)))
+        return out
+
+    def stage_contract_slots(self, X, out, batch: int, adjoint: bool = False, stream=None):
+        """Stage ii of the folded split-BF16 path on spectra already in its
+        representative-slot layout (rows of 4 * ceil(U/32) * 32 complex)."""
+        _check(lib().pat_stage_contract_slots(self._h, _ptr(X), _ptr(out), batch,
+                                              1 if adjoint else 0, _stream(stream)))
         return out
 
     def stage_image(self, X, out=None, stream=None):

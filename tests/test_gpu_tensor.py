@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 
 import oracle
-from paper_2603_28150_gb300 import Medium, Plan, synth
+from paper_2603_28150_gb300 import Medium, PatError, Plan, synth
 from tests.helpers import MED_50UM, cuda, host
 
 pytestmark = pytest.mark.gpu
@@ -99,3 +99,37 @@ def test_cfg3_sampled_outputs_full_size():
     for v in (0, 15):
         ref = oracle.adjoint_fft(Hf, ys[v], gz)[0]
         assert oracle.rel_l2(a[v, 40], ref) < 1e-3, v
+
+
+def test_contract_slots_equals_converting_stage():
+    """pat_stage_contract_slots on spectra placed in the representative-slot
+    layout (bin k at 4 u + i) gives, bit for bit, what pat_stage_contract
+    gives on the bin layout (which converts to that layout and back)."""
+    import torch
+
+    from paper_2603_28150_gb300 import pat
+    g = oracle.Grid.square(16, 128, 256)
+    B = 16
+    plan = Plan(g.nx, g.ny, g.nz, g.nt, g.px, g.py, max_batch=B, medium=_medium(g, MED_50UM),
+                bf16_split=True)
+    info = plan.info()
+    assert info["folded"] == 1
+    # with one rank the depth-side map is the slot position itself
+    sinfo, slot, _, _ = pat.shard_layout(g.nx, g.ny, g.nz, g.nt, g.px, g.py, True, 0, 1)
+    srow = sinfo["slot_width"]
+    assert srow == 4 * ((info["table_rows"] + 31) // 32 * 32)
+    slot = torch.tensor(slot, dtype=torch.long, device="cuda")
+    K, Kp = info["bins"], info["bins_padded"]
+    gen = torch.Generator(device="cuda").manual_seed(3)
+    for adjoint, rin, rout in ((False, g.nz, g.nt), (True, g.nt, g.nz)):
+        X = torch.randn((B, rin, Kp), dtype=torch.complex64, device="cuda", generator=gen)
+        Y = plan.stage_contract(X, torch.zeros((B, rout, Kp), dtype=torch.complex64, device="cuda"),
+                                batch=B, adjoint=adjoint)
+        Xs = torch.zeros((B, rin, srow), dtype=torch.complex64, device="cuda")
+        Xs[:, :, slot] = X[:, :, :K]
+        Ys = plan.stage_contract_slots(Xs, torch.zeros((B, rout, srow), dtype=torch.complex64,
+                                                       device="cuda"), B, adjoint=adjoint)
+        plan.check()
+        assert torch.equal(Ys[:, :, slot], Y[:, :, :K])
+    with pytest.raises(PatError):
+        plan.stage_contract_slots(Xs, Ys, 1)   # below the tensor batch: no slot layout
