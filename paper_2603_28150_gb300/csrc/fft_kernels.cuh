@@ -589,9 +589,26 @@ __global__ void __launch_bounds__(kThreads) k_row_r2c(const R* __restrict__ in, 
   }
 }
 
+// The bins ky and P - ky of one column (mirror pair) sit in adjacent slots
+// of the representative-slot layout (members 0 / 1 or 2 / 3 of one D4
+// representative), so a slot-mapped column stores them as one 16-byte access
+// when their slots are an aligned pair, else as two.
+template <typename R>
+__device__ __forceinline__ void slot_store_pair(cx<R>* dst, int s0, int s1, cx<R> v0, cx<R> v1) {
+  if (s1 == s0 + 1 && !(s0 & 1)) {
+    store_pair(dst + s0, v0, v1);
+  } else if (s0 == s1 + 1 && !(s1 & 1)) {
+    store_pair(dst + s1, v1, v0);
+  } else {
+    dst[s0] = v0;
+    dst[s1] = v1;
+  }
+}
+
 // Stage i, column pass: T[s][kx][0..n_in) zero-padded to P, FFT over y,
 // written to out[s][kx][0..P) (slice stride out_stride), or with `slot` to
-// out[s][slot[kx * P + ky]] (the representative-slot layout).
+// out[s][slot[kx * P + ky]] (the representative-slot layout; the transform
+// then lands in the work vector and leaves as mirror pairs).
 template <typename R, int P, bool SLOT, bool ZIN>
 __global__ void __launch_bounds__(kThreads) k_col_fwd(const cx<R>* __restrict__ T, int tstride,
                                                       int64_t tslice, int n_in, int ncols,
@@ -614,10 +631,29 @@ __global__ void __launch_bounds__(kThreads) k_col_fwd(const cx<R>* __restrict__ 
   pdl_wait();
   __syncthreads();
   auto ld = [&](int y) -> cx<R> { return (ok && y < n_in) ? src[y] : mk<R>(0, 0); };
-  auto st = [&](int y, cx<R> val) {
-    if (ok) dst[SLOT ? __ldg(sl + y) : kx * P + y] = val;
-  };
-  run_passes<R, P, 0, false, true, true, ZIN>(bufs + v * SH::VSTR, tw, tid, ld, st);
+  if constexpr (SLOT) {
+    cx<R>* b = bufs + v * SH::VSTR;
+    NoStore<R> ns;
+    run_passes<R, P, 0, false, true, false, ZIN>(b, tw, tid, ld, ns);  // ends with a barrier
+    if (ok) {
+#pragma unroll
+      for (int i = 0; i < (P / 2 + SH::TPV) / SH::TPV; ++i) {
+        const int y = tid + i * SH::TPV;
+        if (y > P / 2) break;
+        const int s0 = __ldg(sl + y);
+        if (y == 0 || y == P / 2) {
+          dst[s0] = b[pidx(y)];
+          continue;
+        }
+        slot_store_pair(dst, s0, __ldg(sl + P - y), b[pidx(y)], b[pidx(P - y)]);
+      }
+    }
+  } else {
+    auto st = [&](int y, cx<R> val) {
+      if (ok) dst[kx * P + y] = val;
+    };
+    run_passes<R, P, 0, false, true, true, ZIN>(bufs + v * SH::VSTR, tw, tid, ld, st);
+  }
 }
 
 // Stage iii, column pass: in[s][kx][0..P) (or with `slot`, in[s][slot[kx * P +
@@ -649,6 +685,8 @@ __global__ void __launch_bounds__(kThreads) k_col_inv(const cx<R>* __restrict__ 
   auto st = [&](int y, cx<R> val) {
     if (ok && y < n_out) dst[y] = val;
   };
+  // (slot-mapped columns load element by element here: gathering mirror
+  // pairs as 16-byte loads through the work vector measured slower)
   run_passes<R, P, 0, true, true, true, false, HOUT>(bufs + v * SH::VSTR, tw, tid, ld, st);
 }
 
