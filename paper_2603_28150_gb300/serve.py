@@ -97,14 +97,17 @@ class Request:
 
 
 class CudaEngine:
-    """A plan with `slots` FISTA slots on its own stream (library generated on the device)."""
+    """A plan with `slots` FISTA slots on its own stream (library generated on
+    the device). `priority` is the CUDA stream priority (0 = default; lower
+    values are scheduled first when several engines have work queued)."""
 
-    def __init__(self, geom: Geometry, slots: int, power_iters: int = 50, force_complex=False):
+    def __init__(self, geom: Geometry, slots: int, power_iters: int = 50, force_complex=False,
+                 priority: int = 0):
         import torch
 
         from .pat import Medium, Plan
         self.geom, self.slots = geom, slots
-        self.stream = torch.cuda.Stream()
+        self.stream = torch.cuda.Stream(priority=priority)
         with torch.cuda.stream(self.stream):
             med = Medium(geom.c, geom.dx, geom.dx, geom.dx, geom.dt, geom.depth_period(), geom.z0)
             self.plan = Plan(geom.n, geom.n, geom.nz, geom.nt, geom.pad, geom.pad,
@@ -114,6 +117,15 @@ class CudaEngine:
             self.L = 1.01 * self.plan.power_norm(v0, power_iters)
         self.ref = None
         self.kernels = 0
+
+    @staticmethod
+    def priorities(ranks: int):
+        """Stream priorities for `ranks` engines, most urgent first: a short
+        step of a small geometry then starts at the next kernel boundary of a
+        large one instead of queueing behind its whole step."""
+        import torch
+        least, greatest = torch.cuda.Stream.priority_range()
+        return [max(greatest, least - (ranks - 1 - r)) for r in range(ranks)]
 
     @staticmethod
     def tensor_ok(geom: Geometry, slots: int) -> bool:
@@ -182,6 +194,12 @@ class Server:
         self.budget = budget_bytes
         self.slots = slots if isinstance(slots, dict) else {k: slots for k in self.geoms}
         self.factory = engine_factory
+        # smaller geometries (shorter steps) get the more urgent streams
+        order = sorted(self.geoms, key=lambda k: engine_factory.estimate(self.geoms[k],
+                                                                         self.slots[k]))
+        prio = engine_factory.priorities(len(order)) if hasattr(engine_factory, "priorities") \
+            else [0] * len(order)
+        self.priority = {k: prio[i] for i, k in enumerate(order)}
         self.max_inflight = max_inflight
         self.engines = {}
         self.active = collections.defaultdict(list)     # key -> requests in slot order
@@ -205,7 +223,7 @@ class Server:
             self._evict_idle(need)
         if self.used + need > self.budget:
             return None
-        eng = self.factory(self.geoms[key], self.slots[key])
+        eng = self.factory(self.geoms[key], self.slots[key], priority=self.priority[key])
         if self.t0 is not None:
             eng.set_origin(self.now())
         self.engines[key] = eng

@@ -16,8 +16,8 @@ class FakeEngine:
     closed = []
     per_step = 0.0
 
-    def __init__(self, geom, slots):
-        self.geom, self.slots = geom, slots
+    def __init__(self, geom, slots, priority=0):
+        self.geom, self.slots, self.priority = geom, slots, priority
         self.x = np.zeros((slots, 4))
         self.y = np.zeros((slots, 4))
         self.k = np.zeros(slots, dtype=int)
@@ -132,3 +132,18 @@ def test_memory_budget_evicts_idle_engines_and_rejects_oversized():
 def test_poisson_arrivals_rate():
     a = poisson_arrivals(20.0, 60.0, seed=0)
     assert 1000 < len(a) < 1400 and all(np.diff(a) > 0)
+
+
+def test_smaller_geometries_get_more_urgent_streams():
+    class PrioEngine(FakeEngine):
+        @staticmethod
+        def priorities(ranks):
+            return list(range(-ranks + 1, 1))   # most urgent (lowest) first
+
+    big = Geometry(24, 2, 4, 48)
+    srv = Server([big, GA, GC], budget_bytes=10 ** 9, slots=2, engine_factory=PrioEngine)
+    order = sorted([big, GA, GC], key=lambda g: g.n)
+    assert [srv.priority[g.key] for g in order] == [-2, -1, 0]
+    eng = srv._engine_for(order[0].key)
+    assert eng.priority == -2
+    srv.close()
