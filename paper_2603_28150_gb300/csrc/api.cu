@@ -352,8 +352,12 @@ cudaError_t gradient_dev(const Plan& p, const void* x, const void* y, void* grad
   const bool sl = tc_slots(p, batch);
   const int64_t row = sl ? slot_row(L) : L.Kpad;
   const int* slot = sl ? p.fold_slot : nullptr;
-  cudaError_t e = launch_spectrum(p, x, plane, L.nx, L.ny, p.X, row, batch * L.nz, s,
-                                  no_sampling(), slot);
+  // with a step that leaves the row transform of the next x in T, stage i
+  // here is its column pass alone
+  cudaError_t e = (step && step->next_T)
+                      ? launch_spectrum_cols(p, L.ny, p.X, row, batch * L.nz, s, slot)
+                      : launch_spectrum(p, x, plane, L.nx, L.ny, p.X, row, batch * L.nz, s,
+                                        no_sampling(), slot);
   if (e != cudaSuccess) return e;
   if ((e = launch_contract_fwd(p, p.X, p.Y, batch, s)) != cudaSuccess) return e;
   if ((e = launch_residual(p, p.Y, row, y, scan, batch * L.nt, sumsq, s, groups, group_sums,
@@ -482,7 +486,7 @@ cudaError_t fista_iter(pat_plan* pp, int batch, cudaStream_t s) {
   PlanExt& x = pp->x;
   // the gradient's last stage applies the step in place (no gradient array)
   const FistaStep step{p.vol_a, p.vol_b, x.scal, p.betas, p.iter_dev, x.res + 1, p.r2_dev,
-                       p.r2_cap, reinterpret_cast<unsigned*>(p.iter_dev + 1)};
+                       p.r2_cap, reinterpret_cast<unsigned*>(p.iter_dev + 1), true};
   return gradient_dev(p, p.vol_a, p.dat_b, nullptr, batch, s, x.res + 1, 0, nullptr, &step);
 }
 
@@ -901,6 +905,9 @@ int pat_fista_solve(pat_plan* plan, const void* y, void* x, int batch,
   if (iters > 0) {
     Graph* g = graph_for(plan, batch, &rc);
     if (!g) return rc;
+    // stage i's row transform of y_1 into T; each iteration's step kernel
+    // leaves the next one there
+    PAT_CUDA(launch_spectrum_rows(p, p.vol_a, (int64_t)L.ny * L.nx, L.nx, L.ny, batch * L.nz, s));
     kernels_per_iter = g->kernels;
     for (int k = 0; k < iters; ++k) PAT_CUDA(cudaGraphLaunch(g->exec, s));
   }

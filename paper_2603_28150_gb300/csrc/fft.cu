@@ -31,6 +31,30 @@ cudaError_t spectrum_t(const Plan& p, const R* in, int64_t in_stride, int nx_in,
 }
 
 template <typename R>
+cudaError_t spectrum_rows_t(const Plan& p, const R* in, int64_t in_stride, int nx_in, int ny_in,
+                            int S, cudaStream_t st) {
+  const Layout& L = p.L;
+  const int tstride = ny_in + (ny_in & 1);
+  const int64_t tslice = (int64_t)(L.px / 2 + 1) * tstride;
+  cx<R>* T = static_cast<cx<R>*>(p.T);
+  const cx<R>* twx = static_cast<const cx<R>*>(p.twx);
+  PAT_P_SWITCH(L.px, (FftLen<R, P_>::row_r2c(in, in_stride, nx_in, ny_in, T, tstride, tslice, S, twx, st,
+                                      no_sampling())))
+}
+
+template <typename R>
+cudaError_t spectrum_cols_t(const Plan& p, int ny_in, cx<R>* out, int64_t out_stride, int S,
+                            cudaStream_t st, const int* slot) {
+  const Layout& L = p.L;
+  const int tstride = ny_in + (ny_in & 1);
+  const int64_t tslice = (int64_t)(L.px / 2 + 1) * tstride;
+  cx<R>* T = static_cast<cx<R>*>(p.T);
+  const cx<R>* twy = static_cast<const cx<R>*>(p.twy);
+  PAT_P_SWITCH(L.py, (FftLen<R, P_>::col_fwd(T, tstride, tslice, ny_in, L.px / 2 + 1, S, out, out_stride,
+                                      twy, st, slot)))
+}
+
+template <typename R>
 cudaError_t image_t(const Plan& p, const cx<R>* in, int64_t in_stride, R* out, int64_t out_stride,
                     int S, const R* sub, double* sumsq, cudaStream_t st, int groups,
                     double* group_sums, Samp sm, const int* slot) {
@@ -121,6 +145,22 @@ cudaError_t image_step_t(const Plan& p, const cx<R>* in, int64_t in_stride, int 
 }
 
 }  // namespace
+
+cudaError_t launch_spectrum_rows(const Plan& p, const void* in, int64_t in_stride, int nx_in,
+                                 int ny_in, int S, cudaStream_t s) {
+  if (S <= 0) return cudaSuccess;
+  if (p.L.fp64)
+    return spectrum_rows_t<double>(p, static_cast<const double*>(in), in_stride, nx_in, ny_in, S, s);
+  return spectrum_rows_t<float>(p, static_cast<const float*>(in), in_stride, nx_in, ny_in, S, s);
+}
+
+cudaError_t launch_spectrum_cols(const Plan& p, int ny_in, void* out, int64_t out_stride, int S,
+                                 cudaStream_t s, const int* slot) {
+  if (S <= 0) return cudaSuccess;
+  if (p.L.fp64)
+    return spectrum_cols_t<double>(p, ny_in, static_cast<cx<double>*>(out), out_stride, S, s, slot);
+  return spectrum_cols_t<float>(p, ny_in, static_cast<cx<float>*>(out), out_stride, S, s, slot);
+}
 
 cudaError_t launch_image_step(const Plan& p, const void* in, int64_t in_stride, int S,
                               const FistaStep& f, cudaStream_t s, const int* slot) {

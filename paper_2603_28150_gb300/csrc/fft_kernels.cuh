@@ -857,10 +857,13 @@ __global__ void __launch_bounds__(kThreads) k_row_resid(cx<R>* __restrict__ T, i
 // in place of the gradient store: each gradient value g of the kept columns
 // updates y (momentum point) and xprev (x_{k-1}) of its voxel in place; the
 // last block to finish advances the iteration (see FistaStep). Only x < P/2
-// is formed (a plan's nx is at most P/2).
-template <typename R, int P>
+// is formed (a plan's nx is at most P/2). With NEXT the block then takes the
+// new momentum point y_{k+1} of its rows through the forward row transform
+// of stage i (as k_row_r2c does) and writes it over the same rows of T, so
+// the next iteration's stage i is its column pass alone.
+template <typename R, int P, bool NEXT>
 __global__ void __launch_bounds__(kThreads) k_row_c2r_step(
-    const cx<R>* __restrict__ T, int tstride, int64_t tslice, int nx, int ny, int64_t plane,
+    cx<R>* __restrict__ T, int tstride, int64_t tslice, int nx, int ny, int64_t plane,
     R* __restrict__ yv, R* __restrict__ xprev, const double* __restrict__ scal,
     const double* __restrict__ betas, int* __restrict__ iter, const double* __restrict__ r2_cur,
     double* __restrict__ r2_hist, int cap, unsigned* __restrict__ done,
@@ -895,6 +898,26 @@ __global__ void __launch_bounds__(kThreads) k_row_c2r_step(
   };
   SmemLoad<R> ld;
   run_passes<R, P, 0, true, false, true, false, true>(bufs + v * SH::VSTR, tw, tid, ld, st);
+  if constexpr (NEXT) {
+    // y_{k+1} of this block's rows, just written: packed as row y0 + i row y0 + 1
+    __syncthreads();
+    cx<R>* b = bufs + v * SH::VSTR;
+    for (int x = tid; x < P; x += SH::TPV)
+      b[pidx(x)] = x < nx ? mk<R>(ok0 ? ys[x] : (R)0, ok1 ? ys[nx + x] : (R)0) : mk<R>(0, 0);
+    __syncthreads();
+    NoStore<R> ns;
+    run_passes<R, P, 0, false, false, false, true>(b, tw, tid, ld, ns);  // zero half skipped
+    cx<R>* Ts = T + s * tslice;
+#pragma unroll 4
+    for (int i = threadIdx.x; i < SH::VPB * (P / 2 + 1); i += kThreads) {
+      const int vv = i % SH::VPB, kx = i / SH::VPB;
+      const int yy = 2 * (pair0 + vv);
+      if (yy >= ny) continue;
+      cx<R> A, B;
+      untangle(bufs[vv * SH::VSTR + pidx(kx)], bufs[vv * SH::VSTR + pidx((P - kx) % P)], &A, &B);
+      store_pair(Ts + (int64_t)kx * tstride + yy, A, B);  // tstride even: yy + 1 < tstride
+    }
+  }
   __shared__ bool last;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -1001,11 +1024,12 @@ cudaError_t FftLen<R, P>::row_c2r_step(const cx<R>* T, int tstride, int64_t tsli
                                        int64_t plane, int S, const FistaStep& f, const cx<R>* tw,
                                        cudaStream_t st) {
   using SH = Shape<P>;
-  cudaError_t e = set_smem_attr<R, P>((const void*)k_row_c2r_step<R, P>);
+  auto fn = f.next_T ? k_row_c2r_step<R, P, true> : k_row_c2r_step<R, P, false>;
+  cudaError_t e = set_smem_attr<R, P>((const void*)fn);
   if (e != cudaSuccess) return e;
   const int pairs = (ny + 1) / 2;
   dim3 grid((pairs + SH::VPB - 1) / SH::VPB, S);
-  return launch_pdl(k_row_c2r_step<R, P>, grid, dim3(kThreads), smem_bytes<R, P>(), st, T, tstride,
+  return launch_pdl(fn, grid, dim3(kThreads), smem_bytes<R, P>(), st, const_cast<cx<R>*>(T), tstride,
                     tslice, nx, ny, plane, static_cast<R*>(f.y), static_cast<R*>(f.xprev), f.scal,
                     f.betas, f.iter, f.r2_cur, f.r2_hist, f.cap, f.done, tw);
 }

@@ -340,11 +340,19 @@ struct FistaStep {
   double* r2_hist;
   int cap;
   unsigned* done;
+  bool next_T;  // also write the row transform of y_{k+1} over the rows of T
+                // (the next iteration's stage i then runs its column pass only)
 };
 // Stage iii over the depth slices of `S` = batch * nz spectra with the FISTA
 // step in place of the gradient store.
 cudaError_t launch_image_step(const Plan& p, const void* in, int64_t in_stride, int S,
                               const FistaStep& f, cudaStream_t s, const int* slot);
+// Stage i split in its two passes: rows of the real slices into the plan's T,
+// and the column pass from T (launch_spectrum runs both).
+cudaError_t launch_spectrum_rows(const Plan& p, const void* in, int64_t in_stride, int nx_in,
+                                 int ny_in, int S, cudaStream_t s);
+cudaError_t launch_spectrum_cols(const Plan& p, int ny_in, void* out, int64_t out_stride, int S,
+                                 cudaStream_t s, const int* slot);
 // Contractions over the resident table (tensor cores when the plan has the
 // split tables and batch >= tc_min_batch).
 cudaError_t launch_contract_fwd(const Plan& p, const void* X, void* Y, int batch, cudaStream_t s);
