@@ -437,7 +437,10 @@ int pat_shard_layout(const pat_geometry* g, int fold, int rank, int world, pat_s
 
 /* A plan holding only this rank's rows of the library generated from `m`
  * (as pat_plan_create_kspace; single precision, max_batch = 1). It runs only
- * the pat_shard_* stages (other operator entry points return PAT_ERR_ARG). */
+ * the pat_shard_* stages (other operator entry points return PAT_ERR_ARG).
+ * Its workspace holds no spectra, object or data buffers (the exchange
+ * buffers are the caller's): twiddles, the FFT intermediate of
+ * max(nz, nt) / world slices, reduction scratch and scalars. */
 int pat_plan_create_kspace_shard(const pat_geometry* g, const pat_medium* m, int rank, int world,
                                  pat_stream stream, pat_plan** out);
 int pat_plan_shard_info(const pat_plan* plan, pat_shard_info* info);

@@ -164,22 +164,30 @@ constexpr size_t kWsAlign = 256;
 
 // Walks the workspace regions of a plan in their fixed order, each aligned to
 // 256 bytes; with `base` the plan's pointers are set to their regions.
-// `with_io` adds the host-pointer staging buffers. Returns the bytes spanned.
-size_t ws_walk(pat_plan* pp, unsigned char* base, bool with_io) {
+// `with_io` adds the host-pointer staging buffers. `lean_slices` > 0 gives
+// the arena of a frequency shard, whose spectra are the caller's exchange
+// buffers: only the twiddles, an FFT intermediate of that many slices, the
+// reduction scratch and the scalars (every other pointer stays NULL).
+// Returns the bytes spanned.
+size_t ws_walk(pat_plan* pp, unsigned char* base, bool with_io, int64_t lean_slices = 0) {
   Plan& p = pp->p;
   PlanExt& x = pp->x;
   const Layout& L = p.L;
+  const bool lean = lean_slices > 0;
   const size_t cs = 2 * L.rsize;
-  const int64_t smax = (int64_t)L.max_batch * std::max(L.nz, L.nt);
-  const size_t xy = (size_t)smax * spectrum_row_cap(L) * cs;
+  const int64_t smax = lean ? lean_slices : (int64_t)L.max_batch * std::max(L.nz, L.nt);
+  const size_t xy = lean ? 0 : (size_t)smax * spectrum_row_cap(L) * cs;
   const size_t tb = (size_t)smax * L.tslice * cs;
-  const size_t vol = (size_t)L.max_batch * L.nz * L.ny * L.nx * L.rsize;
-  const size_t dat = (size_t)L.max_batch * L.nt * L.ny * L.nx * L.rsize;
+  const size_t vol = lean ? 0 : (size_t)L.max_batch * L.nz * L.ny * L.nx * L.rsize;
+  const size_t dat = lean ? 0 : (size_t)L.max_batch * L.nt * L.ny * L.nx * L.rsize;
   const int partials = std::max(kReduceBlocks, c2r_partials_bound(L));
-  const size_t sb = sizeof(double) * L.max_batch;
+  const size_t sb = lean ? 0 : sizeof(double) * L.max_batch;
+  const int hist = lean ? 0 : kHistCap;
   size_t off = 0;
   auto take = [&](auto** dst, size_t bytes) {
-    if (base) *dst = reinterpret_cast<std::remove_pointer_t<decltype(dst)>>(base + off);
+    if (base) {
+      *dst = bytes ? reinterpret_cast<std::remove_pointer_t<decltype(dst)>>(base + off) : nullptr;
+    }
     off += (bytes + kWsAlign - 1) / kWsAlign * kWsAlign;
   };
   take(&p.twx, (size_t)L.px * cs);
@@ -201,18 +209,18 @@ size_t ws_walk(pat_plan* pp, unsigned char* base, bool with_io) {
   take(&x.slots.invL, sb);
   take(&x.slots.lamL, sb);
   take(&x.slots.r2, sb);
-  take(&x.slots.k, sizeof(int) * L.max_batch);
-  take(&p.betas, sizeof(double) * kHistCap);
-  take(&p.r2_dev, sizeof(double) * kHistCap);
+  take(&x.slots.k, lean ? 0 : sizeof(int) * L.max_batch);
+  take(&p.betas, sizeof(double) * hist);
+  take(&p.r2_dev, sizeof(double) * hist);
   take(&p.tc_err, sizeof(int));
-  if (with_io) {
+  if (with_io && !lean) {
     take(&x.io_obj[0], vol);
     take(&x.io_obj[1], vol);
     take(&x.io_dat, dat);
   }
   if (base) {
     x.c2r_partials = partials;
-    p.betas_cap = p.r2_cap = kHistCap;
+    p.betas_cap = p.r2_cap = hist;
   }
   return off;
 }
@@ -228,10 +236,10 @@ int64_t workspace_bytes(const Layout& L, bool with_io) {
 // Carves the workspace from `user` (caller-owned device memory of ws_bytes)
 // or from one block the plan allocates, and initialises what must start at
 // zero or at fixed values.
-int setup_workspace(pat_plan* pp, void* user, size_t ws_bytes) {
+int setup_workspace(pat_plan* pp, void* user, size_t ws_bytes, int64_t lean_slices = 0) {
   Plan& p = pp->p;
   const bool ext = user != nullptr;
-  const size_t need = ws_walk(pp, nullptr, ext);
+  const size_t need = ws_walk(pp, nullptr, ext, lean_slices);
   if (ext) {
     if (!is_device_ptr(user)) return fail(PAT_ERR_ARG, "workspace is not device memory");
     if (reinterpret_cast<uintptr_t>(user) % kWsAlign)
@@ -245,7 +253,7 @@ int setup_workspace(pat_plan* pp, void* user, size_t ws_bytes) {
     PAT_CUDA(dev_alloc(&p.ws_base, need));
   }
   p.ws_cap = ext ? ws_bytes : need;
-  p.ws_used = ws_walk(pp, p.ws_base, ext);
+  p.ws_used = ws_walk(pp, p.ws_base, ext, lean_slices);
   p.ws_bytes = p.ws_used;
   PAT_CUDA(cudaMemset(p.iter_dev, 0, 3 * sizeof(int)));
   PAT_CUDA(cudaMemset(p.tc_err, 0, sizeof(int)));
@@ -274,7 +282,7 @@ struct AllocHook {
 };
 
 int create_common(const pat_geometry* g, void* ws, size_t ws_bytes, pat_plan** out,
-                  pat_plan** pp_out) {
+                  pat_plan** pp_out, int64_t lean_slices = 0) {
   if (!out) return fail(PAT_ERR_ARG, "out is NULL");
   *out = nullptr;
   int rc = validate(g);
@@ -283,7 +291,7 @@ int create_common(const pat_geometry* g, void* ws, size_t ws_bytes, pat_plan** o
   if (!pp) return fail(PAT_ERR_OOM, "host allocation of the plan failed");
   pp->p.L = make_layout(g);
   pp->p.tc_spin = kTcSpinDefault;
-  if ((rc = setup_workspace(pp, ws, ws_bytes)) != PAT_OK) {
+  if ((rc = setup_workspace(pp, ws, ws_bytes, lean_slices)) != PAT_OK) {
     free_plan(pp);
     return rc;
   }
@@ -527,8 +535,9 @@ Graph* graph_for(pat_plan* pp, int batch, int* rc) {
 }  // namespace
 
 namespace pat {
-int plan_create_common(const pat_geometry* g, pat_plan** out, pat_plan** pp) {
-  return create_common(g, nullptr, 0, out, pp);
+int plan_create_common(const pat_geometry* g, pat_plan** out, pat_plan** pp,
+                       int64_t lean_slices) {
+  return create_common(g, nullptr, 0, out, pp, lean_slices);
 }
 void plan_free(pat_plan* pp) { free_plan(pp); }
 }  // namespace pat

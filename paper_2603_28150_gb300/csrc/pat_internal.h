@@ -271,8 +271,11 @@ cudaError_t adjoint_dev(const Plan& p, const void* d, void* rho, int batch, cuda
 cudaError_t gradient_dev(const Plan& p, const void* x, const void* y, void* grad, int batch,
                          cudaStream_t s, double* sumsq, int groups = 0,
                          double* group_sums = nullptr, const FistaStep* step = nullptr);
-// Plan shell with its workspace (api.cu) and its release.
-int plan_create_common(const pat_geometry* g, pat_plan** out, pat_plan** pp);
+// Plan shell with its workspace (api.cu) and its release; lean_slices > 0
+// gives a frequency shard's arena (no spectra, object or data buffers; an FFT
+// intermediate of lean_slices slices).
+int plan_create_common(const pat_geometry* g, pat_plan** out, pat_plan** pp,
+                       int64_t lean_slices = 0);
 void plan_free(pat_plan* pp);
 // Records the kernel nodes of `graph`; instantiates it.
 cudaError_t instantiate_counted(cudaGraph_t graph, cudaGraphExec_t* exec, int* kernels);

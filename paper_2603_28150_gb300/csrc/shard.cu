@@ -180,7 +180,7 @@ int pat_plan_create_kspace_shard(const pat_geometry* g, const pat_medium* m, int
     int rc = partition(g, fold ? 1 : 0, rank, world, &pt, &members, &rep);
     if (rc != PAT_OK) return rc;
     pat_plan* pp = nullptr;
-    rc = plan_create_common(g, out, &pp);
+    rc = plan_create_common(g, out, &pp, std::max<int64_t>(pt.nz_local, pt.nt_local));
     if (rc != PAT_OK) return rc;
     Plan& p = pp->p;
     Layout& L = p.L;

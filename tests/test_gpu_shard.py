@@ -131,6 +131,10 @@ def test_sharded_benchmark_geometry():
               for r in range(world)]
     tb = [p.info()["table_bytes"] for p in shards]
     assert max(tb) <= full.info()["table_bytes"] // 2 + 32 * 256 * 64 * 4
+    # a shard's workspace: no spectra, object or data buffers, and an FFT
+    # intermediate of its own 128 time samples (the full plan's holds 256)
+    ws = [p.info()["workspace_bytes"] for p in shards]
+    assert max(ws) < full.info()["workspace_bytes"] // 4
     ex = LocalExchange(world)
     rho = cuda(synth.vessel_phantom(g.nx, g.nz, seed=0))
     y = cuda(synth.gaussian_field((g.nt, g.ny, g.nx), seed=1))
