@@ -69,6 +69,9 @@ enum {
   PAT_FLAG_FORCE_COMPLEX = 2, /* keep the complex table even when it is real     */
   PAT_FLAG_NO_FOLD = 8,       /* keep one table row per bin even when the spectra have
                                  the D4 symmetry of radially symmetric kernels */
+  PAT_FLAG_NO_RADIAL = 16,    /* folded plans: keep one stored row per D4
+                                 representative even when representatives of equal
+                                 kx^2 + ky^2 have equal spectra */
   PAT_FLAG_BF16_SPLIT = 4     /* also build the split-BF16 tensor-core tables: calls
                                  with batch >= 2 contract 16 volumes per table pass on
                                  tcgen05 (BF16 hi/lo operands, FP32 accumulation).
@@ -132,8 +135,12 @@ typedef struct {
   int64_t tensor_table_bytes; /* device bytes of the split-BF16 tables (0 if not built) */
   int32_t tensor_min_batch;   /* batches >= this use the tensor-core contraction (0: never) */
   int32_t folded;             /* 1: one table row per D4 representative {|kx|, |ky|} */
-  int64_t table_rows;         /* stored frequency rows: representatives if folded, else bins */
+  int64_t table_rows;         /* frequency rows: representatives if folded, else bins */
   int32_t workspace_external; /* 1: the workspace is caller-owned memory */
+  int32_t radial;             /* 1: folded, and representatives with equal kx^2 + ky^2
+                                 share one stored row (see pat_fold_blocks) */
+  int64_t stored_rows;        /* rows held in device memory (padded to 32):
+                                 table_bytes = stored_rows * nt * nz * element size */
 } pat_plan_info_t;
 
 /* FISTA settings (Eq. 12-14; Beck & Teboulle's constant-step scheme).
@@ -175,13 +182,20 @@ typedef struct {
  * max |Hh|) under ky -> -ky and kx <-> ky -- kernels with the radial symmetry
  * of Eq. 5 -- is stored once per representative {|kx|, |ky|} ("folded", ~4x
  * fewer bytes; the bins of a representative share its row) unless
- * PAT_FLAG_NO_FOLD is set. Synchronises `stream` before returning.
+ * PAT_FLAG_NO_FOLD is set. A folded table whose representatives of equal
+ * kx^2 + ky^2 also agree (to the same 1e-6) -- spectra that depend on |k| only,
+ * as Eq. 5's do for a homogeneous medium on an isotropic grid -- keeps one
+ * stored row per radius group (pat_fold_blocks; ~30 % fewer bytes at P = 256)
+ * unless PAT_FLAG_NO_RADIAL is set. Synchronises `stream` before returning.
  * Table source: Sec. 3.2. */
 int pat_plan_create(const pat_geometry* g, const void* table, pat_table_format fmt,
                     pat_stream stream, pat_plan** out);
 
 /* Builds a plan whose library is generated on the device from `m` (formula
- * above; Eq. 1-2 and the single-solve reciprocity construction of Sec. 3.2). */
+ * above; Eq. 1-2 and the single-solve reciprocity construction of Sec. 3.2).
+ * The generated spectra depend on kx^2 + ky^2 (and z, t) only, so with
+ * dx = dy on a square padded grid the plan is folded and radial (unless
+ * PAT_FLAG_NO_FOLD / PAT_FLAG_NO_RADIAL). */
 int pat_plan_create_kspace(const pat_geometry* g, const pat_medium* m,
                            pat_stream stream, pat_plan** out);
 
@@ -425,6 +439,27 @@ typedef struct {
   int64_t slot_width;         /* W: complex values per exchange row */
   int64_t bins;               /* frequency bins (px/2 + 1) py */
 } pat_shard_info;
+
+/* Host only (no device call): the block layout of the CUDA-core contraction
+ * of a folded P x P plan (D4 representatives u as enumerated by the library:
+ * a = 0..P/2, b = a..P/2, representative (kx, ky) = (a, b), up to 4 bins).
+ * The table is stored as chunks of 32 rows; block j of the contraction reads
+ * chunk rb_chunk[j], and its lane l handles representative rb_rep[32 j + l]
+ * (-1 = none) with the spectra of stored row 32 rb_chunk[j] + l. With
+ * `radial` = 0 block j reads chunk j and handles representatives 32 j ..
+ * 32 j + 31. With `radial` = 1 representatives are grouped by a^2 + b^2: the
+ * m representatives of a radius sit at the same lane of m consecutive blocks
+ * that share one chunk, whose row holds the spectra of the radius's first
+ * representative (the blocks' table reads coincide, so the stored table shrinks
+ * by the shared rows); when that would not store fewer chunks than the
+ * identity layout (small P: every group size pads its last chunk) the identity
+ * layout is returned. Outputs: *nrb blocks, *nch chunks, and (optional, host
+ * arrays) rb_rep[32 nrb], rb_chunk[nrb], row_rep[32 nch] (representative
+ * whose spectra fill each stored row, -1 = unused) and rep_row[U] (stored row
+ * of each representative, U = (P/2 + 1)(P/2 + 2) / 2). Call with NULL arrays
+ * to get the sizes. PAT_ERR_ARG for P not a supported even length. */
+int pat_fold_blocks(int P, int radial, int64_t* nrb, int64_t* nch, int32_t* rb_rep,
+                    int32_t* rb_chunk, int32_t* row_rep, int32_t* rep_row);
 
 /* Host only (no device call): the partition of rank `rank` of `world` for a
  * library stored folded (`fold` = 1) or per bin. Optional outputs (host

@@ -63,7 +63,8 @@ int validate(const pat_geometry* g) {
   if (g->px < 2 * g->nx - 1 || g->py < 2 * g->ny - 1)
     return fail(PAT_ERR_ARG, "padding too small for linear convolution: need px >= 2nx-1, py >= 2ny-1");
   if (g->max_batch < 1) return fail(PAT_ERR_ARG, "max_batch must be >= 1");
-  if (g->flags & ~(PAT_FLAG_FP64 | PAT_FLAG_FORCE_COMPLEX | PAT_FLAG_BF16_SPLIT | PAT_FLAG_NO_FOLD))
+  if (g->flags & ~(PAT_FLAG_FP64 | PAT_FLAG_FORCE_COMPLEX | PAT_FLAG_BF16_SPLIT | PAT_FLAG_NO_FOLD |
+                   PAT_FLAG_NO_RADIAL))
     return fail(PAT_ERR_ARG, "unknown flags");
   const int64_t smax = (int64_t)g->max_batch * std::max(g->nz, g->nt);
   if (smax > 65535) return fail(PAT_ERR_UNSUPPORTED, "max_batch * max(nz, nt) must be <= 65535");
@@ -104,8 +105,9 @@ void free_plan(pat_plan* pp) {
   }
   // the plan's own memory: the table side, buffers allocated on first use,
   // and the workspace arena unless the caller owns it
-  void* owned[] = {p.table,         p.tc_fwd,        p.tc_adj,    p.fold_members, p.fold_rep,
-                   p.fold_slot,     p.shard_zmap,    p.shard_tmap, p.shard_members};
+  void* owned[] = {p.table,      p.tc_fwd,     p.tc_adj,     p.fold_members, p.fold_rep,
+                   p.fold_slot,  p.rb_members, p.rb_chunk,   p.rep_row,      p.shard_zmap,
+                   p.shard_tmap, p.shard_members};
   for (void* b : owned) dev_free(b);
   if (x.io_heap) {
     dev_free(x.io_obj[0]);
@@ -569,7 +571,8 @@ int pat_plan_create_with_workspace(const pat_geometry* g, const void* table, pat
   int rc = create_common(g, workspace, ws_bytes, out, &pp);
   if (rc != PAT_OK) return rc;
   rc = build_table_from_source(pp->p, table, fmt, (g->flags & PAT_FLAG_FORCE_COMPLEX) != 0,
-                               (g->flags & PAT_FLAG_NO_FOLD) == 0, (cudaStream_t)stream);
+                               (g->flags & PAT_FLAG_NO_FOLD) == 0,
+                               (g->flags & PAT_FLAG_NO_RADIAL) == 0, (cudaStream_t)stream);
   if (rc == PAT_OK) rc = build_tensor_tables(pp, g->flags, (cudaStream_t)stream);
   if (rc != PAT_OK) {
     free_plan(pp);
@@ -599,7 +602,8 @@ int pat_plan_create_kspace_with_workspace(const pat_geometry* g, const pat_mediu
   int rc = create_common(g, workspace, ws_bytes, out, &pp);
   if (rc != PAT_OK) return rc;
   rc = build_table_kspace(pp->p, *m, (g->flags & PAT_FLAG_FORCE_COMPLEX) != 0,
-                          (g->flags & PAT_FLAG_NO_FOLD) == 0, (cudaStream_t)stream);
+                          (g->flags & PAT_FLAG_NO_FOLD) == 0,
+                          (g->flags & PAT_FLAG_NO_RADIAL) == 0, (cudaStream_t)stream);
   if (rc == PAT_OK) rc = build_tensor_tables(pp, g->flags, (cudaStream_t)stream);
   if (rc != PAT_OK) {
     free_plan(pp);
@@ -681,6 +685,8 @@ int pat_plan_info(const pat_plan* plan, pat_plan_info_t* info) {
   info->tensor_min_batch = p.tc_fwd ? p.tc_min_batch : 0;
   info->folded = p.L.fold ? 1 : 0;
   info->table_rows = p.L.fold ? p.L.U : p.L.K;
+  info->radial = p.L.fold && p.L.radial ? 1 : 0;
+  info->stored_rows = 32 * (p.L.fold ? p.L.nch : p.L.nkb);
   return PAT_OK;
 }
 

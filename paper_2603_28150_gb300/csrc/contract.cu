@@ -209,8 +209,11 @@ __global__ void __launch_bounds__(kWarps * 32, (sizeof(R) == 4 && !CPLX && VB ==
 // ---- D4-folded real tables ----------------------------------------------------
 // A CTA owns 32 representatives {|kx|, |ky|} (one per lane); the table row of
 // a representative is read once and applied to each of its (up to 4) bins,
-// whose bin indices come from `members` (-1 = absent). One volume per
-// blockIdx.y; every volume streams the (folded) table once.
+// whose bin indices come from `members` ([block][lane][4], -1 = absent). CTA j
+// reads stored chunk chunk[j] of 32 rows (chunk j when `chunk` is NULL): with
+// radial sharing the CTAs of one radius group read the same chunk at about
+// the same time, so DRAM delivers it once and L2 serves the others. One
+// volume per blockIdx.y; every volume streams the (folded) table once.
 constexpr int kRT = 4;   // forward: time samples per register block
 constexpr int kTC = 32;  // adjoint: time samples per shared D tile
 
@@ -218,14 +221,14 @@ constexpr int kTC = 32;  // adjoint: time samples per shared D tile
 // z-group it loads kRT table float4s and the 4 members' X from shared memory.
 __global__ void __launch_bounds__(kWarps * 32, 2)
     k_fold_fwd(const float4* __restrict__ table, const int4* __restrict__ members,
-               const cx<float>* __restrict__ X, cx<float>* __restrict__ Y, int nz, int nt,
-               int nzg, int64_t U, int64_t Kpad) {
+               const int* __restrict__ chunk, const cx<float>* __restrict__ X,
+               cx<float>* __restrict__ Y, int nz, int nt, int nzg, int64_t Kpad) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<float>* xs = reinterpret_cast<cx<float>*>(smem_raw);  // [4][nzp][32]
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t ub = blockIdx.x, u = ub * 32 + lane;
+  const int64_t ub = blockIdx.x;
   const int b = blockIdx.y, nzp = nzg * 4;
-  const int4 mem = u < U ? members[u] : make_int4(-1, -1, -1, -1);
+  const int4 mem = members[ub * 32 + lane];
   const int bins[4] = {mem.x, mem.y, mem.z, mem.w};
   const cx<float>* Xb = X + (int64_t)b * nz * Kpad;
   pdl_wait();
@@ -236,7 +239,8 @@ __global__ void __launch_bounds__(kWarps * 32, 2)
           (bins[m] >= 0 && z < nz) ? Xb[(int64_t)z * Kpad + bins[m]] : mk<float>(0.f, 0.f);
   }
   __syncthreads();
-  const float4* tb = table + ub * nt * (int64_t)nzg * 32 + lane;
+  const int64_t cb = chunk ? chunk[ub] : ub;
+  const float4* tb = table + cb * nt * (int64_t)nzg * 32 + lane;
   for (int t0 = warp * kRT; t0 < nt; t0 += kWarps * kRT) {
     cx<float> acc[kRT][4];
 #pragma unroll
@@ -282,17 +286,18 @@ __global__ void __launch_bounds__(kWarps * 32, 2)
 template <int GPW>
 __global__ void __launch_bounds__(kWarps * 32, 2)
     k_fold_adj(const float4* __restrict__ table, const int4* __restrict__ members,
-               const cx<float>* __restrict__ D, cx<float>* __restrict__ Z, int nz, int nt,
-               int nzg, int64_t U, int64_t Kpad) {
+               const int* __restrict__ chunk, const cx<float>* __restrict__ D,
+               cx<float>* __restrict__ Z, int nz, int nt, int nzg, int64_t Kpad) {
   __shared__ cx<float> ds[kTC][4][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t ub = blockIdx.x, u = ub * 32 + lane;
+  const int64_t ub = blockIdx.x;
   const int b = blockIdx.y;
   const int gbase = blockIdx.z * kWarps * GPW + warp;
-  const int4 mem = u < U ? members[u] : make_int4(-1, -1, -1, -1);
+  const int4 mem = members[ub * 32 + lane];
   const int bins[4] = {mem.x, mem.y, mem.z, mem.w};
   const cx<float>* Db = D + (int64_t)b * nt * Kpad;
-  const float4* tb = table + ub * nt * (int64_t)nzg * 32 + lane;
+  const int64_t cb = chunk ? chunk[ub] : ub;
+  const float4* tb = table + cb * nt * (int64_t)nzg * 32 + lane;
   cx<float> acc[GPW][4][4];
 #pragma unroll
   for (int j = 0; j < GPW; ++j)
@@ -363,22 +368,22 @@ cudaError_t fold_fwd(const Plan& p, const void* X, void* Y, int batch, cudaStrea
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  dim3 grid((unsigned)L.nub, (unsigned)batch);
+  dim3 grid((unsigned)L.nrb, (unsigned)batch);
   return launch_pdl(k_fold_fwd, grid, dim3(kWarps * 32), smem, s,
-                    static_cast<const float4*>(p.table),
-                    reinterpret_cast<const int4*>(p.fold_members), static_cast<const cx<float>*>(X),
-                    static_cast<cx<float>*>(Y), L.nz, L.nt, L.nzg, L.U, L.Kpad);
+                    static_cast<const float4*>(p.table), reinterpret_cast<const int4*>(p.rb_members),
+                    static_cast<const int*>(p.rb_chunk), static_cast<const cx<float>*>(X),
+                    static_cast<cx<float>*>(Y), L.nz, L.nt, L.nzg, L.Kpad);
 }
 
 cudaError_t fold_adj(const Plan& p, const void* D, void* Z, int batch, cudaStream_t s) {
   const Layout& L = p.L;
   constexpr int GPW = 2;
-  dim3 grid((unsigned)L.nub, (unsigned)batch,
+  dim3 grid((unsigned)L.nrb, (unsigned)batch,
             (unsigned)((L.nzg + kWarps * GPW - 1) / (kWarps * GPW)));
   return launch_pdl(k_fold_adj<GPW>, grid, dim3(kWarps * 32), 0, s,
-                    static_cast<const float4*>(p.table),
-                    reinterpret_cast<const int4*>(p.fold_members), static_cast<const cx<float>*>(D),
-                    static_cast<cx<float>*>(Z), L.nz, L.nt, L.nzg, L.U, L.Kpad);
+                    static_cast<const float4*>(p.table), reinterpret_cast<const int4*>(p.rb_members),
+                    static_cast<const int*>(p.rb_chunk), static_cast<const cx<float>*>(D),
+                    static_cast<cx<float>*>(Z), L.nz, L.nt, L.nzg, L.Kpad);
 }
 
 template <typename R, bool CPLX, int VB>

@@ -86,11 +86,16 @@ struct Layout {
   int tstride;         // ny rounded up to even (row stride of the FFT intermediate)
   int64_t tslice;      // (px/2 + 1) * tstride
   size_t rsize;        // sizeof(real_t)
-  size_t table_bytes;  // (fold ? nub : nkb) * nt * nzg * 32 * 16
+  size_t table_bytes;  // (fold ? nch : nkb) * nt * nzg * 32 * 16
   // D4 folding: the spectra depend only on {|kx|, |ky|}; one table row per
   // representative (a, b), 0 <= a <= b <= P/2, shared by up to 4 bins.
   bool fold = false;
   int64_t U = 0, Upad = 0, nub = 0;  // representatives, padded to 32, blocks of 32
+  // Blocks of the CUDA-core contraction and stored chunks of 32 rows (equal
+  // to nub without radial sharing; with it, the blocks of one radius group
+  // share a chunk: representatives of equal a^2 + b^2 have one stored row).
+  int64_t nrb = 0, nch = 0;
+  bool radial = false;
   // Measurement operator: data live on the scan grid x = ox + sx i, y = oy + sy j
   // (i < mx, j < my) of the sensor grid; sx = sy = 1 is the plain operator.
   int sx = 1, sy = 1, ox = 0, oy = 0, mx = 0, my = 0;
@@ -207,6 +212,13 @@ struct Plan {
   // representative u), so a representative's bins share one 32-byte sector.
   int* fold_slot = nullptr;     // [K]
   double fold_deviation = 0;    // max |Hh(bin) - Hh(representative)| seen (stored scale)
+  double radial_deviation = 0;  // max |Hh(representative) - Hh(its stored row)| (user tables)
+  // Block maps of the CUDA-core contraction (device): the bins of the
+  // representative of each block slot (-1 = none), the stored chunk of each
+  // block, and (radial plans) the stored row of each representative.
+  int* rb_members = nullptr;    // [nrb * 32][4]
+  int* rb_chunk = nullptr;      // [nrb]; NULL = block j reads chunk j
+  int* rep_row = nullptr;       // [U]; NULL = representative u is row u
   // split-BF16 tensor-core tables (tc_contract.cu)
   void* tc_fwd = nullptr;
   void* tc_adj = nullptr;
@@ -386,9 +398,9 @@ constexpr int64_t kTcSpinDefault = int64_t(1) << 22;
 // Table construction (table.cu). Both allocate p.table and set the
 // representation (real or complex) of p.L.
 int build_table_from_source(Plan& p, const void* table, pat_table_format fmt, bool force_complex,
-                            bool allow_fold, cudaStream_t s);
+                            bool allow_fold, bool allow_radial, cudaStream_t s);
 int build_table_kspace(Plan& p, const pat_medium& m, bool force_complex, bool allow_fold,
-                       cudaStream_t s);
+                       bool allow_radial, cudaStream_t s);
 // Whether a k-space library of this layout is stored folded (real table on a
 // square grid, dx = dy, single precision, folding allowed).
 bool kspace_folds(const Layout& L, const pat_medium& m, bool allow_fold);
@@ -412,15 +424,28 @@ inline void set_representation(Layout& L, bool real, bool fold = false) {
   const size_t esz = (L.fp64 ? 8 : 4) * (real ? 1 : 2);
   L.zg = (int)(16 / esz);
   L.nzg = (L.nz + L.zg - 1) / L.zg;
-  L.table_bytes = (size_t)(fold ? L.nub : L.nkb) * L.nt * L.nzg * 32 * 16;
+  L.table_bytes = (size_t)(fold ? L.nch : L.nkb) * L.nt * L.nzg * 32 * 16;
 }
 
 // D4 folding is possible for real single-precision tables on square padded
 // grids (the symmetry itself is checked or guaranteed by the table builder).
 inline bool fold_possible(const Layout& L) { return L.real && !L.fp64 && L.px == L.py; }
 // Builds the folding maps of p (host enumeration, device copies) and sets
-// L.U / Upad / nub; rep_bins (optional) receives each representative's own bin.
-int build_fold_maps(Plan& p, std::vector<int>* rep_bins);
+// L.U / Upad / nub; members (optional) receives the host copy of the
+// representatives' bins [Upad][4].
+int build_fold_maps(Plan& p, std::vector<int>* members);
+// Block layout of the CUDA-core contraction of a folded table (see
+// pat_fold_blocks): identity (one chunk per block) or radial sharing.
+struct FoldBlocks {
+  int64_t nrb = 0, nch = 0;
+  std::vector<int> rb_rep;    // [nrb * 32] representative of each block slot, -1 = none
+  std::vector<int> rb_chunk;  // [nrb] stored chunk of each block
+  std::vector<int> row_rep;   // [nch * 32] representative filling each stored row, -1 = none
+  std::vector<int> rep_row;   // [U] stored row of each representative
+};
+void fold_blocks(int P, const std::vector<int>& members, int64_t U, bool radial, FoldBlocks& fb);
+// Sets L.nrb / nch / radial and uploads the block maps of `fb` to p.
+int install_fold_blocks(Plan& p, const std::vector<int>& members, const FoldBlocks& fb);
 // Folds the sensors' temporal response r[0..nr) into the resident table
 // (causal convolution along time); synchronises `s`.
 int apply_sensor_response(Plan& p, const double* r, int nr, cudaStream_t s);

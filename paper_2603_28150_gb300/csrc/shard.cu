@@ -193,10 +193,10 @@ int pat_plan_create_kspace_shard(const pat_geometry* g, const pat_medium* m, int
       fill_maps(pt, L.K, members, rep, zmap.data(), tmap.data(), fold ? mloc.data() : nullptr);
       // the table of this shard: its rows only, in the plan's blocked layout
       set_representation(L, L.real, fold);
-      if (fold) {
+      if (fold) {  // one block per chunk of 32 rows (no radial sharing)
         L.U = pt.rows;
         L.Upad = pt.Wr;
-        L.nub = pt.Wr / 32;
+        L.nub = L.nrb = L.nch = pt.Wr / 32;
       }
       const int64_t blocks = pt.Wr / 32;
       L.table_bytes = (size_t)blocks * L.nt * L.nzg * 32 * 16;
@@ -289,7 +289,8 @@ int pat_shard_contract(pat_plan* plan, int adjoint, const void* in, void* out, p
     v.tc_min_batch = 0;
     v.L.Kpad = p.shard_W;
     if (p.L.fold) {
-      v.fold_members = p.shard_members;
+      v.rb_members = p.shard_members;  // block j reads chunk j (rb_chunk NULL)
+      v.rb_chunk = nullptr;
     } else {
       v.L.K = p.shard_rows;
       v.L.nkb = p.shard_Wr / 32;

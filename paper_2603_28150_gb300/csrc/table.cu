@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <vector>
 
 #include "pat_internal.h"
@@ -145,11 +146,12 @@ __global__ void k_kspace(int px, int py, int mz, int nz, int nt, int nzg, int ZG
   }
 }
 
-// max |T[k] - T[rep(k)]| over a real blocked table (bits of a non-negative double).
-__global__ void k_fold_check(const float* __restrict__ table, const int* __restrict__ rep,
-                             const int* __restrict__ members, int64_t K, int nt, int nzg,
+// max |T[ka[j]] - T[kb[j]]| over pairs of bins of a real blocked table, every
+// (t, z) (bits of a non-negative double).
+__global__ void k_pair_check(const float* __restrict__ table, const int* __restrict__ ka,
+                             const int* __restrict__ kb, int64_t npairs, int nt, int nzg,
                              unsigned long long* out) {
-  const int64_t n = K * nt * nzg * 4;
+  const int64_t n = npairs * nt * nzg * 4;
   double m = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -157,8 +159,8 @@ __global__ void k_fold_check(const float* __restrict__ table, const int* __restr
     const int64_t r = i >> 2;
     const int g = (int)(r % nzg);
     const int t = (int)((r / nzg) % nt);
-    const int64_t k = r / ((int64_t)nzg * nt);
-    const int64_t kr = members[4 * (int64_t)rep[k]];  // the representative's own bin
+    const int64_t j = r / ((int64_t)nzg * nt);
+    const int64_t k = ka[j], kr = kb[j];
     const float a = table[(((k >> 5) * nt + t) * nzg + g) * 128 + (k & 31) * 4 + q];
     const float b = table[(((kr >> 5) * nt + t) * nzg + g) * 128 + (kr & 31) * 4 + q];
     m = fmax(m, fabs((double)a - (double)b));
@@ -167,21 +169,19 @@ __global__ void k_fold_check(const float* __restrict__ table, const int* __restr
   if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
 }
 
-// folded[u] = full[bin of representative u] for every (t, z-group), real tables.
+// folded row r = full[row_bin[r]] (zero where row_bin[r] < 0) for every
+// (t, z-group), real tables.
 __global__ void k_fold_gather(const float4* __restrict__ full, float4* __restrict__ folded,
-                              const int* __restrict__ members, int64_t U, int64_t Upad, int nt,
-                              int nzg) {
-  const int64_t n = Upad * nt * nzg;
+                              const int* __restrict__ row_bin, int64_t rows, int nt, int nzg) {
+  const int64_t n = rows * nt * nzg;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int g = (int)(i % nzg);
     const int t = (int)((i / nzg) % nt);
     const int64_t u = i / ((int64_t)nzg * nt);
     float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (u < U) {
-      const int64_t k = members[4 * u];
-      v = full[(((k >> 5) * nt + t) * nzg + g) * 32 + (k & 31)];
-    }
+    const int64_t k = row_bin[u];
+    if (k >= 0) v = full[(((k >> 5) * nt + t) * nzg + g) * 32 + (k & 31)];
     folded[(((u >> 5) * nt + t) * nzg + g) * 32 + (u & 31)] = v;
   }
 }
@@ -253,7 +253,7 @@ __global__ void k_sensor_fir(S* __restrict__ table, int64_t blocks, int nt, int6
 
 int apply_sensor_response(Plan& p, const double* r, int nr, cudaStream_t s) {
   const Layout& L = p.L;
-  const int64_t blocks = L.fold ? L.nub : L.nkb;
+  const int64_t blocks = L.fold ? L.nch : L.nkb;  // stored chunks of 32 rows
   const int64_t inner = (int64_t)L.nzg * 32 * 16 / (int64_t)L.rsize;
   double* rd = nullptr;
   PAT_CUDA(dev_alloc(&rd, sizeof(double) * nr));
@@ -303,7 +303,90 @@ void fold_enumerate(int P, std::vector<int>& members, std::vector<int>& rep,
     }
 }
 
-int build_fold_maps(Plan& p, std::vector<int>* rep_bins) {
+static void radial_blocks(int P, const std::vector<int>& members, int64_t U, FoldBlocks& fb);
+
+void fold_blocks(int P, const std::vector<int>& members, int64_t U, bool radial, FoldBlocks& fb) {
+  if (radial) {
+    radial_blocks(P, members, U, fb);
+    if (fb.nch < (U + 31) / 32) return;
+    // every group size pads its last chunk: on small grids sharing can store
+    // more chunks than it saves, and then the identity layout is kept
+  }
+  fb = FoldBlocks();
+  fb.nrb = fb.nch = (U + 31) / 32;
+  fb.rb_rep.assign((size_t)fb.nrb * 32, -1);
+  fb.row_rep.assign((size_t)fb.nch * 32, -1);
+  fb.rep_row.assign((size_t)U, -1);
+  fb.rb_chunk.resize((size_t)fb.nrb);
+  for (int64_t j = 0; j < fb.nrb; ++j) fb.rb_chunk[j] = (int)j;
+  for (int64_t u = 0; u < U; ++u) fb.rb_rep[u] = fb.row_rep[u] = fb.rep_row[u] = (int)u;
+}
+
+// Radial sharing: representatives of equal a^2 + b^2 at the same lane of
+// consecutive blocks that read one chunk.
+static void radial_blocks(int P, const std::vector<int>& members, int64_t U, FoldBlocks& fb) {
+  fb = FoldBlocks();
+  fb.rep_row.assign((size_t)U, -1);
+  // representatives by radius a^2 + b^2 (a representative's own bin is a P + b)
+  std::map<int64_t, std::vector<int>> by_radius;
+  for (int64_t u = 0; u < U; ++u) {
+    const int64_t a = members[4 * u] / P, b = members[4 * u] % P;
+    by_radius[a * a + b * b].push_back((int)u);
+  }
+  // radii ordered by group size m, then radius; 32 radii of equal m per chunk,
+  // read by m consecutive blocks (lane l of block j: the j-th representative
+  // of the chunk's l-th radius)
+  std::map<size_t, std::vector<const std::vector<int>*>> by_size;
+  for (const auto& kv : by_radius) by_size[kv.second.size()].push_back(&kv.second);
+  for (const auto& sv : by_size) {
+    const size_t m = sv.first;
+    const auto& radii = sv.second;
+    for (size_t r0 = 0; r0 < radii.size(); r0 += 32) {
+      const int64_t ch = fb.nch++;
+      fb.row_rep.resize((size_t)fb.nch * 32, -1);
+      fb.rb_rep.resize((size_t)(fb.nrb + (int64_t)m) * 32, -1);
+      for (size_t j = 0; j < m; ++j) fb.rb_chunk.push_back((int)ch);
+      for (size_t l = 0; l < 32 && r0 + l < radii.size(); ++l) {
+        const std::vector<int>& reps = *radii[r0 + l];
+        fb.row_rep[(size_t)ch * 32 + l] = reps[0];
+        for (size_t j = 0; j < m; ++j) {
+          fb.rb_rep[((size_t)fb.nrb + j) * 32 + l] = reps[j];
+          fb.rep_row[reps[j]] = (int)(ch * 32 + (int64_t)l);
+        }
+      }
+      fb.nrb += (int64_t)m;
+    }
+  }
+}
+
+int install_fold_blocks(Plan& p, const std::vector<int>& members, const FoldBlocks& fb) {
+  Layout& L = p.L;
+  const bool radial = fb.nch != fb.nrb;
+  std::vector<int> rbm(fb.rb_rep.size() * 4, -1);
+  for (size_t v = 0; v < fb.rb_rep.size(); ++v)
+    if (fb.rb_rep[v] >= 0)
+      for (int i = 0; i < 4; ++i) rbm[4 * v + i] = members[4 * (size_t)fb.rb_rep[v] + i];
+  dev_free(p.rb_members);
+  dev_free(p.rb_chunk);
+  dev_free(p.rep_row);
+  p.rb_members = p.rb_chunk = p.rep_row = nullptr;
+  PAT_CUDA(dev_alloc(&p.rb_members, rbm.size() * sizeof(int)));
+  PAT_CUDA(cudaMemcpy(p.rb_members, rbm.data(), rbm.size() * sizeof(int), cudaMemcpyHostToDevice));
+  PAT_CUDA(dev_alloc(&p.rb_chunk, fb.rb_chunk.size() * sizeof(int)));
+  PAT_CUDA(cudaMemcpy(p.rb_chunk, fb.rb_chunk.data(), fb.rb_chunk.size() * sizeof(int),
+                      cudaMemcpyHostToDevice));
+  if (radial) {
+    PAT_CUDA(dev_alloc(&p.rep_row, fb.rep_row.size() * sizeof(int)));
+    PAT_CUDA(cudaMemcpy(p.rep_row, fb.rep_row.data(), fb.rep_row.size() * sizeof(int),
+                        cudaMemcpyHostToDevice));
+  }
+  L.nrb = fb.nrb;
+  L.nch = fb.nch;
+  L.radial = radial;
+  return PAT_OK;
+}
+
+int build_fold_maps(Plan& p, std::vector<int>* members_out) {
   Layout& L = p.L;
   std::vector<int> members, rep, slot;
   fold_enumerate(L.px, members, rep, slot);
@@ -313,10 +396,7 @@ int build_fold_maps(Plan& p, std::vector<int>* rep_bins) {
   members.resize((size_t)L.Upad * 4, -1);
   for (int64_t k = 0; k < L.K; ++k)
     if (rep[k] < 0) return fail(PAT_ERR_CUDA, "internal: a bin without representative");
-  if (rep_bins) {
-    rep_bins->resize((size_t)L.U);
-    for (int64_t u = 0; u < L.U; ++u) (*rep_bins)[u] = members[4 * u];
-  }
+  if (members_out) *members_out = members;
   PAT_CUDA(dev_alloc(&p.fold_slot, slot.size() * sizeof(int)));
   PAT_CUDA(cudaMemcpy(p.fold_slot, slot.data(), slot.size() * sizeof(int),
                       cudaMemcpyHostToDevice));
@@ -346,8 +426,38 @@ int device_of(const void* p) {
   return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) ? a.device : -1;
 }
 
+// max over pairs j and every (t, z) of |T[ka[j]] - T[kb[j]]| of the real
+// blocked (per-bin) table p.table; synchronises `s`.
+static int max_pair_deviation(Plan& p, const std::vector<int>& ka, const std::vector<int>& kb,
+                              cudaStream_t s, double* out) {
+  const Layout& L = p.L;
+  const int64_t n = (int64_t)ka.size();
+  int *a_d = nullptr, *b_d = nullptr;
+  unsigned long long* dev_max = nullptr;
+  cudaError_t e = dev_alloc(&a_d, ka.size() * sizeof(int));
+  if (e == cudaSuccess) e = dev_alloc(&b_d, kb.size() * sizeof(int));
+  if (e == cudaSuccess) e = dev_alloc(&dev_max, sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemcpy(a_d, ka.data(), ka.size() * sizeof(int), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(b_d, kb.data(), kb.size() * sizeof(int), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemsetAsync(dev_max, 0, sizeof(unsigned long long), s);
+  if (e == cudaSuccess && n > 0) {
+    k_pair_check<<<grid_for(n * L.nt * L.nzg * 4), 256, 0, s>>>(
+        static_cast<const float*>(p.table), a_d, b_d, n, L.nt, L.nzg, dev_max);
+    e = cudaGetLastError();
+  }
+  unsigned long long hm = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hm, dev_max, sizeof(hm), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  dev_free(a_d);
+  dev_free(b_d);
+  dev_free(dev_max);
+  if (e != cudaSuccess) return cuda_fail(e, "checking the symmetry of the table");
+  memcpy(out, &hm, 8);
+  return PAT_OK;
+}
+
 int build_table_from_source(Plan& p, const void* table, pat_table_format fmt, bool force_complex,
-                            bool allow_fold, cudaStream_t s) {
+                            bool allow_fold, bool allow_radial, cudaStream_t s) {
   Layout& L = p.L;
   const bool spatial = fmt == PAT_TABLE_SPATIAL_F64 || fmt == PAT_TABLE_SPATIAL_F32;
   const bool src64 = fmt == PAT_TABLE_SPATIAL_F64 || fmt == PAT_TABLE_SPECTRAL_C128;
@@ -478,37 +588,64 @@ int build_table_from_source(Plan& p, const void* table, pat_table_format fmt, bo
   PREP_CUDA(cudaStreamSynchronize(s));
   cleanup();
 
-  // D4 folding when every bin equals its representative (to 1e-6 of max |Hh|).
+  // D4 folding when every bin equals its representative (to 1e-6 of max |Hh|),
+  // then radial sharing when every representative also equals the first
+  // representative of its radius (same bound).
   if (allow_fold && fold_possible(L)) {
-    int rc = build_fold_maps(p, nullptr);
+    std::vector<int> members;
+    int rc = build_fold_maps(p, &members);
     if (rc != PAT_OK) return rc;
-    unsigned long long* dev_max = nullptr;
-    PAT_CUDA(dev_alloc(&dev_max, sizeof(unsigned long long)));
-    cudaError_t e = cudaMemsetAsync(dev_max, 0, sizeof(unsigned long long), s);
-    if (e == cudaSuccess) {
-      k_fold_check<<<grid_for(L.K * L.nt * L.nzg * 4), 256, 0, s>>>(
-          static_cast<const float*>(p.table), p.fold_rep, p.fold_members, L.K, L.nt, L.nzg,
-          dev_max);
-      e = cudaGetLastError();
+    const double tol = 1e-6 * p.table_max_abs / ((double)L.px * (double)L.py);
+    std::vector<int> ka((size_t)L.K), kb((size_t)L.K);
+    {
+      std::vector<int> mem, repk, slot;
+      fold_enumerate(L.px, mem, repk, slot);
+      for (int64_t k = 0; k < L.K; ++k) {
+        ka[k] = (int)k;
+        kb[k] = mem[4 * (size_t)repk[k]];  // the representative's own bin
+      }
     }
-    unsigned long long hm = 0;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&hm, dev_max, sizeof(hm), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    dev_free(dev_max);
-    if (e != cudaSuccess) return cuda_fail(e, "checking the D4 symmetry of the table");
-    double dmax;
-    memcpy(&dmax, &hm, 8);
+    double dmax = 0;
+    if ((rc = max_pair_deviation(p, ka, kb, s, &dmax)) != PAT_OK) return rc;
     p.fold_deviation = dmax;
-    if (dmax <= 1e-6 * p.table_max_abs / ((double)L.px * (double)L.py)) {
+    if (dmax <= tol) {
+      FoldBlocks fb;
+      bool radial = false;
+      if (allow_radial) {
+        fold_blocks(L.px, members, L.U, true, fb);
+        std::vector<int> ua((size_t)L.U), ub((size_t)L.U);
+        for (int64_t u = 0; u < L.U; ++u) {
+          ua[u] = members[4 * u];
+          ub[u] = members[4 * (size_t)fb.row_rep[fb.rep_row[u]]];
+        }
+        double rmax = 0;
+        if ((rc = max_pair_deviation(p, ua, ub, s, &rmax)) != PAT_OK) return rc;
+        p.radial_deviation = rmax;
+        radial = rmax <= tol;
+      }
+      if (!radial) fold_blocks(L.px, members, L.U, false, fb);
+      if ((rc = install_fold_blocks(p, members, fb)) != PAT_OK) return rc;
       Layout F = L;
       set_representation(F, true, true);
+      std::vector<int> row_bin(fb.row_rep.size(), -1);
+      for (size_t r = 0; r < row_bin.size(); ++r)
+        if (fb.row_rep[r] >= 0) row_bin[r] = members[4 * (size_t)fb.row_rep[r]];
       void* folded = nullptr;
-      PAT_CUDA(dev_alloc(&folded, F.table_bytes));
-      k_fold_gather<<<grid_for(F.Upad * F.nt * F.nzg), 256, 0, s>>>(
-          static_cast<const float4*>(p.table), static_cast<float4*>(folded), p.fold_members, F.U,
-          F.Upad, F.nt, F.nzg);
-      e = cudaGetLastError();
+      int* row_bin_d = nullptr;
+      cudaError_t e = dev_alloc(&folded, F.table_bytes);
+      if (e == cudaSuccess) e = dev_alloc(&row_bin_d, row_bin.size() * sizeof(int));
+      if (e == cudaSuccess)
+        e = cudaMemcpy(row_bin_d, row_bin.data(), row_bin.size() * sizeof(int),
+                       cudaMemcpyHostToDevice);
+      if (e == cudaSuccess) {
+        const int64_t rows = (int64_t)row_bin.size();
+        k_fold_gather<<<grid_for(rows * F.nt * F.nzg), 256, 0, s>>>(
+            static_cast<const float4*>(p.table), static_cast<float4*>(folded), row_bin_d, rows,
+            F.nt, F.nzg);
+        e = cudaGetLastError();
+      }
       if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      dev_free(row_bin_d);
       if (e != cudaSuccess) {
         dev_free(folded);
         return cuda_fail(e, "folding the table");
@@ -519,7 +656,8 @@ int build_table_from_source(Plan& p, const void* table, pat_table_format fmt, bo
     } else {
       dev_free(p.fold_members);
       dev_free(p.fold_rep);
-      p.fold_members = p.fold_rep = nullptr;
+      dev_free(p.fold_slot);
+      p.fold_members = p.fold_rep = p.fold_slot = nullptr;
     }
   }
   return PAT_OK;
@@ -527,17 +665,27 @@ int build_table_from_source(Plan& p, const void* table, pat_table_format fmt, bo
 }
 
 int build_table_kspace(Plan& p, const pat_medium& m, bool force_complex, bool allow_fold,
-                       cudaStream_t s) {
+                       bool allow_radial, cudaStream_t s) {
   Layout& L = p.L;
   if (L.fp64) return fail(PAT_ERR_UNSUPPORTED, "k-space generation builds single-precision tables");
   set_representation(L, !force_complex);
   // |k| depends on kx^2 + ky^2 only, so with dx = dy on a square grid the
-  // library is exactly D4-symmetric: generate one row per representative.
+  // library is exactly D4-symmetric, and representatives of equal kx^2 + ky^2
+  // have equal spectra: generate one row per stored row (per representative,
+  // or with radial sharing per radius).
   std::vector<int> bins;
   if (kspace_folds(L, m, allow_fold)) {
-    int rc = build_fold_maps(p, &bins);
+    std::vector<int> members;
+    int rc = build_fold_maps(p, &members);
     if (rc != PAT_OK) return rc;
+    FoldBlocks fb;
+    fold_blocks(L.px, members, L.U, allow_radial, fb);
+    if ((rc = install_fold_blocks(p, members, fb)) != PAT_OK) return rc;
     set_representation(L, true, true);
+    // unused rows (no representative) repeat the spectra of representative 0
+    bins.resize(fb.row_rep.size());
+    for (size_t r = 0; r < bins.size(); ++r)
+      bins[r] = members[4 * (size_t)std::max(fb.row_rep[r], 0)];
   } else {
     bins.resize((size_t)L.K);
     for (int64_t k = 0; k < L.K; ++k) bins[k] = (int)k;
@@ -619,3 +767,26 @@ int kspace_generate(Plan& p, const pat_medium& m, const std::vector<int>& bins, 
 }
 
 }  // namespace pat
+
+extern "C" int pat_fold_blocks(int P, int radial, int64_t* nrb, int64_t* nch, int32_t* rb_rep,
+                               int32_t* rb_chunk, int32_t* row_rep, int32_t* rep_row) {
+  using namespace pat;
+  try {
+    if (!nrb || !nch) return fail(PAT_ERR_ARG, "nrb or nch is NULL");
+    if (P < 2 || P > 65536 || (P & 1)) return fail(PAT_ERR_ARG, "P must be even, in [2, 65536]");
+    std::vector<int> members, rep, slot;
+    fold_enumerate(P, members, rep, slot);
+    const int64_t U = (int64_t)members.size() / 4;
+    FoldBlocks fb;
+    fold_blocks(P, members, U, radial != 0, fb);
+    *nrb = fb.nrb;
+    *nch = fb.nch;
+    if (rb_rep) std::copy(fb.rb_rep.begin(), fb.rb_rep.end(), rb_rep);
+    if (rb_chunk) std::copy(fb.rb_chunk.begin(), fb.rb_chunk.end(), rb_chunk);
+    if (row_rep) std::copy(fb.row_rep.begin(), fb.row_rep.end(), row_rep);
+    if (rep_row) std::copy(fb.rep_row.begin(), fb.rep_row.end(), rep_row);
+    return PAT_OK;
+  } catch (...) {
+    return fail(PAT_ERR_OOM, "host allocation failed");
+  }
+}

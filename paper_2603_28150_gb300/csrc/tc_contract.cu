@@ -841,7 +841,8 @@ size_t smem_for(int kchunks) {
 }
 
 // Forward-direction tile of bin k, row tile mt (t rows), part, from the real
-// blocked FP32 table; adjoint tile of bin k, K chunk kc (t columns), part.
+// blocked FP32 table (row rep[k] of the stored table, or row k when rep is
+// NULL); adjoint tile of bin k, K chunk kc (t columns), part.
 __global__ void k_split_tables(const float* __restrict__ table, const int* __restrict__ rep,
                                int nz, int nt, int nzg, int64_t K,
                                unsigned char* __restrict__ fwd, unsigned char* __restrict__ adj) {
@@ -888,12 +889,14 @@ size_t tc_table_bytes(const Layout& L) {
 
 cudaError_t tc_build_tables(const Plan& p, void* fwd, void* adj, cudaStream_t s) {
   const Layout& L = p.L;
-  // folded: tile set u is table row u (the representative's row)
+  // folded: tile set u is the stored row of representative u (row u, or
+  // rep_row[u] with radial sharing)
   const int64_t rows = L.fold ? L.U : L.K;
   int64_t n = rows * L.nt * L.nz;
   int64_t g = (n + 255) / 256;
   if (g > 152 * 64) g = 152 * 64;
-  tc::k_split_tables<<<(int)g, 256, 0, s>>>(static_cast<const float*>(p.table), nullptr, L.nz,
+  tc::k_split_tables<<<(int)g, 256, 0, s>>>(static_cast<const float*>(p.table),
+                                            L.fold ? p.rep_row : nullptr, L.nz,
                                             L.nt, L.nzg, rows, static_cast<unsigned char*>(fwd),
                                             static_cast<unsigned char*>(adj));
   return cudaGetLastError();

@@ -30,6 +30,7 @@ FLAG_FP64 = 1
 FLAG_FORCE_COMPLEX = 2
 FLAG_BF16_SPLIT = 4
 FLAG_NO_FOLD = 8
+FLAG_NO_RADIAL = 16
 
 TABLE_SPATIAL_F64 = 0
 TABLE_SPATIAL_F32 = 1
@@ -48,7 +49,7 @@ EXPORTS = (
     "pat_plan_set_wait_limit", "pat_debug_live_allocations", "pat_power_norm_seed",
     "pat_shard_layout", "pat_plan_create_kspace_shard", "pat_plan_shard_info",
     "pat_shard_spectrum", "pat_shard_contract", "pat_shard_image", "pat_fista_step",
-    "pat_axpby", "pat_stage_contract_slots",
+    "pat_axpby", "pat_stage_contract_slots", "pat_fold_blocks",
 )
 
 WAIT_LIMIT_DEFAULT = 4194304
@@ -79,7 +80,8 @@ class PlanInfo(ctypes.Structure):
                 ("workspace_bytes", ctypes.c_int64), ("table_max_abs", ctypes.c_double),
                 ("table_max_imag", ctypes.c_double), ("tensor_table_bytes", ctypes.c_int64),
                 ("tensor_min_batch", ctypes.c_int32), ("folded", ctypes.c_int32),
-                ("table_rows", ctypes.c_int64), ("workspace_external", ctypes.c_int32)]
+                ("table_rows", ctypes.c_int64), ("workspace_external", ctypes.c_int32),
+                ("radial", ctypes.c_int32), ("stored_rows", ctypes.c_int64)]
 
 
 class ShardInfo(ctypes.Structure):
@@ -158,6 +160,8 @@ def lib(build_if_missing: bool = True):
         "pat_debug_live_allocations": ([], ctypes.c_int64),
         "pat_power_norm_seed": ([P, I, ctypes.c_uint64, D, P], I),
         "pat_shard_layout": ([ctypes.POINTER(Geometry), I, I, I, ctypes.POINTER(ShardInfo), V, V, V], I),
+        "pat_fold_blocks": ([I, I, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                             V, V, V, V], I),
         "pat_plan_create_kspace_shard": ([ctypes.POINTER(Geometry), ctypes.POINTER(MediumC), I, I, P,
                                           ctypes.POINTER(P)], I),
         "pat_plan_shard_info": ([P, ctypes.POINTER(ShardInfo)], I),
@@ -235,7 +239,7 @@ class Plan:
                  py: int | None = None, max_batch: int = 1, fp64: bool = False,
                  force_complex: bool = False, table=None, medium: Medium | None = None,
                  bf16_split: bool = False, fold: bool = True, stream=None, workspace=None,
-                 shard: tuple | None = None):
+                 shard: tuple | None = None, radial: bool = True):
         L = lib()
         self.nx, self.ny, self.nz, self.nt = nx, ny, nz, nt
         self.mx, self.my = nx, ny          # scan grid of the data (see set_sampling)
@@ -245,7 +249,8 @@ class Plan:
         self.max_batch = max_batch
         self.fp64 = fp64
         flags = ((FLAG_FP64 if fp64 else 0) | (FLAG_FORCE_COMPLEX if force_complex else 0)
-                 | (FLAG_BF16_SPLIT if bf16_split else 0) | (0 if fold else FLAG_NO_FOLD))
+                 | (FLAG_BF16_SPLIT if bf16_split else 0) | (0 if fold else FLAG_NO_FOLD)
+                 | (0 if radial else FLAG_NO_RADIAL))
         self._geom = Geometry(nx, ny, nz, nt, self.px, self.py, max_batch, flags)
         self._h = ctypes.c_void_p(0)
         s = _stream(stream)
@@ -609,6 +614,23 @@ def shard_layout(nx: int, ny: int, nz: int, nt: int, px: int, py: int, fold: boo
     _check(lib().pat_shard_layout(ctypes.byref(g), 1 if fold else 0, rank, world, ctypes.byref(inf),
                                   zmap.ctypes.data, tmap.ctypes.data, mem.ctypes.data))
     return inf.as_dict(), zmap, tmap, (mem if fold else None)
+
+
+def fold_blocks(P: int, radial: bool = True) -> dict:
+    """pat_fold_blocks (host only): the block layout of the CUDA-core
+    contraction of a folded P x P plan. Returns nrb, nch and int32 arrays
+    rb_rep [nrb][32], rb_chunk [nrb], row_rep [nch][32], rep_row [U]."""
+    nrb, nch = ctypes.c_int64(0), ctypes.c_int64(0)
+    _check(lib().pat_fold_blocks(P, 1 if radial else 0, ctypes.byref(nrb), ctypes.byref(nch),
+                                 None, None, None, None))
+    U = (P // 2 + 1) * (P // 2 + 2) // 2
+    out = {"rb_rep": np.empty((nrb.value, 32), np.int32), "rb_chunk": np.empty(nrb.value, np.int32),
+           "row_rep": np.empty((nch.value, 32), np.int32), "rep_row": np.empty(U, np.int32)}
+    _check(lib().pat_fold_blocks(P, 1 if radial else 0, ctypes.byref(nrb), ctypes.byref(nch),
+                                 out["rb_rep"].ctypes.data, out["rb_chunk"].ctypes.data,
+                                 out["row_rep"].ctypes.data, out["rep_row"].ctypes.data))
+    out["nrb"], out["nch"] = nrb.value, nch.value
+    return out
 
 
 def workspace_size(nx: int, ny: int, nz: int, nt: int, px: int | None = None,

@@ -100,7 +100,7 @@ def test_failed_allocation_cleans_up(monkeypatch, kind):
             kw["table"] = torch.tensor(h, device="cuda") if kind == "table_folded" else h
             kw["force_complex"] = kind == "table_complex"
     base = pat.debug_live_allocations()
-    for n in range(1, 40):
+    for n in range(1, 80):
         monkeypatch.setenv("PAT_DEBUG_FAIL_ALLOC", str(n))
         try:
             plan = Plan(g.nx, g.ny, g.nz, g.nt, g.px, g.py, **kw)

@@ -88,6 +88,7 @@ def test_folded_equals_unfolded(g, B):
     pu = Plan(g.nx, g.ny, g.nz, g.nt, g.px, g.py, table=h, max_batch=B, fold=False)
     fi, ui = pf.info(), pu.info()
     assert fi["folded"] == 1 and ui["folded"] == 0
+    assert fi["radial"] == 0     # random D4 kernels: representatives of one radius differ
     P = g.px
     assert fi["table_rows"] == (P // 2 + 1) * (P // 2 + 2) // 2 and ui["table_rows"] == ui["bins"]
     # rows are stored in blocks of 32

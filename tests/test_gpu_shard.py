@@ -84,9 +84,11 @@ def test_sharded_operator_equals_plan(world, fold):
     info = shards[0].shard_info()
     assert info["folded"] == (1 if fold else 0) and info["world"] == world
     assert sum(p.shard_info()["rows"] for p in shards) == info["rows_total"]
-    # each shard stores its share of the rows
-    assert shards[-1].info()["table_bytes"] <= full.info()["table_bytes"] // world + (
-        32 * g.nt * 4 * g.nz * (1 if fold else 1))
+    # each shard stores its share of the rows: rows_per_rank (a multiple of 32,
+    # at most 31 above an even split), one row per representative or bin
+    rpr = info["rows_per_rank"]
+    assert rpr % 32 == 0 and rpr * world >= info["rows_total"] and rpr < info["rows_total"] / world + 32
+    assert all(p.info()["table_bytes"] == rpr * g.nt * g.nz * 4 for p in shards)
     with pytest.raises(PatError):
         shards[0].forward(torch.zeros((g.nz, g.ny, g.nx), device="cuda"))
     ex = LocalExchange(world)
@@ -121,7 +123,7 @@ def test_sharded_operator_equals_plan(world, fold):
 
 def test_sharded_benchmark_geometry():
     """128^2 -> 256^2, 64 depths, 256 samples on 2 shards: H and H* equal the
-    unsharded plan, each shard storing half of the folded table."""
+    unsharded plan, each shard storing half of the representatives' rows."""
     import torch
     g = oracle.Grid.square(128, 64, 256)
     med = _medium(g)
@@ -129,8 +131,10 @@ def test_sharded_benchmark_geometry():
     world = 2
     shards = [Plan(g.nx, g.ny, g.nz, g.nt, g.px, g.py, medium=med, shard=(r, world))
               for r in range(world)]
-    tb = [p.info()["table_bytes"] for p in shards]
-    assert max(tb) <= full.info()["table_bytes"] // 2 + 32 * 256 * 64 * 4
+    info = shards[0].shard_info()
+    rpr = info["rows_per_rank"]
+    assert info["rows_total"] == 129 * 130 // 2 and rpr == (info["rows_total"] + 63) // 64 * 32
+    assert all(p.info()["table_bytes"] == rpr * 256 * 64 * 4 for p in shards)
     # a shard's workspace: no spectra, object or data buffers, and an FFT
     # intermediate of its own 128 time samples (the full plan's holds 256)
     ws = [p.info()["workspace_bytes"] for p in shards]
