@@ -3,7 +3,7 @@ device footprint): builds a plan with a device-generated real library and
 applies `--pairs` gradients H*(H x - y) (one forward and one adjoint each).
 
   python profile_run.py [--n 128] [--nz 64] [--nt 256]
-         [--pairs 3] [--batch 1] [--no-fold] [--complex] [--tensor]
+         [--pairs 3] [--batch 1] [--no-fold] [--no-radial] [--complex] [--tensor]
 
 The data y = H x come first (4 FFT launches, 1 contraction). Each pair then
 launches, in order: stage i over depths (row, column FFT), the depth
@@ -32,6 +32,8 @@ def main(argv=None):
     ap.add_argument("--pairs", type=int, default=3)
     ap.add_argument("--batch", type=int, default=1)
     ap.add_argument("--no-fold", action="store_true")
+    ap.add_argument("--no-radial", action="store_true",
+                    help="one stored row per D4 representative (no radial sharing)")
     ap.add_argument("--complex", action="store_true", help="store the complex table")
     ap.add_argument("--tensor", action="store_true", help="split-BF16 tensor-core tables")
     a = ap.parse_args(argv)
@@ -42,6 +44,7 @@ def main(argv=None):
     while mz < 1 + a.nz + a.nt * 1500.0 * 10e-9 / 50e-6 + 1:
         mz *= 2
     plan = Plan(a.n, a.n, a.nz, a.nt, p, p, max_batch=a.batch, fold=not a.no_fold,
+                radial=not a.no_radial,
                 force_complex=a.complex, bf16_split=a.tensor,
                 medium=Medium(1500.0, 50e-6, 50e-6, 50e-6, 10e-9, mz, 1))
     dev = torch.device("cuda")
@@ -54,7 +57,8 @@ def main(argv=None):
     torch.cuda.synchronize()
     plan.check()
     info = plan.info()
-    print(f"pairs={a.pairs} batch={a.batch} folded={info['folded']} real={info['real_table']} "
+    print(f"pairs={a.pairs} batch={a.batch} folded={info['folded']} radial={info['radial']} "
+          f"real={info['real_table']} "
           f"table_gb={info['table_bytes'] / 1e9:.3f}")
 
 
