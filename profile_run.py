@@ -3,13 +3,15 @@ device footprint): builds a plan with a device-generated real library and
 applies `--pairs` gradients H*(H x - y) (one forward and one adjoint each).
 
   python profile_run.py [--n 128] [--nz 64] [--nt 256]
-         [--pairs 3] [--batch 1] [--no-fold] [--no-radial] [--complex] [--tensor]
+         [--pairs 3] [--fista 0] [--batch 1] [--no-fold] [--no-radial] [--complex] [--tensor]
 
 The data y = H x come first (4 FFT launches, 1 contraction). Each pair then
 launches, in order: stage i over depths (row, column FFT), the depth
 contraction, stage iii over time samples (column, row inverse FFT), stage i
 over time samples, the time contraction, stage iii over depths; so a profiler
 skipping 12 FFT launches (or 3 contractions) starts at the second pair.
+With --fista N a power iteration (5 pairs) and an N-iteration FISTA solve
+follow (one CUDA graph of 8 kernels per iteration).
 """
 from __future__ import annotations
 
@@ -30,6 +32,7 @@ def main(argv=None):
     ap.add_argument("--nz", type=int, default=64)
     ap.add_argument("--nt", type=int, default=256)
     ap.add_argument("--pairs", type=int, default=3)
+    ap.add_argument("--fista", type=int, default=0, help="FISTA iterations after the pairs")
     ap.add_argument("--batch", type=int, default=1)
     ap.add_argument("--no-fold", action="store_true")
     ap.add_argument("--no-radial", action="store_true",
@@ -54,6 +57,9 @@ def main(argv=None):
     g = torch.empty_like(x)
     for _ in range(a.pairs):
         plan.gradient(x, y, out=g, resid=False)
+    if a.fista:
+        L = 1.01 * plan.power_norm(torch.ones_like(x[0]), 5)
+        plan.fista(y[0], iters=a.fista, L=L)
     torch.cuda.synchronize()
     plan.check()
     info = plan.info()
