@@ -764,6 +764,59 @@ __global__ void __launch_bounds__(kThreads) k_row_c2r(const cx<R>* __restrict__ 
   if (partials) block_sum_to(st.acc, partials + (int64_t)blockIdx.y * gridDim.x + blockIdx.x);
 }
 
+// The residual pass stages the measured rows of its block in shared memory
+// (single precision, unsampled data: 2 VPB rows of at most P/2 floats after
+// the work vectors), where that keeps 4 CTAs per SM (<= 56 KB). The data of a
+// solve are written before its first kernel runs, so the copies are issued
+// before the dependency wait and overlap the previous kernel's end and this
+// kernel's spectrum loads.
+template <typename R, int P, bool SAMP>
+struct ResidStage {
+  static constexpr size_t rows_bytes = sizeof(R) * 2 * Shape<P>::VPB * (P / 2);
+  static constexpr bool on =
+      !SAMP && sizeof(R) == 4 && smem_bytes<R, P>() + rows_bytes <= 56 * 1024;
+  static constexpr size_t bytes = on ? rows_bytes : 0;
+};
+
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(
+                   (uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                   (uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n cp.async.wait_group 0;" ::: "memory");
+}
+
+// The step pass stages the FISTA state (y_k and x_{k-1}) of its rows the
+// same way, where that keeps 3 CTAs per SM (<= 76 KB): written by the
+// previous iteration's step pass (or before the first kernel of the solve),
+// it is visible before the dependency wait.
+template <typename R, int P>
+struct StepStage {
+  static constexpr size_t rows_bytes = sizeof(R) * 2 * Shape<P>::VPB * (P / 2);
+  static constexpr bool on = sizeof(R) == 4 && smem_bytes<R, P>() + 2 * rows_bytes <= 76 * 1024;
+  static constexpr size_t bytes = on ? 2 * rows_bytes : 0;
+};
+
+// Copies n floats from global src to shared dst (16-byte copies when both the
+// source and the count allow, else 4-byte copies); the block's threads share
+// the work. Waited for by cp_async_wait_all.
+template <typename R>
+__device__ __forceinline__ void stage_rows(R* dst, const R* src, int n) {
+  if (((reinterpret_cast<uintptr_t>(src) & 15) == 0) && (n & 3) == 0) {
+    for (int i = 4 * threadIdx.x; i < n; i += 4 * kThreads) cp_async16(dst + i, src + i);
+  } else {
+    for (int i = threadIdx.x; i < n; i += kThreads) cp_async4(dst + i, src + i);
+  }
+}
+
 // Residual row pass between H and H* (the gradient of Eq. 15): for the
 // block's row pairs of slice s, the inverse row transform as k_row_c2r does
 // it, then r = image - y at the kept (scan) positions and zero elsewhere, its
@@ -785,14 +838,21 @@ __global__ void __launch_bounds__(kThreads) k_row_resid(cx<R>* __restrict__ T, i
                                                         unsigned* __restrict__ count,
                                                         const cx<R>* __restrict__ tw_g, Samp sm) {
   using SH = Shape<P>;
+  using YS = ResidStage<R, P, SAMP>;
   cx<R>* tw;
   cx<R>* bufs = setup_smem<R, P>(tw_g, &tw);
   const int v = threadIdx.x / SH::TPV, tid = threadIdx.x % SH::TPV;
   const int64_t s = blockIdx.y;
   const int pair0 = blockIdx.x * SH::VPB;
   cx<R>* Ts = T + s * tslice;
+  // rows [2 pair0, 2 pair0 + nrows) of the measured slice, contiguous
+  R* ys = reinterpret_cast<R*>(bufs + SH::VPB * SH::VSTR);
+  if constexpr (YS::on)
+    stage_rows(ys, y + s * y_stride + (int64_t)(2 * pair0) * nx,
+               min(2 * SH::VPB, ny - 2 * pair0) * nx);
   pdl_wait();
   load_packed_pairs<R, P>(Ts, tstride, pair0, ny, bufs);
+  if constexpr (YS::on) cp_async_wait_all();
   __syncthreads();
   cx<R>* b = bufs + v * SH::VSTR;
   SmemLoad<R> sl;
@@ -809,11 +869,11 @@ __global__ void __launch_bounds__(kThreads) k_row_resid(cx<R>* __restrict__ T, i
     if (SAMP && xi >= 0) xi = scan_index(x, sm.ox, sm.sx, sm.mx);
     if (xi >= 0) {
       if (rows.ok0) {
-        r0 = z.x - rows.sslice[rows.off0 + xi];
+        r0 = z.x - (YS::on ? ys[2 * v * nx + xi] : rows.sslice[rows.off0 + xi]);
         acc += (double)r0 * (double)r0;
       }
       if (rows.ok1) {
-        r1 = z.y - rows.sslice[rows.off1 + xi];
+        r1 = z.y - (YS::on ? ys[(2 * v + 1) * nx + xi] : rows.sslice[rows.off1 + xi]);
         acc += (double)r1 * (double)r1;
       }
     }
@@ -869,27 +929,41 @@ __global__ void __launch_bounds__(kThreads) k_row_c2r_step(
     double* __restrict__ r2_hist, int cap, unsigned* __restrict__ done,
     const cx<R>* __restrict__ tw_g) {
   using SH = Shape<P>;
+  using SS = StepStage<R, P>;
   cx<R>* tw;
   cx<R>* bufs = setup_smem<R, P>(tw_g, &tw);
   const int v = threadIdx.x / SH::TPV, tid = threadIdx.x % SH::TPV;
   const int64_t s = blockIdx.y;
   const int pair0 = blockIdx.x * SH::VPB;
+  // y_k and x_{k-1} of rows [2 pair0, 2 pair0 + 2 VPB), staged after the work vectors
+  R* sy = reinterpret_cast<R*>(bufs + SH::VPB * SH::VSTR);
+  R* sx = sy + 2 * SH::VPB * (P / 2);
+  if constexpr (SS::on) {
+    const int n = min(2 * SH::VPB, ny - 2 * pair0) * nx;
+    stage_rows(sy, yv + s * plane + (int64_t)(2 * pair0) * nx, n);
+    stage_rows(sx, xprev + s * plane + (int64_t)(2 * pair0) * nx, n);
+  }
   pdl_wait();
   const R invL = (R)scal[0], lamL = (R)scal[1];
   const int k = *iter;
   const R beta = (R)betas[k];
   load_packed_pairs<R, P>(T + s * tslice, tstride, pair0, ny, bufs);
+  if constexpr (SS::on) cp_async_wait_all();
   __syncthreads();
   const int y0 = 2 * (pair0 + v);
   const bool ok0 = y0 < ny, ok1 = y0 + 1 < ny;
   R* ys = yv + s * plane + (int64_t)y0 * nx;
   R* xs = xprev + s * plane + (int64_t)y0 * nx;
+  R* syv = sy + 2 * v * nx;  // this pair's staged rows (i in [0, 2 nx))
+  R* sxv = sx + 2 * v * nx;
   auto upd = [&](int64_t i, R g) {
-    const R ya = ys[i], xp = xs[i];
+    const R ya = SS::on ? syv[i] : ys[i], xp = SS::on ? sxv[i] : xs[i];
     R x = ya - g * invL - lamL;
     x = x > (R)0 ? x : (R)0;
-    ys[i] = x + beta * (x - xp);
+    const R yn = x + beta * (x - xp);
+    ys[i] = yn;
     xs[i] = x;
+    if (SS::on) syv[i] = yn;
   };
   auto st = [&](int x, cx<R> z) {
     if (x >= nx) return;
@@ -902,8 +976,9 @@ __global__ void __launch_bounds__(kThreads) k_row_c2r_step(
     // y_{k+1} of this block's rows, just written: packed as row y0 + i row y0 + 1
     __syncthreads();
     cx<R>* b = bufs + v * SH::VSTR;
+    const R* yn = SS::on ? syv : ys;
     for (int x = tid; x < P; x += SH::TPV)
-      b[pidx(x)] = x < nx ? mk<R>(ok0 ? ys[x] : (R)0, ok1 ? ys[nx + x] : (R)0) : mk<R>(0, 0);
+      b[pidx(x)] = x < nx ? mk<R>(ok0 ? yn[x] : (R)0, ok1 ? yn[nx + x] : (R)0) : mk<R>(0, 0);
     __syncthreads();
     NoStore<R> ns;
     run_passes<R, P, 0, false, false, false, true>(b, tw, tid, ld, ns);  // zero half skipped
@@ -1010,13 +1085,16 @@ cudaError_t FftLen<R, P>::row_resid(cx<R>* T, int tstride, int64_t tslice, int n
                                     Samp sm) {
   using SH = Shape<P>;
   auto fn = sm.on ? k_row_resid<R, P, true> : k_row_resid<R, P, false>;
-  cudaError_t e = set_smem_attr<R, P>((const void*)fn);
+  const size_t smem =
+      smem_bytes<R, P>() + (sm.on ? ResidStage<R, P, true>::bytes : ResidStage<R, P, false>::bytes);
+  cudaError_t e = cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
   if (e != cudaSuccess) return e;
   const int pairs = (ny + 1) / 2;
   dim3 grid((pairs + SH::VPB - 1) / SH::VPB, S);
   *nblocks = (int)(grid.x * grid.y);
-  return launch_pdl(fn, grid, dim3(kThreads), smem_bytes<R, P>(), st, T, tstride, tslice, nx, ny, y,
-                    y_stride, partials, partials ? total : nullptr, count, tw, sm);
+  return launch_pdl(fn, grid, dim3(kThreads), smem, st, T, tstride, tslice, nx, ny, y, y_stride,
+                    partials, partials ? total : nullptr, count, tw, sm);
 }
 
 template <typename R, int P>
@@ -1025,11 +1103,13 @@ cudaError_t FftLen<R, P>::row_c2r_step(const cx<R>* T, int tstride, int64_t tsli
                                        cudaStream_t st) {
   using SH = Shape<P>;
   auto fn = f.next_T ? k_row_c2r_step<R, P, true> : k_row_c2r_step<R, P, false>;
-  cudaError_t e = set_smem_attr<R, P>((const void*)fn);
+  const size_t smem = smem_bytes<R, P>() + StepStage<R, P>::bytes;
+  cudaError_t e = cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
   if (e != cudaSuccess) return e;
   const int pairs = (ny + 1) / 2;
   dim3 grid((pairs + SH::VPB - 1) / SH::VPB, S);
-  return launch_pdl(fn, grid, dim3(kThreads), smem_bytes<R, P>(), st, const_cast<cx<R>*>(T), tstride,
+  return launch_pdl(fn, grid, dim3(kThreads), smem, st, const_cast<cx<R>*>(T), tstride,
                     tslice, nx, ny, plane, static_cast<R*>(f.y), static_cast<R*>(f.xprev), f.scal,
                     f.betas, f.iter, f.r2_cur, f.r2_hist, f.cap, f.done, tw);
 }
