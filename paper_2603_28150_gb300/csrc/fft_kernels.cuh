@@ -857,13 +857,15 @@ __global__ void __launch_bounds__(kThreads) k_row_resid(cx<R>* __restrict__ T, i
   cx<R>* b = bufs + v * SH::VSTR;
   SmemLoad<R> sl;
   NoStore<R> ns;
-  run_passes<R, P, 0, true, false, false, false, true>(b, tw, tid, sl, ns);  // image rows x < P/2
   // the layout of y: the row pair's offsets (scan rows with sampling on)
   const int y0 = 2 * (pair0 + v);
   RowPairStore<R, SAMP> rows(nullptr, y + s * y_stride, y0, nx, ny, sm);
   double acc = 0.0;
-  for (int x = tid; x < P; x += SH::TPV) {
-    const cx<R> z = b[pidx(x)];
+  // image rows x < P/2 from the last inverse pass, turned into the residual
+  // in place: that pass writes exactly the positions its thread read, so r
+  // replaces the image without a barrier (zero past nx; the forward pass
+  // below does not read x >= P/2)
+  auto resid = [&](int x, cx<R> z) {
     R r0 = 0, r1 = 0;
     int xi = x < nx ? x : -1;
     if (SAMP && xi >= 0) xi = scan_index(x, sm.ox, sm.sx, sm.mx);
@@ -878,7 +880,8 @@ __global__ void __launch_bounds__(kThreads) k_row_resid(cx<R>* __restrict__ T, i
       }
     }
     b[pidx(x)] = mk<R>(r0, r1);
-  }
+  };
+  run_passes<R, P, 0, true, false, true, false, true>(b, tw, tid, sl, resid);
   __syncthreads();
   run_passes<R, P, 0, false, false, false, true>(b, tw, tid, sl, ns);  // spectrum of r0 + i r1
 #pragma unroll 4
@@ -954,31 +957,32 @@ __global__ void __launch_bounds__(kThreads) k_row_c2r_step(
   const bool ok0 = y0 < ny, ok1 = y0 + 1 < ny;
   R* ys = yv + s * plane + (int64_t)y0 * nx;
   R* xs = xprev + s * plane + (int64_t)y0 * nx;
-  R* syv = sy + 2 * v * nx;  // this pair's staged rows (i in [0, 2 nx))
-  R* sxv = sx + 2 * v * nx;
-  auto upd = [&](int64_t i, R g) {
+  const R* syv = sy + 2 * v * nx;  // this pair's staged rows (i in [0, 2 nx))
+  const R* sxv = sx + 2 * v * nx;
+  auto upd = [&](int64_t i, R g) -> R {
     const R ya = SS::on ? syv[i] : ys[i], xp = SS::on ? sxv[i] : xs[i];
     R x = ya - g * invL - lamL;
     x = x > (R)0 ? x : (R)0;
     const R yn = x + beta * (x - xp);
     ys[i] = yn;
     xs[i] = x;
-    if (SS::on) syv[i] = yn;
+    return yn;
   };
+  cx<R>* b = bufs + v * SH::VSTR;
+  // the last inverse pass writes exactly the positions its thread read, so
+  // with NEXT the new momentum point y_{k+1} (rows y0 + i y0 + 1, zero past
+  // nx) replaces the gradient in place as the next forward transform's input
   auto st = [&](int x, cx<R> z) {
-    if (x >= nx) return;
-    if (ok0) upd(x, z.x);
-    if (ok1) upd((int64_t)nx + x, z.y);
+    R n0 = 0, n1 = 0;
+    if (x < nx) {
+      if (ok0) n0 = upd(x, z.x);
+      if (ok1) n1 = upd((int64_t)nx + x, z.y);
+    }
+    if constexpr (NEXT) b[pidx(x)] = mk<R>(n0, n1);
   };
   SmemLoad<R> ld;
-  run_passes<R, P, 0, true, false, true, false, true>(bufs + v * SH::VSTR, tw, tid, ld, st);
+  run_passes<R, P, 0, true, false, true, false, true>(b, tw, tid, ld, st);
   if constexpr (NEXT) {
-    // y_{k+1} of this block's rows, just written: packed as row y0 + i row y0 + 1
-    __syncthreads();
-    cx<R>* b = bufs + v * SH::VSTR;
-    const R* yn = SS::on ? syv : ys;
-    for (int x = tid; x < P; x += SH::TPV)
-      b[pidx(x)] = x < nx ? mk<R>(ok0 ? yn[x] : (R)0, ok1 ? yn[nx + x] : (R)0) : mk<R>(0, 0);
     __syncthreads();
     NoStore<R> ns;
     run_passes<R, P, 0, false, false, false, true>(b, tw, tid, ld, ns);  // zero half skipped
