@@ -232,9 +232,13 @@ int pat_plan_destroy(pat_plan* plan);
 int pat_plan_info(const pat_plan* plan, pat_plan_info_t* info);
 
 /* Device bytes a plan for `g` would take, before creating it (admission
- * control): *table_bytes for the real (real_table = 1) or complex
- * representation of the library, *workspace for everything else (including
- * the host-pointer staging buffers). No device call is made. */
+ * control): *table_bytes for the representation of the library given by
+ * real_table: 0 complex, 1 real (one row per bin), 2 real D4-folded, 3 real
+ * folded with radial sharing (a k-space library with dx = dy gets 3); 2 and 3
+ * need a square padded grid in single precision, else they count as 1. With
+ * PAT_FLAG_BF16_SPLIT the split tensor tables (one tile set per row: per
+ * representative when folded) are included. *workspace for everything else
+ * (including the host-pointer staging buffers). No device call is made. */
 int pat_plan_estimate(const pat_geometry* g, int real_table, int64_t* table_bytes,
                       int64_t* workspace);
 

@@ -659,8 +659,22 @@ int pat_plan_estimate(const pat_geometry* g, int real_table, int64_t* table_byte
   int rc = validate(g);
   if (rc != PAT_OK) return rc;
   if (!table_bytes || !workspace) return fail(PAT_ERR_ARG, "output pointer is NULL");
+  if (real_table < 0 || real_table > 3) return fail(PAT_ERR_ARG, "real_table must be 0..3");
   Layout L = make_layout(g);
   set_representation(L, real_table != 0);
+  if (real_table >= 2 && fold_possible(L)) {  // D4-folded, radially shared with 3
+    std::vector<int> members, rep, slot;
+    fold_enumerate(L.px, members, rep, slot);
+    L.U = (int64_t)members.size() / 4;
+    L.Upad = (L.U + 31) / 32 * 32;
+    L.nub = L.Upad / 32;
+    FoldBlocks fb;
+    fold_blocks(L.px, members, L.U, real_table == 3, fb);
+    L.nrb = fb.nrb;
+    L.nch = fb.nch;
+    L.radial = fb.nch != fb.nrb;
+    set_representation(L, true, true);
+  }
   *table_bytes = (int64_t)L.table_bytes;
   if ((g->flags & PAT_FLAG_BF16_SPLIT) && tc_supported(L))
     *table_bytes += 2 * (int64_t)tc_table_bytes(L);

@@ -546,16 +546,17 @@ class Plan:
 
 def plan_estimate(nx: int, ny: int, nz: int, nt: int, px: int | None = None, py: int | None = None,
                   max_batch: int = 1, fp64: bool = False, real_table: bool = True,
-                  bf16_split: bool = False):
+                  bf16_split: bool = False, fold: bool = False, radial: bool = False):
     """(table bytes including the split-BF16 tables, workspace bytes) a plan
-    would take on the device."""
+    would take on the device; `fold` / `radial` estimate the D4-folded /
+    radially shared representation a k-space library with dx = dy gets."""
     px = px if px is not None else _pow2_at_least(2 * nx)
     py = py if py is not None else _pow2_at_least(2 * ny)
     g = Geometry(nx, ny, nz, nt, px, py, max_batch,
                  (FLAG_FP64 if fp64 else 0) | (FLAG_BF16_SPLIT if bf16_split else 0))
     tb, ws = ctypes.c_int64(0), ctypes.c_int64(0)
-    _check(lib().pat_plan_estimate(ctypes.byref(g), 1 if real_table else 0, ctypes.byref(tb),
-                                   ctypes.byref(ws)))
+    rep = 0 if not real_table else (3 if fold and radial else 2 if fold else 1)
+    _check(lib().pat_plan_estimate(ctypes.byref(g), rep, ctypes.byref(tb), ctypes.byref(ws)))
     return tb.value, ws.value
 
 

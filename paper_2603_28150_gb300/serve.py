@@ -135,8 +135,10 @@ class CudaEngine:
     @classmethod
     def estimate(cls, geom: Geometry, slots: int) -> int:
         from .pat import plan_estimate
+        # the served libraries are k-space libraries of an isotropic grid:
+        # D4-folded and radially shared
         tb, ws = plan_estimate(geom.n, geom.n, geom.nz, geom.nt, geom.pad, geom.pad, slots,
-                               bf16_split=cls.tensor_ok(geom, slots))
+                               bf16_split=cls.tensor_ok(geom, slots), fold=True, radial=True)
         return tb + ws
 
     def bytes(self) -> int:

@@ -83,3 +83,29 @@ def test_rejects_bad_lengths():
     for P in (0, 1, 7, -4):
         with pytest.raises(pat.PatError):
             pat.fold_blocks(P, True)
+
+
+def test_plan_estimate_representations():
+    """pat_plan_estimate's table bytes for the complex, per-bin real, D4-folded
+    and radially shared representations (4 depths per 16-byte group, chunks of
+    32 rows), and the per-representative tensor tiles of a folded plan."""
+    n, nz, nt, P = 128, 64, 256, 256
+    K = (P // 2 + 1) * P
+    row = nt * nz * 4
+    chunks = lambda rows: (rows + 31) // 32 * 32  # noqa: E731
+    U = len(_reps(P))
+    tbc, _ = pat.plan_estimate(n, n, nz, nt, P, P, real_table=False)
+    tbr, _ = pat.plan_estimate(n, n, nz, nt, P, P)
+    tbf, _ = pat.plan_estimate(n, n, nz, nt, P, P, fold=True)
+    tbx, ws = pat.plan_estimate(n, n, nz, nt, P, P, fold=True, radial=True)
+    assert tbr == chunks(K) * row and tbc == 2 * tbr
+    assert tbf == chunks(U) * row
+    assert tbx == 32 * pat.fold_blocks(P, True)["nch"] * row == 396361728
+    assert ws == pat.workspace_size(n, n, nz, nt, P, P)
+    # tensor tiles: hi + lo BF16 per (representative, t, z), both directions
+    t128, _ = pat.plan_estimate(n, n, 128, 512, P, P, max_batch=16, bf16_split=True, fold=True,
+                                radial=True)
+    assert t128 == 32 * pat.fold_blocks(P, True)["nch"] * 512 * 128 * 4 + 2 * U * 512 * 128 * 4
+    # a rectangular grid cannot fold: the per-bin count
+    assert pat.plan_estimate(n, 64, nz, nt, P, 128, fold=True)[0] == \
+        pat.plan_estimate(n, 64, nz, nt, P, 128)[0]

@@ -101,3 +101,24 @@ def test_user_tables_share_rows_only_when_the_radii_agree():
         got, alt = host(got), host(alt)
         assert np.abs(got - alt).max() <= 1e-6 * np.abs(alt).max()
         assert oracle.rel_l2(got, ref) < 1e-5
+
+
+def test_estimate_matches_plans():
+    """pat_plan_estimate with the folded, radially shared representation gives
+    the table bytes a k-space plan allocates (tensor tiles included), and at
+    least its workspace (the estimate counts the host staging too)."""
+    g = oracle.Grid.square(64, 32, 128)
+    med, _ = _medium(g)
+    plan = Plan(g.nx, g.ny, g.nz, g.nt, g.px, g.py, medium=med)
+    tb, ws = pat.plan_estimate(g.nx, g.ny, g.nz, g.nt, g.px, g.py, fold=True, radial=True)
+    inf = plan.info()
+    assert inf["radial"] == 1 and inf["table_bytes"] == tb and inf["workspace_bytes"] <= ws
+    g2 = oracle.Grid.square(32, 128, 256)
+    med2, _ = _medium(g2)
+    p2 = Plan(g2.nx, g2.ny, g2.nz, g2.nt, g2.px, g2.py, max_batch=4, medium=med2,
+              bf16_split=True)
+    tb2, ws2 = pat.plan_estimate(g2.nx, g2.ny, g2.nz, g2.nt, g2.px, g2.py, max_batch=4,
+                                 bf16_split=True, fold=True, radial=True)
+    inf2 = p2.info()
+    assert inf2["table_bytes"] + inf2["tensor_table_bytes"] == tb2
+    assert inf2["workspace_bytes"] <= ws2
