@@ -700,7 +700,8 @@ int pat_plan_info(const pat_plan* plan, pat_plan_info_t* info) {
   info->folded = p.L.fold ? 1 : 0;
   info->table_rows = p.L.fold ? p.L.U : p.L.K;
   info->radial = p.L.fold && p.L.radial ? 1 : 0;
-  info->stored_rows = 32 * (p.L.fold ? p.L.nch : p.L.nkb);
+  // every stored row takes nt z-groups of 16 bytes, whatever the representation
+  info->stored_rows = (int64_t)(p.L.table_bytes / ((size_t)p.L.nt * p.L.nzg * 16));
   return PAT_OK;
 }
 

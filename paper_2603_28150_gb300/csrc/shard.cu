@@ -191,18 +191,42 @@ int pat_plan_create_kspace_shard(const pat_geometry* g, const pat_medium* m, int
     if (rc == PAT_OK) {
       if (fold) mloc.resize((size_t)pt.Wr * 4);
       fill_maps(pt, L.K, members, rep, zmap.data(), tmap.data(), fold ? mloc.data() : nullptr);
-      // the table of this shard: its rows only, in the plan's blocked layout
+      // the table of this shard: its rows only, in the plan's blocked layout;
+      // folded, the representatives of one radius among this shard's rows
+      // share a stored row as in an unsharded plan (the contraction's blocks
+      // then address the exchange slots through their block map)
       set_representation(L, L.real, fold);
-      if (fold) {  // one block per chunk of 32 rows (no radial sharing)
-        L.U = pt.rows;
+      std::vector<int> bins;
+      FoldBlocks fb;
+      if (fold && pt.rows == 0) {  // no rows: an unread table of one block per chunk
+        L.U = 0;
         L.Upad = pt.Wr;
         L.nub = L.nrb = L.nch = pt.Wr / 32;
+      } else if (fold) {
+        L.U = pt.rows;
+        L.Upad = pt.Wr;
+        L.nub = pt.Wr / 32;
+        std::vector<int> local((size_t)pt.rows * 4);
+        for (int64_t j = 0; j < 4 * pt.rows; ++j) local[j] = members[4 * pt.row0 + j];
+        fold_blocks(g->px, local, pt.rows, (g->flags & PAT_FLAG_NO_RADIAL) == 0, fb);
+        L.nrb = fb.nrb;
+        L.nch = fb.nch;
+        L.radial = fb.nch != fb.nrb;
+        bins.resize(fb.row_rep.size());
+        for (size_t r = 0; r < bins.size(); ++r) bins[r] = local[4 * (size_t)std::max(fb.row_rep[r], 0)];
+        if (L.radial) {  // block slot -> exchange slots of its representative
+          std::vector<int32_t> rbm(fb.rb_rep.size() * 4, -1);
+          for (size_t v = 0; v < fb.rb_rep.size(); ++v)
+            if (fb.rb_rep[v] >= 0)
+              for (int i = 0; i < 4; ++i) rbm[4 * v + i] = mloc[4 * (size_t)fb.rb_rep[v] + i];
+          mloc.swap(rbm);
+        }
+      } else {
+        bins.resize((size_t)pt.rows);
+        for (int64_t j = 0; j < pt.rows; ++j) bins[j] = (int)(pt.row0 + j);
       }
-      const int64_t blocks = pt.Wr / 32;
+      const int64_t blocks = fold ? L.nch : pt.Wr / 32;
       L.table_bytes = (size_t)blocks * L.nt * L.nzg * 32 * 16;
-      std::vector<int> bins((size_t)pt.rows);
-      for (int64_t j = 0; j < pt.rows; ++j)
-        bins[j] = fold ? members[4 * (pt.row0 + j)] : (int)(pt.row0 + j);
       p.shard_world = world;
       p.shard_rank = rank;
       p.shard_row0 = pt.row0;
@@ -218,6 +242,10 @@ int pat_plan_create_kspace_shard(const pat_geometry* g, const pat_medium* m, int
         e = cudaMemcpy(p.shard_tmap, tmap.data(), tmap.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
       if (e == cudaSuccess && fold)
         e = cudaMemcpy(p.shard_members, mloc.data(), mloc.size() * sizeof(int32_t),
+                       cudaMemcpyHostToDevice);
+      if (e == cudaSuccess && fold && L.radial) e = dev_alloc(&p.rb_chunk, fb.rb_chunk.size() * sizeof(int));
+      if (e == cudaSuccess && fold && L.radial)
+        e = cudaMemcpy(p.rb_chunk, fb.rb_chunk.data(), fb.rb_chunk.size() * sizeof(int),
                        cudaMemcpyHostToDevice);
       if (e != cudaSuccess) rc = cuda_fail(e, "uploading the shard maps");
       if (rc == PAT_OK) rc = kspace_generate(p, *m, bins, s);
@@ -289,8 +317,10 @@ int pat_shard_contract(pat_plan* plan, int adjoint, const void* in, void* out, p
     v.tc_min_batch = 0;
     v.L.Kpad = p.shard_W;
     if (p.L.fold) {
-      v.rb_members = p.shard_members;  // block j reads chunk j (rb_chunk NULL)
-      v.rb_chunk = nullptr;
+      // block slots address this shard's exchange slots; with radial sharing
+      // the blocks of a radius group read one chunk (else block j reads chunk j)
+      v.rb_members = p.shard_members;
+      v.rb_chunk = p.L.radial ? p.rb_chunk : nullptr;
     } else {
       v.L.K = p.shard_rows;
       v.L.nkb = p.shard_Wr / 32;

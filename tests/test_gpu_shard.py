@@ -84,11 +84,16 @@ def test_sharded_operator_equals_plan(world, fold):
     info = shards[0].shard_info()
     assert info["folded"] == (1 if fold else 0) and info["world"] == world
     assert sum(p.shard_info()["rows"] for p in shards) == info["rows_total"]
-    # each shard stores its share of the rows: rows_per_rank (a multiple of 32,
-    # at most 31 above an even split), one row per representative or bin
+    # each shard holds its share of the rows: rows_per_rank (a multiple of 32,
+    # at most 31 above an even split), stored one per representative or bin,
+    # or (folded) one per radius among its representatives
     rpr = info["rows_per_rank"]
     assert rpr % 32 == 0 and rpr * world >= info["rows_total"] and rpr < info["rows_total"] / world + 32
-    assert all(p.info()["table_bytes"] == rpr * g.nt * g.nz * 4 for p in shards)
+    for p in shards:
+        pi = p.info()
+        assert pi["table_bytes"] == pi["stored_rows"] * g.nt * g.nz * 4
+        assert pi["stored_rows"] <= rpr and pi["radial"] == (1 if pi["stored_rows"] < 32 * (
+            (p.shard_info()["rows"] + 31) // 32) else 0)
     with pytest.raises(PatError):
         shards[0].forward(torch.zeros((g.nz, g.ny, g.nx), device="cuda"))
     ex = LocalExchange(world)
@@ -134,7 +139,11 @@ def test_sharded_benchmark_geometry():
     info = shards[0].shard_info()
     rpr = info["rows_per_rank"]
     assert info["rows_total"] == 129 * 130 // 2 and rpr == (info["rows_total"] + 63) // 64 * 32
-    assert all(p.info()["table_bytes"] == rpr * 256 * 64 * 4 for p in shards)
+    # radial sharing among each shard's representatives: together the shards
+    # store fewer rows than one per representative
+    stored = [p.info()["stored_rows"] for p in shards]
+    assert all(p.info()["radial"] == 1 for p in shards) and sum(stored) < info["rows_total"]
+    assert all(p.info()["table_bytes"] == r * 256 * 64 * 4 for p, r in zip(shards, stored))
     # a shard's workspace: no spectra, object or data buffers, and an FFT
     # intermediate of its own 128 time samples (the full plan's holds 256)
     ws = [p.info()["workspace_bytes"] for p in shards]
