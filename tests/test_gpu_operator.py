@@ -339,6 +339,45 @@ def test_three_times_power_of_two_sampled_outputs():
         assert oracle.rel_l2(a[j], ref) < 1e-5, j
 
 
+def test_largest_padded_grid_1024():
+    """The largest supported padded length, 512^2 -> 1024^2 (8 depths, 16
+    samples): a library generated on the device (real, D4-folded, radially
+    shared: 131,841 representatives) against the oracle's closed-form
+    library at sampled time samples and depths, and an asymmetric random
+    library (complex spectra, one row per bin) against the oracle's operator."""
+    g = oracle.Grid.square(512, 8, 16)
+    med = MED_50UM
+    mz = oracle.mz_for(g.nz, g.nt, med)
+    plan = Plan(g.nx, g.ny, g.nz, g.nt, g.px, g.py,
+                medium=Medium(med.c, med.dx, med.dy, med.dz, med.dt, mz, 1))
+    info = plan.info()
+    assert info["folded"] == 1 and info["radial"] == 1, info
+    rho = synth.vessel_phantom(g.nx, g.nz, seed=3)
+    d = host(plan.forward(cuda(rho)))
+    for t in (0, 15):
+        Hf = oracle.table_kspace_closed(g, med, mz, t_idx=[t])
+        gt = oracle.Grid(g.nx, g.ny, g.nz, 1, g.px, g.py)
+        ref = oracle.forward_fft(Hf, rho, gt)[0]
+        assert np.abs(d[t] - ref).max() < 1e-5 * np.abs(d).max(), t
+    y = synth.gaussian_field((g.nt, g.ny, g.nx), 6)
+    a = host(plan.adjoint(cuda(y)))
+    for j in (0, 7):
+        Hf = oracle.table_kspace_closed(g, med, mz, z_idx=[j])
+        gz = oracle.Grid(g.nx, g.ny, 1, g.nt, g.px, g.py)
+        ref = oracle.adjoint_fft(Hf, y, gz)[0]
+        assert oracle.rel_l2(a[j], ref) < 1e-5, j
+    plan.close()
+    g2 = oracle.Grid(nx=512, ny=512, nz=2, nt=2, px=1024, py=1024)
+    h = synth.random_kernels(g2.nz, g2.nt, g2.px, g2.py, seed=7)
+    A, AT = _ref_ops(h, g2)
+    p2 = Plan(g2.nx, g2.ny, g2.nz, g2.nt, g2.px, g2.py, table=h)
+    assert p2.info()["real_table"] == 0
+    r2 = synth.blobs(g2.nx, g2.ny, g2.nz, count=6, seed=8)
+    y2 = synth.gaussian_field((g2.nt, g2.ny, g2.nx), seed=9)
+    assert oracle.rel_l2(host(p2.forward(cuda(r2))), A(r2)) < 1e-5
+    assert oracle.rel_l2(host(p2.adjoint(cuda(y2))), AT(y2)) < 1e-5
+
+
 def test_in_vivo_geometry_768():
     """The in vivo scan grid (384 x 326 transverse, padded to 768 x 768, a
     3 * 2^k length) with an asymmetric random library: H and H* against the
