@@ -200,6 +200,17 @@ def _stream(stream=None) -> int:
     return 0
 
 
+def _need(a, n: int, dtype, what: str) -> None:
+    """Raises ValueError unless `a` holds exactly n elements of numpy dtype
+    `dtype`: the C ABI takes raw pointers and sizes, so a short or wrongly
+    typed buffer would be read or written past its end."""
+    m = int(np.prod(a.shape))
+    dt = a.dtype if isinstance(a, np.ndarray) else _np_dtype(a.dtype)
+    if m != n or dt != np.dtype(dtype):
+        raise ValueError(f"{what}: expected {n} elements of {np.dtype(dtype).name}, "
+                         f"got {m} of {dt}")
+
+
 def _ptr(a) -> int:
     """Data pointer of a contiguous torch tensor or numpy array."""
     if isinstance(a, np.ndarray):
@@ -253,6 +264,8 @@ class Plan:
                  | (0 if radial else FLAG_NO_RADIAL))
         self._geom = Geometry(nx, ny, nz, nt, self.px, self.py, max_batch, flags)
         self._h = ctypes.c_void_p(0)
+        self._kp = None      # bins_padded, read once from the plan
+        self._sinf = None    # shard layout, read once from the plan
         s = _stream(stream)
         if (table is None) == (medium is None):
             raise ValueError("give exactly one of table= or medium=")
@@ -353,6 +366,12 @@ class Plan:
         dev = like.device if hasattr(like, "device") and like.device.type == "cuda" else "cpu"
         return torch.empty(shape, dtype=self._torch_dtype(), device=dev)
 
+    def _rdt(self):
+        return np.float64 if self.fp64 else np.float32
+
+    def _cdt(self):
+        return np.complex128 if self.fp64 else np.complex64
+
     def _check_dtype(self, *arrs):
         want = np.float64 if self.fp64 else np.float32
         for a in arrs:
@@ -368,6 +387,7 @@ class Plan:
         if out is None:
             out = self._empty_like_device(self.data_shape(b) if rho.ndim == 4 else
                                           self.data_shape(1)[1:], rho)
+        _need(out, b * self.nt * self.my * self.mx, self._rdt(), "out")
         _check(lib().pat_forward(self._h, _ptr(rho), _ptr(out), b, _stream(stream)))
         return out
 
@@ -378,6 +398,7 @@ class Plan:
         if out is None:
             out = self._empty_like_device(self.obj_shape(b) if d.ndim == 4 else
                                           self.obj_shape(1)[1:], d)
+        _need(out, b * self.nz * self.ny * self.nx, self._rdt(), "out")
         _check(lib().pat_adjoint(self._h, _ptr(d), _ptr(out), b, _stream(stream)))
         return out
 
@@ -385,8 +406,10 @@ class Plan:
         """grad = H*(H x - y) (Eq. 15); returns (grad, ||H x - y||^2 or None)."""
         self._check_dtype(x, y)
         b = self._batch_of(x, self.nz * self.ny * self.nx)
+        _need(y, b * self.nt * self.my * self.mx, self._rdt(), "y")
         if out is None:
             out = self._empty_like_device(tuple(x.shape), x)
+        _need(out, b * self.nz * self.ny * self.nx, self._rdt(), "out")
         r2 = ctypes.c_double(0.0)
         _check(lib().pat_gradient(self._h, _ptr(x), _ptr(y), _ptr(out), b,
                                   ctypes.byref(r2) if resid else None, _stream(stream)))
@@ -395,6 +418,7 @@ class Plan:
     def power_norm(self, v0, iters: int, stream=None) -> float:
         """L = ||H*H|| by power iteration from v0."""
         self._check_dtype(v0)
+        _need(v0, self.nz * self.ny * self.nx, self._rdt(), "v0")
         Lout = ctypes.c_double(0.0)
         _check(lib().pat_power_norm(self._h, _ptr(v0), iters, ctypes.byref(Lout), _stream(stream)))
         return Lout.value
@@ -415,6 +439,7 @@ class Plan:
             x = self._empty_like_device(self.obj_shape(b) if y.ndim == 4 else
                                         self.obj_shape(1)[1:], y)
             warm_start = False
+        _need(x, b * self.nz * self.ny * self.nx, self._rdt(), "x")
         prm = FistaParams(iters, power_iters, 1 if warm_start else 0, 0, lam, L)
         rep = FistaReport()
         _check(lib().pat_fista_solve(self._h, _ptr(y), _ptr(x), b, ctypes.byref(prm),
@@ -435,6 +460,7 @@ class Plan:
     def slot_load(self, slot: int, y, lam: float, L: float, stream=None) -> None:
         """Loads one FISTA request (data y [nt][my][mx]) into `slot`."""
         self._check_dtype(y)
+        _need(y, self.nt * self.my * self.mx, self._rdt(), "y")
         _check(lib().pat_slot_load(self._h, slot, _ptr(y), lam, L, _stream(stream)))
 
     def slot_move(self, dst: int, src: int, stream=None) -> None:
@@ -452,6 +478,7 @@ class Plan:
         if out is None:
             torch = _torch()
             out = torch.empty((self.nz, self.ny, self.nx), dtype=self._torch_dtype(), device="cuda")
+        _need(out, self.nz * self.ny * self.nx, self._rdt(), "out")
         r2 = ctypes.c_double(0.0)
         _check(lib().pat_slot_read(self._h, slot, _ptr(out), ctypes.byref(r2) if resid else None,
                                    _stream(stream)))
@@ -459,9 +486,11 @@ class Plan:
 
     # ------------------------------------------------------------------ frequency shards
     def shard_info(self) -> dict:
-        inf = ShardInfo()
-        _check(lib().pat_plan_shard_info(self._h, ctypes.byref(inf)))
-        return inf.as_dict()
+        if self._sinf is None:
+            inf = ShardInfo()
+            _check(lib().pat_plan_shard_info(self._h, ctypes.byref(inf)))
+            self._sinf = inf.as_dict()
+        return dict(self._sinf)
 
     def shard_spectrum(self, side: int, x, send=None, stream=None):
         """Stage i of this rank's slices (side 0: depth slices of an object,
@@ -470,19 +499,24 @@ class Plan:
         torch = _torch()
         inf = self.shard_info()
         n = inf["nt_local"] if side else inf["nz_local"]
+        _need(x, n * self.ny * self.nx, np.float32, "x")
         if send is None:
             send = torch.empty((inf["world"], n, inf["slot_width"]), dtype=torch.complex64,
                                device=x.device)
+        _need(send, inf["world"] * n * inf["slot_width"], np.complex64, "send")
         _check(lib().pat_shard_spectrum(self._h, side, _ptr(x), _ptr(send), _stream(stream)))
         return send
 
     def shard_contract(self, inp, out=None, adjoint: bool = False, stream=None):
         """Stage ii on this rank's rows: [nz][W] -> [nt][W] (or the adjoint)."""
         torch = _torch()
+        inf = self.shard_info()
+        W = inf["slot_width"]
+        _need(inp, (self.nt if adjoint else self.nz) * W, np.complex64, "inp")
+        rows = self.nz if adjoint else self.nt
         if out is None:
-            inf = self.shard_info()
-            rows = self.nz if adjoint else self.nt
-            out = torch.empty((rows, inf["slot_width"]), dtype=torch.complex64, device=inp.device)
+            out = torch.empty((rows, W), dtype=torch.complex64, device=inp.device)
+        _need(out, rows * W, np.complex64, "out")
         _check(lib().pat_shard_contract(self._h, 1 if adjoint else 0, _ptr(inp), _ptr(out),
                                         _stream(stream)))
         return out
@@ -494,8 +528,12 @@ class Plan:
         torch = _torch()
         inf = self.shard_info()
         n = inf["nt_local"] if side else inf["nz_local"]
+        _need(recv, inf["world"] * n * inf["slot_width"], np.complex64, "recv")
         if out is None:
             out = torch.empty((n, self.ny, self.nx), dtype=torch.float32, device=recv.device)
+        _need(out, n * self.ny * self.nx, np.float32, "out")
+        if sub is not None:
+            _need(sub, n * self.ny * self.nx, np.float32, "sub")
         r2 = ctypes.c_double(0.0)
         _check(lib().pat_shard_image(self._h, side, _ptr(recv), _ptr(out),
                                      _ptr(sub) if sub is not None else None,
@@ -519,11 +557,18 @@ class Plan:
         cdt = torch.complex128 if self.fp64 else torch.complex64
         if out is None:
             out = torch.empty((S, self.px // 2 + 1, self.py), dtype=cdt, device=x.device)
+        _need(out, S * (self.px // 2 + 1) * self.py, self._cdt(), "out")
         _check(lib().pat_stage_spectrum(self._h, _ptr(x), _ptr(out), S, _stream(stream)))
         return out
 
     def stage_contract(self, X, out, batch: int = 1, adjoint: bool = False, stream=None):
         """Stage ii alone on complex [batch][rows][bins_padded] device arrays."""
+        if self._kp is None:
+            self._kp = int(self.info()["bins_padded"])
+        kp = self._kp
+        rin, rout = (self.nt, self.nz) if adjoint else (self.nz, self.nt)
+        _need(X, batch * rin * kp, self._cdt(), "X")
+        _need(out, batch * rout * kp, self._cdt(), "out")
         _check(lib().pat_stage_contract(self._h, _ptr(X), _ptr(out), batch, 1 if adjoint else 0,
                                         _stream(stream)))
         return out
@@ -538,8 +583,10 @@ class Plan:
     def stage_image(self, X, out=None, stream=None):
         """Unnormalised inverse 2D DFT of [S][px//2+1][py] spectra, real part, cropped to [S][ny][nx]."""
         S = int(np.prod(X.shape)) // ((self.px // 2 + 1) * self.py)
+        _need(X, S * (self.px // 2 + 1) * self.py, self._cdt(), "X")
         if out is None:
             out = self._empty_like_device((S, self.ny, self.nx), X)
+        _need(out, S * self.ny * self.nx, self._rdt(), "out")
         _check(lib().pat_stage_image(self._h, _ptr(X), _ptr(out), S, _stream(stream)))
         return out
 
@@ -588,7 +635,8 @@ def spectrum_noalloc(x, px: int, py: int, out=None, stream=None):
 def fista_step(y, xprev, grad, invL: float, lamL: float, beta: float, stream=None) -> None:
     """pat_fista_step: the FISTA update of Eq. 14-15 in place on float32 CUDA arrays."""
     n = int(np.prod(y.shape))
-    assert int(np.prod(xprev.shape)) == n and int(np.prod(grad.shape)) == n
+    for a, what in ((y, "y"), (xprev, "xprev"), (grad, "grad")):
+        _need(a, n, np.float32, what)
     _check(lib().pat_fista_step(_ptr(y), _ptr(xprev), _ptr(grad), n, invL, lamL, beta,
                                 _stream(stream)))
 
@@ -596,7 +644,8 @@ def fista_step(y, xprev, grad, invL: float, lamL: float, beta: float, stream=Non
 def axpby(y, x, a: float, b: float, stream=None) -> None:
     """y = a x + b y in place on float32 CUDA arrays (pat_axpby)."""
     n = int(np.prod(y.shape))
-    assert int(np.prod(x.shape)) == n
+    _need(y, n, np.float32, "y")
+    _need(x, n, np.float32, "x")
     _check(lib().pat_axpby(_ptr(y), _ptr(x), n, a, b, _stream(stream)))
 
 

@@ -5,6 +5,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 from paper_2603_28150_gb300 import pat
@@ -156,3 +157,20 @@ def test_shard_arguments_without_gpu():
                                           ctypes.byref(out)) == pat.PAT_ERR_UNSUPPORTED
     assert L.pat_shard_spectrum(None, 0, None, None, None) == pat.PAT_ERR_ARG
     assert L.pat_fista_step(None, None, None, 5, 1.0, 0.0, 0.0, None) == pat.PAT_ERR_ARG
+
+
+def test_binding_rejects_mismatched_buffers_without_gpu():
+    """The C ABI takes raw pointers and sizes: the Python binding checks the
+    element count and type of every array it forwards, before any library
+    call, so a short or wrongly typed buffer never reaches a kernel."""
+    torch = pytest.importorskip("torch")
+    f32, f64 = torch.zeros(8), torch.zeros(8, dtype=torch.float64)
+    with pytest.raises(ValueError, match="xprev"):
+        pat.fista_step(f32, f64, f32, 1.0, 0.0, 0.0)
+    with pytest.raises(ValueError, match="grad"):
+        pat.fista_step(f32, f32, torch.zeros(7), 1.0, 0.0, 0.0)
+    with pytest.raises(ValueError, match="x"):
+        pat.axpby(f32, torch.zeros(9), 1.0, 1.0)
+    with pytest.raises(ValueError, match="expected 8 elements of float32"):
+        pat._need(np.zeros(8), 8, np.float32, "a")
+    pat._need(np.zeros((2, 4), np.float32), 8, np.float32, "a")  # shape is free, count is not

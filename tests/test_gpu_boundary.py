@@ -80,6 +80,36 @@ def test_workspace_rejected_when_too_small_misaligned_or_host():
     Plan(G.nx, G.ny, G.nz, G.nt, G.px, G.py, medium=MED, workspace=_ws(n)[1]).close()
 
 
+def test_binding_rejects_short_or_mistyped_buffers():
+    """Caller-supplied outputs and second inputs of the operator, stage and
+    slot calls are checked (element count and type) before the library is
+    called; the plan then still computes correctly."""
+    import torch
+    p = Plan(G.nx, G.ny, G.nz, G.nt, G.px, G.py, medium=MED)
+    rho = torch.rand((G.nz, G.ny, G.nx), device="cuda")
+    d = torch.rand((G.nt, G.ny, G.nx), device="cuda")
+    short_d = torch.empty(G.nt * G.ny * G.nx - 1, device="cuda")
+    f64_rho = torch.empty((G.nz, G.ny, G.nx), dtype=torch.float64, device="cuda")
+    kp = p.info()["bins_padded"]
+    X = torch.zeros((G.nz, kp), dtype=torch.complex64, device="cuda")
+    with pytest.raises(ValueError, match="out"):
+        p.forward(rho, out=short_d)
+    with pytest.raises(ValueError, match="out"):
+        p.adjoint(d, out=f64_rho)
+    with pytest.raises(ValueError, match="y"):
+        p.gradient(rho, short_d)
+    with pytest.raises(ValueError, match="X"):
+        p.stage_contract(X[:-1], torch.zeros((G.nt, kp), dtype=torch.complex64, device="cuda"))
+    with pytest.raises(ValueError, match="out"):
+        p.stage_contract(X, torch.zeros((G.nt, kp), dtype=torch.complex128, device="cuda"))
+    with pytest.raises(ValueError, match="x"):
+        p.fista(d, x=short_d, iters=2, L=1.0, warm_start=True)
+    out = torch.full((G.nt, G.ny, G.nx), float("nan"), device="cuda")
+    p.forward(rho, out=out)
+    assert torch.equal(out, p.forward(rho))
+    p.close()
+
+
 @pytest.mark.parametrize("kind", ["kspace", "table_folded", "table_complex", "bf16"])
 def test_failed_allocation_cleans_up(monkeypatch, kind):
     """The n-th device allocation of plan creation fails (n = 1, 2, ...): each
