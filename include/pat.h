@@ -226,13 +226,18 @@ int pat_plan_create_kspace_with_workspace(const pat_geometry* g, const pat_mediu
                                           pat_plan** out);
 
 /* Frees the plan's device memory (synchronises the device first); a
- * caller-owned workspace is left alone. NULL is a no-op. */
+ * caller-owned workspace is left alone. NULL is a no-op. (Plan management:
+ * no counterpart in the paper.) */
 int pat_plan_destroy(pat_plan* plan);
 
+/* Fills *info with the plan's representation of the stored library (Sec. 3.2:
+ * the spectra precomputed once and kept resident; Sec. 4: their size) and its
+ * sizes. No device call; PAT_ERR_ARG for a NULL plan or info. */
 int pat_plan_info(const pat_plan* plan, pat_plan_info_t* info);
 
 /* Device bytes a plan for `g` would take, before creating it (admission
- * control): *table_bytes for the representation of the library given by
+ * control; the stored operator's size is the limitation Sec. 4 discusses):
+ * *table_bytes for the representation of the library given by
  * real_table: 0 complex, 1 real (one row per bin), 2 real D4-folded, 3 real
  * folded with radial sharing (a k-space library with dx = dy gets 3); 2 and 3
  * need a square padded grid in single precision, else they count as 1. With
@@ -245,8 +250,11 @@ int pat_plan_estimate(const pat_geometry* g, int real_table, int64_t* table_byte
 /* Message of the last failure on the calling thread ("" if none). */
 const char* pat_last_error(void);
 
-/* Sets the smallest batch that uses the tensor-core contraction of a plan
- * built with PAT_FLAG_BF16_SPLIT (default 2; 0 = always the CUDA-core path). */
+/* Sets the smallest batch that uses the tensor-core contraction (stage ii,
+ * Eq. 16 term (ii), on split-BF16 tables) of a plan built with
+ * PAT_FLAG_BF16_SPLIT (default 2; 0 = always the CUDA-core path). PAT_ERR_ARG
+ * for a negative min_batch; PAT_ERR_UNSUPPORTED for min_batch > 0 on a plan
+ * without split-BF16 tables. */
 int pat_plan_set_tensor_batch(pat_plan* plan, int min_batch);
 
 /* Measurement operator (Sec. 2.3, Sec. 3.3): the object stays on the
@@ -327,7 +335,8 @@ int pat_gradient(pat_plan* plan, const void* x, const void* y, void* grad, int b
 int pat_power_norm(pat_plan* plan, const void* v0, int iters, double* L_out,
                    pat_stream stream);
 
-/* pat_power_norm from a seeded start vector generated on the device:
+/* pat_power_norm (the step-size constant L of Eq. 12-14; not printed in the
+ * paper) from a seeded start vector generated on the device:
  *   v0[i] = 2 u_i - 1,  u_i = (splitmix64(seed + (i + 1) * 0x9E3779B97F4A7C15) >> 11) * 2^-53,
  * i = 0 .. nz*ny*nx - 1 in the object's memory order (x fastest), splitmix64
  * the finaliser of Steele, Lea & Flood (2014): z ^= z >> 30; z *= 0xBF58476D1CE4E5B9;
@@ -466,7 +475,9 @@ int pat_fold_blocks(int P, int radial, int64_t* nrb, int64_t* nch, int32_t* rb_r
                     int32_t* rb_chunk, int32_t* row_rep, int32_t* rep_row);
 
 /* Host only (no device call): the partition of rank `rank` of `world` for a
- * library stored folded (`fold` = 1) or per bin. Optional outputs (host
+ * library stored folded (`fold` = 1) or per bin (stage ii is independent per
+ * frequency bin, Eq. 16 term (ii); splitting its rows divides the stored
+ * operator of Sec. 4 over the ranks). Optional outputs (host
  * arrays): zmap[bins] / tmap[bins], the position of every bin k of one slice
  * in the depth-side / time-side exchange buffer (owner q of k's row:
  * q * (slices per rank) * W + slot of k), and members_local[rows_per_rank * 4]
@@ -482,6 +493,8 @@ int pat_shard_layout(const pat_geometry* g, int fold, int rank, int world, pat_s
  * max(nz, nt) / world slices, reduction scratch and scalars. */
 int pat_plan_create_kspace_shard(const pat_geometry* g, const pat_medium* m, int rank, int world,
                                  pat_stream stream, pat_plan** out);
+/* The partition of a shard plan (as pat_shard_layout); PAT_ERR_ARG for a plan
+ * that is not a shard. No device call. */
 int pat_plan_shard_info(const pat_plan* plan, pat_shard_info* info);
 
 /* Stage i of this rank's slices (side 0: depth slices of an object, side 1:
@@ -508,7 +521,8 @@ int pat_fista_step(float* y, float* xprev, const float* grad, int64_t n, double 
                    double beta, pat_stream stream);
 
 /* y = a x + b y on n device floats (x may equal y): the scaling and
- * combination steps of a distributed power iteration or data synthesis. */
+ * combination steps of a distributed power iteration (the L of Eq. 12-14) or
+ * data synthesis. */
 int pat_axpby(float* y, const float* x, int64_t n, double a, double b, pat_stream stream);
 
 /* Stage ii of the folded split-BF16 path as the operator runs it, on spectra
